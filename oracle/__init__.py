@@ -1,0 +1,304 @@
+"""FP64 CPU oracle of the Trick-GS rasterizer hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package. It is built from ``tgs_oracle.c`` (plain C, double precision) and shares
+no code with the CUDA library.
+
+Functions follow the paper's notation: Eq. 1 (EWA projection to G'), Eq. 2 (front-to-back
+blending), the straight-through volume mask and the straight-through SH-band masks (Eq.
+sh-masks). ``tgs_oracle.c`` states the conventions the paper inherits from 3DGS.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "tgs_oracle.c")
+
+SUPPORT_BOX3 = 0
+SUPPORT_ALPHA = 1
+
+
+def build(force=False):
+    """Compile the oracle with gcc (no contraction of a*b+c, so x86 and Arm agree)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp,
+                           _SRC, "-lm", "-lpthread"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+_dp = C.POINTER(C.c_double)
+_i32p = C.POINTER(C.c_int32)
+_u32p = C.POINTER(C.c_uint32)
+_u64p = C.POINTER(C.c_uint64)
+_u8p = C.POINTER(C.c_uint8)
+
+
+class _Params(C.Structure):
+    _fields_ = [("n", C.c_int64), ("means", _dp), ("log_scales", _dp), ("quats", _dp),
+                ("opacity_logits", _dp), ("sh_dc", _dp), ("sh_rest", _dp),
+                ("sh_degree", _u8p), ("mask_logits", _dp), ("sh_mask_logits", _dp),
+                ("deg_max", C.c_int64)]
+
+
+class _Grads(C.Structure):
+    _fields_ = [(k, _dp) for k in ("means", "log_scales", "quats", "opacity_logits", "sh_dc",
+                                   "sh_rest", "mask_logits", "sh_mask_logits")]
+
+
+class _Splats(C.Structure):
+    _fields_ = [("mean2d", _dp), ("depth", _dp), ("conic", _dp), ("opacity", _dp),
+                ("rgb", _dp), ("radius", _i32p), ("rect", _i32p), ("m_all", _dp),
+                ("m_edge", _dp)]
+
+
+def _declare(L):
+    L.orc_sh_basis.argtypes = [C.c_int64, _dp, _dp, _dp]
+    L.orc_preprocess.argtypes = [C.POINTER(_Params), _dp, _dp, C.POINTER(_Splats)]
+    L.orc_count_keys.argtypes = [C.c_int64, _i32p, _i32p, C.c_int]
+    L.orc_count_keys.restype = C.c_int64
+    L.orc_keys.argtypes = [C.c_int64, _i32p, _i32p, _dp, C.c_int, C.c_int, C.c_int, C.c_uint64,
+                           C.c_uint32, _u64p, _u32p, _u32p]
+    L.orc_keys.restype = C.c_int64
+    L.orc_blend.argtypes = [C.c_int64, C.POINTER(_Splats), C.c_int, C.c_int, C.c_int, _dp,
+                            C.c_int, C.c_int, C.c_int, _dp, _dp, _i32p, _i32p, _i32p, _dp]
+    L.orc_blend_backward.argtypes = [C.c_int64, C.POINTER(_Splats), C.c_int, C.c_int, C.c_int,
+                                     _dp, _dp, C.c_int, _dp]
+    L.orc_preprocess_backward.argtypes = [C.POINTER(_Params), _dp, _dp, _dp, C.POINTER(_Grads),
+                                          _dp, _i32p, _i32p]
+    L.orc_l1.argtypes = [C.c_int64, _dp, _dp, C.c_double, _dp]
+    L.orc_l1.restype = C.c_double
+
+
+def _ptr(a, t=_dp):
+    if a is None:
+        return C.cast(None, t)
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(t)
+
+
+@dataclasses.dataclass
+class Settings:
+    """Rasterizer settings: tile size, footprint rule, mask thresholds, near plane, background
+    and the low-pass term s of Sigma' + sI."""
+    tile: int = 16
+    support: int = SUPPORT_BOX3
+    eps_mask: float = 0.05
+    eps_sh: float = 0.1
+    near: float = 0.2
+    bg: tuple = (0.0, 0.0, 0.0)
+    low_pass: float = 0.3
+
+
+def cam_vec(cam, low_pass):
+    v = np.zeros(22)
+    vm = np.asarray(cam.viewmat, dtype=np.float64)
+    v[0:9] = vm[:3, :3].reshape(-1)
+    v[9:12] = vm[:3, 3]
+    v[12:15] = np.asarray(cam.campos, dtype=np.float64)
+    v[15:22] = [cam.fx, cam.fy, cam.cx, cam.cy, cam.width, cam.height, low_pass]
+    return v
+
+
+def cfg_vec(st: Settings):
+    return np.array([st.tile, st.support, st.eps_mask, st.eps_sh, st.near, *st.bg],
+                    dtype=np.float64)
+
+
+class _Scene:
+    """Keeps the float64 copies alive while the C structure points at them."""
+
+    def __init__(self, scene):
+        d = lambda k: None if scene.get(k) is None else np.ascontiguousarray(
+            scene[k], dtype=np.float64)
+        self.arrs = {k: d(k) for k in ("means", "log_scales", "quats", "opacity_logits",
+                                       "sh_dc", "sh_rest", "mask_logits", "sh_mask_logits")}
+        self.deg = None if scene.get("sh_degree") is None else np.ascontiguousarray(
+            scene["sh_degree"], dtype=np.uint8)
+        self.n = self.arrs["means"].shape[0]
+        deg_max = 3 if self.arrs["sh_rest"] is not None else 0
+        if "deg_max" in scene:
+            deg_max = scene["deg_max"]
+        a = self.arrs
+        self.c = _Params(self.n, _ptr(a["means"]), _ptr(a["log_scales"]), _ptr(a["quats"]),
+                         _ptr(a["opacity_logits"]), _ptr(a["sh_dc"]), _ptr(a["sh_rest"]),
+                         _ptr(self.deg, _u8p), _ptr(a["mask_logits"]),
+                         _ptr(a["sh_mask_logits"]), deg_max)
+
+
+def sh_basis(dirs):
+    dirs = np.ascontiguousarray(dirs, dtype=np.float64)
+    n = dirs.shape[0]
+    Y = np.zeros((n, 16))
+    dY = np.zeros((n, 16, 3))
+    lib().orc_sh_basis(n, _ptr(dirs), _ptr(Y), _ptr(dY))
+    return Y, dY
+
+
+def _alloc_splats(n):
+    return dict(mean2d=np.zeros((n, 2)), depth=np.zeros(n), conic=np.zeros((n, 3)),
+                opacity=np.zeros(n), rgb=np.zeros((n, 3)), radius=np.zeros(n, np.int32),
+                rect=np.zeros((n, 4), np.int32), m_all=np.full(n, np.inf),
+                m_edge=np.full(n, np.inf))
+
+
+def _splats_struct(s):
+    return _Splats(_ptr(s["mean2d"]), _ptr(s["depth"]), _ptr(s["conic"]), _ptr(s["opacity"]),
+                   _ptr(s["rgb"]), _ptr(s["radius"], _i32p), _ptr(s["rect"], _i32p),
+                   _ptr(s.get("m_all")), _ptr(s.get("m_edge")))
+
+
+def preprocess(scene, cam, st: Settings):
+    """Per-Gaussian projection of one view (Eq. 1 with masks and SH colour)."""
+    sc = _Scene(scene)
+    out = _alloc_splats(sc.n)
+    lib().orc_preprocess(C.byref(sc.c), _ptr(cam_vec(cam, st.low_pass)), _ptr(cfg_vec(st)),
+                         C.byref(_splats_struct(out)))
+    return out
+
+
+def splats_from(mean2d, depth, conic, opacity, rgb, radius, rect):
+    """Per-Gaussian records given from outside (e.g. float32 values), promoted to float64."""
+    f = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    i = lambda a: np.ascontiguousarray(a, dtype=np.int32)
+    n = np.asarray(radius).shape[0]
+    return dict(mean2d=f(mean2d).reshape(n, 2), depth=f(depth).reshape(n),
+                conic=f(conic).reshape(n, 3), opacity=f(opacity).reshape(n),
+                rgb=f(rgb).reshape(n, 3), radius=i(radius).reshape(n), rect=i(rect).reshape(n, 4),
+                m_all=None, m_edge=None)
+
+
+def keys(radius, rect, depth, W, H, tile, tile_offset=0, value_offset=0):
+    """Key emission, stable sort and tile ranges of one view."""
+    radius = np.ascontiguousarray(radius, np.int32)
+    rect = np.ascontiguousarray(rect, np.int32)
+    depth = np.ascontiguousarray(depth, np.float64)
+    n = radius.shape[0]
+    L = lib()
+    K = L.orc_count_keys(n, _ptr(radius, _i32p), _ptr(rect, _i32p), tile)
+    gx, gy = (W + tile - 1) // tile, (H + tile - 1) // tile
+    k = np.zeros(max(K, 1), np.uint64)
+    v = np.zeros(max(K, 1), np.uint32)
+    r = np.zeros((gx * gy, 2), np.uint32)
+    L.orc_keys(n, _ptr(radius, _i32p), _ptr(rect, _i32p), _ptr(depth), W, H, tile, tile_offset,
+               value_offset, _ptr(k, _u64p), _ptr(v, _u32p), _ptr(r, _u32p))
+    return k[:K], v[:K], r
+
+
+def blend(splats, W, H, tile=16, bg=(0.0, 0.0, 0.0), brute=False, nthreads=1,
+          margins=False, depth_margin=False):
+    """Front-to-back blending of one view (Eq. 2). Returns image [3,H,W], T_final, last
+    (1-based position in the tile list of the last contributor, 0 if none), n_contrib,
+    n_examined and, if requested, the per-pixel decision margin."""
+    n = splats["radius"].shape[0]
+    out = dict(image=np.zeros((3, H, W)), T_final=np.zeros((H, W)),
+               last=np.zeros((H, W), np.int32), n_contrib=np.zeros((H, W), np.int32),
+               n_examined=np.zeros((H, W), np.int32))
+    if margins:
+        out["margin"] = np.zeros((H, W))
+    bgv = np.asarray(bg, dtype=np.float64)
+    lib().orc_blend(n, C.byref(_splats_struct(splats)), W, H, tile, _ptr(bgv), int(brute),
+                    nthreads, int(depth_margin), _ptr(out["image"]), _ptr(out["T_final"]),
+                    _ptr(out["last"], _i32p), _ptr(out["n_contrib"], _i32p),
+                    _ptr(out["n_examined"], _i32p), _ptr(out.get("margin")))
+    return out
+
+
+def blend_backward(splats, W, H, dL_dimg, tile=16, bg=(0.0, 0.0, 0.0), nthreads=1):
+    """dL/d(mean2d[2], conic[3], opacity, rgb[3]) per Gaussian, [n,9]."""
+    n = splats["radius"].shape[0]
+    g9 = np.zeros((n, 9))
+    d = np.ascontiguousarray(dL_dimg, dtype=np.float64)
+    bgv = np.asarray(bg, dtype=np.float64)
+    lib().orc_blend_backward(n, C.byref(_splats_struct(splats)), W, H, tile, _ptr(bgv), _ptr(d),
+                             nthreads, _ptr(g9))
+    return g9
+
+
+GRAD_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh_dc", "sh_rest",
+             "mask_logits", "sh_mask_logits")
+
+
+def zero_grads(scene):
+    return {k: (None if scene.get(k) is None else np.zeros(np.shape(scene[k])))
+            for k in GRAD_KEYS}
+
+
+def preprocess_backward(scene, cam, st: Settings, g9, grads, stats=None):
+    """Adds this view's parameter gradients into ``grads`` and its statistics into ``stats``
+    (dict with accum float64 [n], count int32 [n], max_radius int32 [n])."""
+    sc = _Scene(scene)
+    g9 = np.ascontiguousarray(g9, dtype=np.float64)
+    G = _Grads(*[_ptr(grads.get(k)) for k in GRAD_KEYS])
+    s = stats or {}
+    lib().orc_preprocess_backward(C.byref(sc.c), _ptr(cam_vec(cam, st.low_pass)),
+                                  _ptr(cfg_vec(st)), _ptr(g9), C.byref(G),
+                                  _ptr(s.get("accum")), _ptr(s.get("count"), _i32p),
+                                  _ptr(s.get("max_radius"), _i32p))
+    return grads
+
+
+def render(scene, cam, st: Settings, brute=False, nthreads=1, margins=False):
+    """Full forward of one view: preprocess, then blend."""
+    sp = preprocess(scene, cam, st)
+    out = blend(sp, cam.width, cam.height, st.tile, st.bg, brute=brute, nthreads=nthreads,
+                margins=margins, depth_margin=margins)
+    out["splats"] = sp
+    return out
+
+
+def new_stats(n):
+    return dict(accum=np.zeros(n), count=np.zeros(n, np.int32),
+                max_radius=np.zeros(n, np.int32))
+
+
+def grad(scene, cams, st: Settings, dL_dimgs, nthreads=1):
+    """Gradients of L with respect to every input, given dL/dimage per view, plus the
+    densification statistics; returns (grads, stats, per-view screen-space grads)."""
+    n = np.shape(scene["means"])[0]
+    grads = zero_grads(scene)
+    stats = new_stats(n)
+    g9s = []
+    for cam, d in zip(cams, dL_dimgs):
+        sp = preprocess(scene, cam, st)
+        g9 = blend_backward(sp, cam.width, cam.height, d, st.tile, st.bg, nthreads)
+        preprocess_backward(scene, cam, st, g9, grads, stats)
+        g9s.append(g9)
+    return grads, stats, g9s
+
+
+def l1(images, targets):
+    """Mean over views of the mean over 3HW of |C - target|, and dL/dC per view."""
+    V = len(images)
+    loss = 0.0
+    gs = []
+    L = lib()
+    for img, tgt in zip(images, targets):
+        img = np.ascontiguousarray(img, np.float64)
+        tgt = np.ascontiguousarray(tgt, np.float64)
+        g = np.zeros_like(img)
+        loss += L.orc_l1(img.size, _ptr(img), _ptr(tgt), 1.0 / (img.size * V), _ptr(g))
+        gs.append(g)
+    return loss, gs
