@@ -1,0 +1,253 @@
+/*
+ * tgs.h -- C ABI of libtgs, a GB300 (sm_103a) differentiable Gaussian-splatting rasterizer
+ * with the learned volume masks and SH-band masks of Trick-GS (arXiv 2501.14534).
+ *
+ * The library computes, for N Gaussians and V pinhole views:
+ *   (a) preprocess: the straight-through volume mask M applied to opacity and scale
+ *       (Sec. "Pruning with Volume Masking", mask equation), the EWA projection of each 3D
+ *       Gaussian to the 2D Gaussian G'(x) = exp(-1/2 (x-mu')^T Sigma'^-1 (x-mu')) with
+ *       Sigma' = J W Sigma W^T J^T + sI (Sec. "Preliminaries", Eq. 1; s = 0.3 from Sec.
+ *       "Progressive training by scales of Gaussians"), the footprint radius and pixel rect,
+ *       and the view-dependent colour from SH of degree <= 3 with per-band straight-through
+ *       masks (Sec. "Spherical Harmonic (SH) Masking", Eq. sh-masks);
+ *   (b) key emission of (tile id, depth bits) per touched tile, a stable radix sort and
+ *       per-tile ranges;
+ *   (c) front-to-back alpha blending C = sum_i c_i a_i prod_{j<i} (1 - a_j) (Eq. 2);
+ *   (d) the backward of (c) and (a), including the gradients of the mask logits through the
+ *       straight-through estimator, and the 2D-mean gradient-norm statistics used for
+ *       densification and pruning (Sec. "Preliminaries": pruning and densification by
+ *       gradient magnitudes).
+ *
+ * Conventions the paper inherits from 3DGS, fixed here:
+ *   - camera: world->camera 4x4 row-major matrix, x right, y down, z forward; pixel (px, py)
+ *     samples the Gaussian at integer coordinates in the frame mean2d = f t_xy / t_z + c - 1/2;
+ *   - near plane: Gaussians with t_z <= near are culled; the Jacobian uses t_x/t_z clamped to
+ *     +-1.3 * W / (2 fx) (y likewise) and is differentiated exactly, clamp included;
+ *   - radius r = ceil(3 sqrt(lambda_max)) (TGS_SUPPORT_BOX3) or the exact alpha >= 1/255 radius
+ *     (TGS_SUPPORT_ALPHA), lambda_max = mid + sqrt(max(0.1, mid^2 - det));
+ *   - a Gaussian covers exactly the pixels of its inclusive pixel rect
+ *     [ceil(mx - r), floor(mx + r)] x [ceil(my - r), floor(my + r)] clipped to the image, so
+ *     the image does not depend on the tile size;
+ *   - blending: a = min(0.99, o' G'(p)); fragments with a < 1/255 are skipped; a pixel stops
+ *     before the fragment that would bring T below 1e-4; out = C + T_final * bg;
+ *   - colour: c = max(0, 1/2 + sum_l M^l sum_m Y_lm(d) f_lm), d = unit(mean - campos);
+ *   - mask thresholds: M = 1 iff logit > float32(log(eps / (1 - eps))).
+ *
+ * Data layout (all float32 unless stated, device memory, C-contiguous):
+ *   Gaussians (structure of arrays): means [N,3], log_scales [N,3], quats [N,4] (w,x,y,z;
+ *   normalised inside), opacity_logits [N], sh_dc [N,3], sh_rest [N,15,3] (bands 1..3,
+ *   coefficient-major, channel-minor), sh_degree uint8 [N] (optional), mask_logits [N]
+ *   (optional), sh_mask_logits [N,3] (optional).
+ *   Images: [3,H,W] planar RGB. T_final [H,W]. last [H,W] int32: 1-based position, within
+ *   the pixel's tile list, of its last contributing Gaussian (0: none).
+ *   Splat record (one per (view, Gaussian), 12 x 32 bit, index v * N + g):
+ *     [0..1] mean2d, [2..4] conic a, b, c of Sigma'^-1 = [[a, b], [b, c]], [5] opacity o',
+ *     [6..8] rgb, [9] uint32 x_lo | x_hi << 16, [10] uint32 y_lo | y_hi << 16, [11] depth t_z.
+ *   Splat gradient record (12 floats, same index): dL/d mean2d [0..1], conic a, b, c [2..4]
+ *     (with respect to the scalar b of power = -1/2 (a dx^2 + c dy^2) - b dx dy), opacity [5],
+ *     rgb [6..8]; [9..11] unused.
+ *
+ * Ownership: the caller allocates every input and output pointer passed in (device memory
+ * unless stated). A tgs_ctx owns a device scratch arena (sort buffers, splat records, key
+ * lists) that it grows on demand outside stream capture and frees in tgs_destroy. Nothing is
+ * freed across the ABI. Calls are asynchronous on the given stream except where stated.
+ *
+ * Errors: every call returns a tgs_status; no C++ exception crosses the ABI. Errors found on
+ * the device (key capacity overflow, a bounded wait that ran out) are recorded in a device
+ * status word and returned by tgs_poll_status (which synchronises the stream).
+ */
+#ifndef TGS_H
+#define TGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t tgs_status;
+#define TGS_OK 0
+#define TGS_ERR_INVALID_ARG 1   /* a pointer, size or setting is out of range */
+#define TGS_ERR_CUDA 2          /* a CUDA runtime call failed */
+#define TGS_ERR_CAPACITY 3      /* more (Gaussian, tile) keys than the key capacity */
+#define TGS_ERR_TIMEOUT 4       /* a bounded device wait ran out; the results are invalid */
+#define TGS_ERR_OOM 5           /* device memory for the scratch arena could not be had */
+#define TGS_ERR_NOT_SUPPORTED 6 /* e.g. a tile size or launch shape that is not compiled */
+
+#define TGS_SUPPORT_BOX3 0      /* 3-sigma square box (3DGS) */
+#define TGS_SUPPORT_ALPHA 1     /* smallest box outside which a < 1/255 */
+
+#define TGS_MAX_VIEWS 64        /* views per call */
+
+/* flags */
+#define TGS_ACCUMULATE 1u       /* add parameter gradients into the outputs instead of overwriting */
+#define TGS_NO_SH_REST_GRAD 2u  /* skip dL/d sh_rest (SH rest bands updated every 16 steps) */
+#define TGS_USE_GRAPH 4u        /* batched step: replay a captured CUDA graph when arguments repeat */
+
+typedef struct tgs_ctx tgs_ctx;
+typedef void *tgs_stream; /* a cudaStream_t; NULL is the legacy default stream */
+
+typedef struct {
+    int32_t tile;          /* tile edge in pixels: 8, 16 or 32 */
+    int32_t ppt;           /* pixels per thread in the blend kernels: 1, 2 or 4 */
+    int32_t support;       /* TGS_SUPPORT_BOX3 or TGS_SUPPORT_ALPHA */
+    float low_pass;        /* s of Sigma' + sI (default 0.3) */
+    float eps_mask;        /* volume-mask threshold eps_m (default 0.05) */
+    float eps_sh;          /* SH-band-mask threshold eps_sh (default 0.1) */
+    float near_plane;      /* default 0.2 */
+    float bg[3];           /* background colour (default 0) */
+    int64_t key_capacity;  /* (Gaussian, tile) keys the batched path may hold; 0 = sized by tgs_plan */
+    int64_t spin_limit;    /* iterations of any bounded device wait (default 1 << 22) */
+} tgs_config;
+
+typedef struct {
+    int64_t n;                   /* number of Gaussians */
+    int32_t sh_degree_max;       /* 0..3; rest bands above it are not read */
+    int32_t reserved;
+    const float *means;          /* [n,3] */
+    const float *log_scales;     /* [n,3] */
+    const float *quats;          /* [n,4] */
+    const float *opacity_logits; /* [n] */
+    const float *sh_dc;          /* [n,3] */
+    const float *sh_rest;        /* [n,15,3]; may be NULL when sh_degree_max == 0 */
+    const uint8_t *sh_degree;    /* [n] or NULL */
+    const float *mask_logits;    /* [n] or NULL: no volume mask */
+    const float *sh_mask_logits; /* [n,3] or NULL: no band masks */
+} tgs_gaussians;
+
+typedef struct {
+    float viewmat[16];  /* world -> camera, row-major */
+    float campos[3];    /* camera centre in world space */
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float low_pass;     /* per-view s; <= 0 selects tgs_config.low_pass */
+} tgs_camera;           /* host memory */
+
+typedef struct {
+    float *image;        /* [3,H,W] */
+    float *T_final;      /* [H,W] or NULL */
+    int32_t *last;       /* [H,W] or NULL */
+    int32_t *n_examined; /* [H,W] or NULL: list entries each pixel looked at */
+    int32_t *radii;      /* [n] or NULL */
+} tgs_view_out;
+
+typedef struct {
+    float *means, *log_scales, *quats, *opacity_logits, *sh_dc, *sh_rest, *mask_logits,
+        *sh_mask_logits; /* same shapes as the inputs; NULL = not wanted */
+} tgs_grads;
+
+typedef struct {
+    float *grad_norm_accum; /* [n] += |dL/d mean2d|_2 (pixels) per view where visible, or NULL */
+    int32_t *vis_count;     /* [n] += 1 per view where visible, or NULL */
+    int32_t *max_radius;    /* [n] = max(max_radius, radius), or NULL */
+} tgs_stats;
+
+/* --- context ------------------------------------------------------------------------ */
+
+/* Fills *cfg with the defaults named in tgs_config. */
+void tgs_default_config(tgs_config *cfg);
+/* Creates a context on the current CUDA device. cfg may be NULL (defaults). */
+tgs_status tgs_create(tgs_ctx **out, const tgs_config *cfg);
+void tgs_destroy(tgs_ctx *ctx);
+tgs_status tgs_get_config(const tgs_ctx *ctx, tgs_config *cfg);
+/* Replaces the settings (tile, ppt, thresholds ...). Invalidates captured graphs. */
+tgs_status tgs_set_config(tgs_ctx *ctx, const tgs_config *cfg);
+const char *tgs_status_string(tgs_status s);
+/* Synchronises the stream, returns and clears the device status word. */
+tgs_status tgs_poll_status(tgs_ctx *ctx, tgs_stream stream);
+
+/* --- the plain single-view path (3DGS-like: one host read-back of the key count) ---- */
+
+/* Renders each view in turn (preprocess, keys, sort, blend). The binning of the last view
+   rendered stays in the context so that an immediately following tgs_backward of that view
+   reuses it; other views are re-binned in tgs_backward (per-view checkpointing).
+   Synchronises the stream once per view to size the key buffers. */
+tgs_status tgs_forward(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                       const tgs_view_out *outs, uint32_t flags, tgs_stream stream);
+/* Backward of tgs_forward given dL/d image per view (device [3,H,W] each) and each view's
+   saved T_final and last (outs[v].T_final, outs[v].last). Writes (or with TGS_ACCUMULATE
+   adds) parameter gradients summed over the V views, and adds statistics. */
+tgs_status tgs_backward(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams,
+                        int32_t V, const tgs_view_out *outs, const float *const *dL_dimages,
+                        const tgs_grads *grads, const tgs_stats *stats, uint32_t flags,
+                        tgs_stream stream);
+/* L1 loss of one image: *loss += scale * sum |img - target|, grad = scale * sign(img -
+   target) (sign(0) = 0). count = 3 H W. loss_accum is a device float. */
+tgs_status tgs_l1_loss(const float *image, const float *target, int64_t count, float scale,
+                       float *loss_accum, float *grad, tgs_stream stream);
+
+/* --- the batched path ---------------------------------------------------------------- */
+
+/* Sizes the key capacity for these views: runs preprocess and the key count once, waits,
+   and sets capacity = ceil(headroom * K). */
+tgs_status tgs_plan(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                    double headroom, int64_t *keys_out);
+/* One training step over V views of any sizes: preprocess of all views, one key sort, a
+   persistent fused forward + L1 loss + backward over (view, tile) work items heaviest first,
+   and the preprocess backward. loss_out (device float) = mean over views of mean |C - t|.
+   images (optional, host array of V device pointers) receives the rendered views.
+   Never synchronises; with TGS_USE_GRAPH the whole step is captured once into a CUDA graph
+   and replayed while g, cams, targets, images, grads, stats and loss_out are unchanged.
+   A key-capacity overflow sets TGS_ERR_CAPACITY in the device status word. */
+tgs_status tgs_train_step_batched(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams,
+                                  int32_t V, const float *const *targets, float *const *images,
+                                  const tgs_grads *grads, const tgs_stats *stats,
+                                  float *loss_out, uint32_t flags, tgs_stream stream);
+/* Times the batched step for tile in {8, 16, 32} x ppt in {1, 2, 4} and keeps the fastest in
+   the context's config. cache_path (may be NULL) is a JSON file read first and written after. */
+tgs_status tgs_autotune(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                        const float *const *targets, const char *cache_path,
+                        tgs_stream stream);
+
+/* --- the individual steps (caller-owned buffers) --------------------------------------- */
+
+/* (a) Writes splat records [V*n,12] and radii [V*n] (0 = culled). */
+tgs_status tgs_preprocess(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams,
+                          int32_t V, float *splats, int32_t *radii, tgs_stream stream);
+/* (b) From splat records and radii: sorted Gaussian record indices (v*n + g) in tile order,
+   the sorted 64-bit keys ((global tile << 32) | float32 bits of depth, or NULL) and per-tile
+   [start, end) ranges [tiles,2] (uint32). Global tile ids count the views' tiles in order,
+   row-major within a view. Synchronises once to read the key count K into *K_out; returns
+   TGS_ERR_CAPACITY without sorting when K > capacity. */
+tgs_status tgs_bin(tgs_ctx *ctx, const float *splats, const int32_t *radii, int64_t n,
+                   const tgs_camera *cams, int32_t V, uint32_t *sorted_ids, uint64_t *sorted_keys,
+                   uint32_t *ranges, int64_t capacity, int64_t *K_out, tgs_stream stream);
+/* (c) Forward blend of V views from the binned lists. */
+tgs_status tgs_blend_forward(tgs_ctx *ctx, const float *splats, const uint32_t *sorted_ids,
+                             const uint32_t *ranges, const tgs_camera *cams, int32_t V,
+                             const tgs_view_out *outs, tgs_stream stream);
+/* (d) Backward blend: adds into splat gradient records [V*n,12] (zero them first). */
+tgs_status tgs_blend_backward(tgs_ctx *ctx, const float *splats, const uint32_t *sorted_ids,
+                              const uint32_t *ranges, const tgs_camera *cams, int32_t V,
+                              const tgs_view_out *outs, const float *const *dL_dimages,
+                              float *splat_grads, tgs_stream stream);
+/* (e) Backward preprocess: parameter gradients (overwritten, or added with TGS_ACCUMULATE)
+   summed over the V views, and statistics (always added). */
+tgs_status tgs_preprocess_backward(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams,
+                                   int32_t V, const float *splat_grads, const int32_t *radii,
+                                   const tgs_grads *grads, const tgs_stats *stats,
+                                   uint32_t flags, tgs_stream stream);
+
+/* --- measurement ------------------------------------------------------------------------ */
+
+/* With profiling on, the batched step records a CUDA event between its stages (also inside
+   a captured graph). tgs_stage_times synchronises on the last event and writes the duration
+   in milliseconds of each stage of the most recent step; *n_out = number of stages. */
+#define TGS_MAX_STAGES 8
+tgs_status tgs_set_profiling(tgs_ctx *ctx, int32_t on);
+tgs_status tgs_stage_times(tgs_ctx *ctx, float *ms, int32_t max, int32_t *n_out);
+const char *tgs_stage_name(tgs_ctx *ctx, int32_t i);
+/* Kernels the most recent batched step launched (for a graph replay: the kernel nodes of the
+   graph). */
+int64_t tgs_kernels_per_step(const tgs_ctx *ctx);
+
+/* Number of tiles of a view at the context's tile size, and bytes of scratch the batched
+   path needs for n Gaussians and these views at the current key capacity. */
+int64_t tgs_num_tiles(const tgs_ctx *ctx, const tgs_camera *cams, int32_t V);
+size_t tgs_workspace_bytes(const tgs_ctx *ctx, int64_t n, const tgs_camera *cams, int32_t V);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TGS_H */

@@ -548,6 +548,7 @@ typedef struct {
     const uint32_t *order;   /* brute: visible Gaussians sorted by (depth bits, id) */
     int64_t n_order;
     int use_depth_margin;
+    const uint8_t *tile_mask; /* NULL, or 1 for every tile to process */
     /* forward outputs */
     double *image, *T_final, *margin;
     int32_t *last, *n_contrib, *n_examined;
@@ -686,6 +687,7 @@ static void *blend_worker(void *p) {
     if (J->dL_dimg) frags = (frag_t *)malloc(sizeof(frag_t) * (size_t)(maxlen > 0 ? maxlen : 1));
     double *acc = J->acc ? J->acc + (int64_t)a->tid * J->n * 9 : NULL;
     for (int t = a->tid; t < ntiles; t += J->nthreads) {
+        if (J->tile_mask && !J->tile_mask[t]) continue;
         int tx = t % J->gx, ty = t / J->gx;
         const uint32_t *list;
         int64_t len;
@@ -789,10 +791,12 @@ static int run_blend(blend_job *J) {
 /* Forward blend of one view. brute = 1 scans all Gaussians per pixel in (depth, id) order
    instead of the tile lists. Any output pointer may be NULL. */
 int orc_blend(int64_t n, const orc_splats *S, int W, int H, int tile, const double *bg,
-              int brute, int nthreads, int use_depth_margin, double *image, double *T_final,
-              int32_t *last, int32_t *n_contrib, int32_t *n_examined, double *margin) {
+              int brute, int nthreads, int use_depth_margin, const uint8_t *tile_mask,
+              double *image, double *T_final, int32_t *last, int32_t *n_contrib,
+              int32_t *n_examined, double *margin) {
     blend_job J;
     memset(&J, 0, sizeof J);
+    J.tile_mask = tile_mask;
     J.S = S;
     J.n = n;
     J.W = W;
@@ -814,9 +818,10 @@ int orc_blend(int64_t n, const orc_splats *S, int W, int H, int tile, const doub
 /* Backward of the blend of one view: writes dL/d(mean2d[2], conic[3], opacity, rgb[3]) per
    Gaussian into g9 [n,9] (overwritten). */
 int orc_blend_backward(int64_t n, const orc_splats *S, int W, int H, int tile, const double *bg,
-                       const double *dL_dimg, int nthreads, double *g9) {
+                       const double *dL_dimg, int nthreads, const uint8_t *tile_mask, double *g9) {
     blend_job J;
     memset(&J, 0, sizeof J);
+    J.tile_mask = tile_mask;
     J.S = S;
     J.n = n;
     J.W = W;

@@ -1,0 +1,898 @@
+// libtgs host runtime: context, scratch arena, the plain and batched paths, CUDA-graph
+// capture of the batched step, and the autotuner. Every entry point is extern "C" and
+// returns a tgs_status; no exception crosses the ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tgs_internal.cuh"
+
+using namespace tgs;
+
+namespace tgs {
+thread_local int64_t g_launches = 0;
+}
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct tgs_ctx {
+    tgs_config cfg;
+    int device = 0;
+    // scratch arena
+    Buf splats, radii, tt, dbits, pos, ck0, cv0, ck1, cv1, offsets, tk0, tv0, tk1, tv1, ranges,
+        hist, partials, sgrads, counts, status, pixstate, dimg, images, keys64;
+    uint32_t *h_counts = nullptr;   // pinned host copy of (visible, K)
+    // binning kept from the last plain forward
+    bool state_valid = false;
+    tgs_gaussians state_g{};
+    tgs_camera state_cam{};
+    int state_tile = 0;
+    uint32_t *state_ids = nullptr;  // where the sorted ids of that binning live
+    uint32_t *sorted_tk = nullptr;  // sorted tile keys of the last binning
+    // captured batched step
+    cudaGraphExec_t graph = nullptr;
+    std::vector<unsigned char> graph_key;
+    cudaStream_t side = nullptr;
+    // measurement
+    bool profiling = false;
+    cudaEvent_t stage_ev[TGS_MAX_STAGES + 1] = {};
+    const char *stage_names[TGS_MAX_STAGES] = {};
+    int n_stages = 0;
+    int64_t kernels_per_step = 0;
+};
+
+namespace {
+
+tgs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TGS_OK : TGS_ERR_CUDA; }
+
+#define TGS_CHECK(x)                                   \
+    do {                                               \
+        cudaError_t e_ = (x);                          \
+        if (e_ != cudaSuccess) return TGS_ERR_CUDA;    \
+    } while (0)
+
+#define TGS_TRY(x)                     \
+    do {                               \
+        tgs_status s_ = (x);           \
+        if (s_ != TGS_OK) return s_;   \
+    } while (0)
+
+bool capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return false;
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Grows a scratch buffer; never inside stream capture.
+tgs_status ensure(Buf &b, size_t bytes, cudaStream_t st) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return TGS_OK;
+    if (capturing(st)) return TGS_ERR_CAPACITY;
+    size_t nb = bytes + bytes / 4;
+    if (b.p) {
+        cudaStreamSynchronize(st);
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (cudaMalloc(&b.p, nb) != cudaSuccess) {
+        cudaGetLastError();
+        return TGS_ERR_OOM;
+    }
+    b.bytes = nb;
+    return TGS_OK;
+}
+
+template <class T>
+T *as(Buf &b) { return reinterpret_cast<T *>(b.p); }
+
+bool valid_cfg(const tgs_config &c) {
+    return blend_supported(c.tile, c.ppt) && (c.support == TGS_SUPPORT_BOX3 || c.support == TGS_SUPPORT_ALPHA) &&
+           c.low_pass >= 0.f && c.eps_mask > 0.f && c.eps_mask < 1.f && c.eps_sh > 0.f && c.eps_sh < 1.f &&
+           c.near_plane > 0.f && c.key_capacity >= 0;
+}
+
+tgs_status make_batch(const tgs_config &cfg, const tgs_camera *cams, int V, CamBatch &cb) {
+    if (!cams || V <= 0 || V > kMaxViews) return TGS_ERR_INVALID_ARG;
+    memset(&cb, 0, sizeof cb);
+    cb.V = V;
+    cb.tile = cfg.tile;
+    int off = 0, poff = 0;
+    for (int v = 0; v < V; v++) {
+        const tgs_camera &c = cams[v];
+        if (c.width <= 0 || c.height <= 0 || c.width > 65535 || c.height > 65535 || !(c.fx > 0.f) ||
+            !(c.fy > 0.f))
+            return TGS_ERR_INVALID_ARG;
+        DevCam &d = cb.c[v];
+        for (int r = 0; r < 3; r++) {
+            for (int k = 0; k < 3; k++) d.R[3 * r + k] = c.viewmat[4 * r + k];
+            d.t[r] = c.viewmat[4 * r + 3];
+            d.campos[r] = c.campos[r];
+        }
+        d.fx = c.fx;
+        d.fy = c.fy;
+        d.cx = c.cx;
+        d.cy = c.cy;
+        d.limx = (float)(1.3 * (0.5 * c.width / (double)c.fx));
+        d.limy = (float)(1.3 * (0.5 * c.height / (double)c.fy));
+        d.s = c.low_pass > 0.f ? c.low_pass : cfg.low_pass;
+        d.W = c.width;
+        d.H = c.height;
+        d.gx = (c.width + cfg.tile - 1) / cfg.tile;
+        d.gy = (c.height + cfg.tile - 1) / cfg.tile;
+        d.tile_offset = off;
+        d.pix_offset = poff;
+        off += d.gx * d.gy;
+        poff += c.width * c.height;
+    }
+    cb.total_tiles = off;
+    return TGS_OK;
+}
+
+float logit_threshold(float eps) { return (float)std::log((double)eps / (1.0 - (double)eps)); }
+
+tgs_status make_gauss(const tgs_config &cfg, const tgs_gaussians *g, GaussPtrs &gp) {
+    if (!g || g->n < 0) return TGS_ERR_INVALID_ARG;
+    // an empty scene may come with null pointers
+    if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh_dc))
+        return TGS_ERR_INVALID_ARG;
+    if (g->sh_degree_max < 0 || g->sh_degree_max > 3) return TGS_ERR_INVALID_ARG;
+    if (g->n > 0 && g->sh_degree_max > 0 && !g->sh_rest) return TGS_ERR_INVALID_ARG;
+    if ((int64_t)g->n * kMaxViews >= (int64_t)1 << 32) return TGS_ERR_INVALID_ARG;
+    gp.means = g->means;
+    gp.log_scales = g->log_scales;
+    gp.quats = g->quats;
+    gp.opac = g->opacity_logits;
+    gp.sh_dc = g->sh_dc;
+    gp.sh_rest = g->sh_rest;
+    gp.sh_degree = g->sh_degree;
+    gp.mask = g->mask_logits;
+    gp.shmask = g->sh_mask_logits;
+    gp.n = g->n;
+    gp.deg_max = g->sh_degree_max;
+    gp.tau_m = logit_threshold(cfg.eps_mask);
+    gp.tau_sh = logit_threshold(cfg.eps_sh);
+    gp.support = cfg.support;
+    gp.near_z = cfg.near_plane;
+    return TGS_OK;
+}
+
+int bits_for(int64_t x) {
+    int b = 0;
+    while (((int64_t)1 << b) < x) b++;
+    return b < 1 ? 1 : b;
+}
+
+// Buffers for V views of n Gaussians (per-record arrays).
+tgs_status ensure_records(tgs_ctx *c, int64_t nt, cudaStream_t st) {
+    TGS_TRY(ensure(c->splats, sizeof(float) * 12 * (size_t)nt, st));
+    TGS_TRY(ensure(c->sgrads, sizeof(float) * 12 * (size_t)nt, st));
+    TGS_TRY(ensure(c->radii, sizeof(int32_t) * (size_t)nt, st));
+    TGS_TRY(ensure(c->tt, sizeof(uint32_t) * (size_t)nt, st));
+    TGS_TRY(ensure(c->dbits, sizeof(uint32_t) * (size_t)nt, st));
+    TGS_TRY(ensure(c->pos, sizeof(uint32_t) * (size_t)nt, st));
+    TGS_TRY(ensure(c->ck0, sizeof(uint32_t) * (size_t)nt, st));
+    TGS_TRY(ensure(c->cv0, sizeof(uint32_t) * (size_t)nt, st));
+    TGS_TRY(ensure(c->ck1, sizeof(uint32_t) * (size_t)nt, st));
+    TGS_TRY(ensure(c->cv1, sizeof(uint32_t) * (size_t)nt, st));
+    TGS_TRY(ensure(c->offsets, sizeof(uint32_t) * (size_t)nt, st));
+    TGS_TRY(ensure(c->counts, sizeof(uint32_t) * 4, st));
+    size_t h = std::max(radix_hist_needed(nt), (size_t)16);
+    TGS_TRY(ensure(c->hist, sizeof(uint32_t) * h, st));
+    size_t p = std::max(scan_partials_needed(nt), scan_partials_needed((int64_t)h));
+    TGS_TRY(ensure(c->partials, sizeof(uint32_t) * p, st));
+    return TGS_OK;
+}
+
+tgs_status ensure_keys(tgs_ctx *c, int64_t cap, int total_tiles, cudaStream_t st) {
+    TGS_TRY(ensure(c->tk0, sizeof(uint32_t) * (size_t)cap, st));
+    TGS_TRY(ensure(c->tv0, sizeof(uint32_t) * (size_t)cap, st));
+    TGS_TRY(ensure(c->tk1, sizeof(uint32_t) * (size_t)cap, st));
+    TGS_TRY(ensure(c->tv1, sizeof(uint32_t) * (size_t)cap, st));
+    TGS_TRY(ensure(c->ranges, sizeof(uint2) * (size_t)std::max(total_tiles, 1), st));
+    size_t h = radix_hist_needed(cap);
+    TGS_TRY(ensure(c->hist, sizeof(uint32_t) * std::max(h, c->hist.bytes / sizeof(uint32_t)), st));
+    size_t p = std::max(scan_partials_needed(cap), scan_partials_needed((int64_t)h));
+    TGS_TRY(ensure(c->partials, sizeof(uint32_t) * std::max(p, c->partials.bytes / sizeof(uint32_t)), st));
+    return TGS_OK;
+}
+
+// Visibility compaction, depth sort and the key-count scan. Leaves the depth-sorted record
+// ids in *sorted and the key count in counts[1].
+void bin_front(tgs_ctx *c, int64_t nt, uint32_t **sorted, cudaStream_t st) {
+    uint32_t *cnt = as<uint32_t>(c->counts);
+    scan_flags(as<uint32_t>(c->tt), nt, as<uint32_t>(c->pos), cnt + 0, as<uint32_t>(c->partials), st);
+    compact_visible(as<uint32_t>(c->tt), as<uint32_t>(c->dbits), as<uint32_t>(c->pos), nt,
+                    as<uint32_t>(c->ck0), as<uint32_t>(c->cv0), st);
+    uint32_t *k = as<uint32_t>(c->ck0), *v = as<uint32_t>(c->cv0);
+    radix_sort_pairs(k, v, as<uint32_t>(c->ck1), as<uint32_t>(c->cv1), cnt + 0, nt, 0, 32,
+                     as<uint32_t>(c->hist), as<uint32_t>(c->partials), st);
+    gather_tiles_scan(v, as<uint32_t>(c->tt), cnt + 0, nt, as<uint32_t>(c->offsets), cnt + 1,
+                      as<uint32_t>(c->partials), nullptr, st);
+    *sorted = v;
+}
+
+// Key emission, tile sort and ranges for a key grid of cap. Returns the sorted record ids.
+uint32_t *bin_back(tgs_ctx *c, int64_t nt, int64_t n, const uint32_t *sorted, const CamBatch &cb,
+                   int64_t cap, cudaStream_t st) {
+    uint32_t *cnt = as<uint32_t>(c->counts);
+    emit_keys(sorted, as<uint32_t>(c->offsets), cnt + 0, nt, as<float4>(c->splats), n, cb,
+              as<uint32_t>(c->tk0), as<uint32_t>(c->tv0), cnt + 1, cap, as<uint32_t>(c->status), st);
+    uint32_t *k = as<uint32_t>(c->tk0), *v = as<uint32_t>(c->tv0);
+    radix_sort_pairs(k, v, as<uint32_t>(c->tk1), as<uint32_t>(c->tv1), cnt + 1, cap, 0,
+                     bits_for(cb.total_tiles), as<uint32_t>(c->hist), as<uint32_t>(c->partials), st);
+    find_ranges(k, cnt + 1, cap, as<uint2>(c->ranges), cb.total_tiles, st);
+    c->sorted_tk = k;  // tgs_bin exports the 64-bit keys from these
+    return v;
+}
+
+// Synchronous read of (visible, K) after bin_front.
+tgs_status read_counts(tgs_ctx *c, cudaStream_t st, int64_t *vis, int64_t *K) {
+    TGS_CHECK(cudaMemcpyAsync(c->h_counts, c->counts.p, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, st));
+    TGS_CHECK(cudaStreamSynchronize(st));
+    if (vis) *vis = c->h_counts[0];
+    if (K) *K = c->h_counts[1];
+    return TGS_OK;
+}
+
+// Full plain binning of V views whose splat records are already in the arena.
+tgs_status bin_plain(tgs_ctx *c, int64_t n, const CamBatch &cb, cudaStream_t st, int64_t *K_out,
+                     int64_t cap_limit, uint32_t **ids) {
+    const int64_t nt = n * cb.V;
+    uint32_t *sorted = nullptr;
+    bin_front(c, nt, &sorted, st);
+    int64_t K = 0;
+    TGS_TRY(read_counts(c, st, nullptr, &K));
+    if (K_out) *K_out = K;
+    if (cap_limit >= 0 && K > cap_limit) return TGS_ERR_CAPACITY;
+    TGS_TRY(ensure_keys(c, std::max<int64_t>(K, 1), cb.total_tiles, st));
+    *ids = bin_back(c, nt, n, sorted, cb, std::max<int64_t>(K, 1), st);
+    if (K == 0) {
+        cudaMemsetAsync(c->ranges.p, 0, sizeof(uint2) * (size_t)std::max(cb.total_tiles, 1), st);
+    }
+    return TGS_OK;
+}
+
+PixPtrs pix_for(const tgs_view_out *outs, int V, const float *const *dL) {
+    PixPtrs p;
+    memset(&p, 0, sizeof p);
+    for (int v = 0; v < V; v++) {
+        p.image[v] = outs[v].image;
+        p.T_final[v] = outs[v].T_final;
+        p.last[v] = outs[v].last;
+        p.n_exam[v] = outs[v].n_examined;
+        p.dL[v] = dL ? dL[v] : nullptr;
+    }
+    return p;
+}
+
+GradPtrs grad_ptrs(const tgs_grads *g, const tgs_stats *s, int acc) {
+    GradPtrs o;
+    memset(&o, 0, sizeof o);
+    if (g) {
+        o.means = g->means;
+        o.log_scales = g->log_scales;
+        o.quats = g->quats;
+        o.opac = g->opacity_logits;
+        o.sh_dc = g->sh_dc;
+        o.sh_rest = g->sh_rest;
+        o.mask = g->mask_logits;
+        o.shmask = g->sh_mask_logits;
+    }
+    if (s) {
+        o.stat_accum = s->grad_norm_accum;
+        o.stat_count = s->vis_count;
+        o.stat_maxr = s->max_radius;
+    }
+    o.accumulate = acc;
+    return o;
+}
+
+bool same_cam(const tgs_camera &a, const tgs_camera &b) { return memcmp(&a, &b, sizeof a) == 0; }
+bool same_g(const tgs_gaussians &a, const tgs_gaussians &b) { return memcmp(&a, &b, sizeof a) == 0; }
+
+tgs_status last_error() { return cuda_status(cudaGetLastError()); }
+
+// Records the boundary event before stage i (profiling only).
+void mark(tgs_ctx *c, int i, const char *name, cudaStream_t st) {
+    if (!c->profiling || i > TGS_MAX_STAGES) return;
+    // inside stream capture only an external record becomes a node of the graph
+    if (capturing(st))
+        cudaEventRecordWithFlags(c->stage_ev[i], st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(c->stage_ev[i], st);
+    if (i < TGS_MAX_STAGES) c->stage_names[i] = name;
+    c->n_stages = i;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tgs_default_config(tgs_config *cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->tile = 16;
+    cfg->ppt = 1;
+    cfg->support = TGS_SUPPORT_BOX3;
+    cfg->low_pass = 0.3f;
+    cfg->eps_mask = 0.05f;
+    cfg->eps_sh = 0.1f;
+    cfg->near_plane = 0.2f;
+    cfg->key_capacity = 0;
+    cfg->spin_limit = (int64_t)1 << 22;
+}
+
+const char *tgs_status_string(tgs_status s) {
+    switch (s) {
+        case TGS_OK: return "ok";
+        case TGS_ERR_INVALID_ARG: return "invalid argument";
+        case TGS_ERR_CUDA: return "CUDA runtime error";
+        case TGS_ERR_CAPACITY: return "key capacity exceeded";
+        case TGS_ERR_TIMEOUT: return "bounded device wait ran out";
+        case TGS_ERR_OOM: return "out of device memory";
+        case TGS_ERR_NOT_SUPPORTED: return "not supported";
+        default: return "unknown status";
+    }
+}
+
+tgs_status tgs_create(tgs_ctx **out, const tgs_config *cfg) {
+    if (!out) return TGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    tgs_config c;
+    if (cfg) c = *cfg; else tgs_default_config(&c);
+    if (!valid_cfg(c)) return TGS_ERR_INVALID_ARG;
+    tgs_ctx *x = new (std::nothrow) tgs_ctx();
+    if (!x) return TGS_ERR_OOM;
+    x->cfg = c;
+    if (cudaGetDevice(&x->device) != cudaSuccess ||
+        cudaMallocHost((void **)&x->h_counts, sizeof(uint32_t) * 4) != cudaSuccess) {
+        cudaGetLastError();
+        delete x;
+        return TGS_ERR_CUDA;
+    }
+    if (ensure(x->status, sizeof(uint32_t) * 4, nullptr) != TGS_OK ||
+        ensure(x->counts, sizeof(uint32_t) * 4, nullptr) != TGS_OK) {
+        tgs_destroy(x);
+        return TGS_ERR_OOM;
+    }
+    cudaMemset(x->status.p, 0, x->status.bytes);
+    cudaMemset(x->counts.p, 0, x->counts.bytes);
+    *out = x;
+    return TGS_OK;
+}
+
+void tgs_destroy(tgs_ctx *c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    Buf *bufs[] = {&c->splats, &c->radii, &c->tt, &c->dbits, &c->pos, &c->ck0, &c->cv0, &c->ck1,
+                   &c->cv1, &c->offsets, &c->tk0, &c->tv0, &c->tk1, &c->tv1, &c->ranges, &c->hist,
+                   &c->partials, &c->sgrads, &c->counts, &c->status, &c->pixstate, &c->dimg,
+                   &c->images, &c->keys64};
+    for (Buf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    if (c->h_counts) cudaFreeHost(c->h_counts);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->side) cudaStreamDestroy(c->side);
+    for (cudaEvent_t e : c->stage_ev)
+        if (e) cudaEventDestroy(e);
+    delete c;
+}
+
+tgs_status tgs_get_config(const tgs_ctx *c, tgs_config *cfg) {
+    if (!c || !cfg) return TGS_ERR_INVALID_ARG;
+    *cfg = c->cfg;
+    return TGS_OK;
+}
+
+tgs_status tgs_set_config(tgs_ctx *c, const tgs_config *cfg) {
+    if (!c || !cfg || !valid_cfg(*cfg)) return TGS_ERR_INVALID_ARG;
+    c->cfg = *cfg;
+    c->state_valid = false;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        c->graph_key.clear();
+    }
+    return TGS_OK;
+}
+
+tgs_status tgs_poll_status(tgs_ctx *c, tgs_stream stream) {
+    if (!c) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t h = 0;
+    TGS_CHECK(cudaMemcpyAsync(c->h_counts + 2, c->status.p, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    TGS_CHECK(cudaStreamSynchronize(st));
+    h = c->h_counts[2];
+    TGS_CHECK(cudaMemsetAsync(c->status.p, 0, sizeof(uint32_t), st));
+    TGS_CHECK(cudaStreamSynchronize(st));
+    if (h & kStatusTimeout) return TGS_ERR_TIMEOUT;
+    if (h & kStatusCapacity) return TGS_ERR_CAPACITY;
+    return TGS_OK;
+}
+
+int64_t tgs_num_tiles(const tgs_ctx *c, const tgs_camera *cams, int32_t V) {
+    if (!c) return -1;
+    CamBatch cb;
+    if (make_batch(c->cfg, cams, V, cb) != TGS_OK) return -1;
+    return cb.total_tiles;
+}
+
+size_t tgs_workspace_bytes(const tgs_ctx *c, int64_t n, const tgs_camera *cams, int32_t V) {
+    if (!c) return 0;
+    CamBatch cb;
+    if (make_batch(c->cfg, cams, V, cb) != TGS_OK) return 0;
+    const size_t nt = (size_t)n * V;
+    size_t pix = 0;
+    for (int v = 0; v < V; v++) pix += (size_t)cams[v].width * cams[v].height;
+    const size_t cap = (size_t)c->cfg.key_capacity;
+    return nt * (12 * 4 * 2 + 4 * 9) + cap * 16 + (size_t)cb.total_tiles * 8 +
+           radix_hist_needed((int64_t)std::max(nt, cap)) * 4 + pix * 4 * (3 + 2 + 3 + 3);
+}
+
+// ---- individual steps -------------------------------------------------------------------
+
+tgs_status tgs_preprocess(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                          float *splats, int32_t *radii, tgs_stream stream) {
+    if (!c || !splats || !radii) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CamBatch cb;
+    GaussPtrs gp;
+    TGS_TRY(make_batch(c->cfg, cams, V, cb));
+    TGS_TRY(make_gauss(c->cfg, g, gp));
+    const int64_t nt = g->n * V;
+    TGS_TRY(ensure(c->tt, sizeof(uint32_t) * (size_t)nt, st));
+    TGS_TRY(ensure(c->dbits, sizeof(uint32_t) * (size_t)nt, st));
+    launch_preprocess(gp, cb, reinterpret_cast<float4 *>(splats), radii, as<uint32_t>(c->tt),
+                      as<uint32_t>(c->dbits), nullptr, st);
+    return last_error();
+}
+
+tgs_status tgs_bin(tgs_ctx *c, const float *splats, const int32_t *radii, int64_t n,
+                   const tgs_camera *cams, int32_t V, uint32_t *sorted_ids, uint64_t *sorted_keys,
+                   uint32_t *ranges, int64_t capacity, int64_t *K_out, tgs_stream stream) {
+    if (!c || !splats || !radii || n < 0 || !sorted_ids || !ranges || capacity < 0) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CamBatch cb;
+    TGS_TRY(make_batch(c->cfg, cams, V, cb));
+    const int64_t nt = n * V;
+    TGS_TRY(ensure_records(c, nt, st));
+    // records come from the caller: copy them in and derive tiles touched and depth bits
+    TGS_CHECK(cudaMemcpyAsync(c->splats.p, splats, sizeof(float) * 12 * (size_t)nt, cudaMemcpyDeviceToDevice, st));
+    TGS_CHECK(cudaMemcpyAsync(c->radii.p, radii, sizeof(int32_t) * (size_t)nt, cudaMemcpyDeviceToDevice, st));
+    derive_touched(as<float4>(c->splats), as<int32_t>(c->radii), nt, c->cfg.tile, as<uint32_t>(c->tt),
+                   as<uint32_t>(c->dbits), st);
+    int64_t K = 0;
+    uint32_t *ids = nullptr;
+    tgs_status s = bin_plain(c, n, cb, st, &K, capacity, &ids);
+    if (K_out) *K_out = K;
+    if (s != TGS_OK) return s;
+    c->state_valid = false;
+    if (K > 0) {
+        TGS_CHECK(cudaMemcpyAsync(sorted_ids, ids, sizeof(uint32_t) * (size_t)K, cudaMemcpyDeviceToDevice, st));
+        if (sorted_keys)
+            make_full_keys(c->sorted_tk, ids, as<float4>(c->splats), as<uint32_t>(c->counts) + 1, K,
+                           sorted_keys, st);
+    }
+    TGS_CHECK(cudaMemcpyAsync(ranges, c->ranges.p, sizeof(uint2) * (size_t)cb.total_tiles, cudaMemcpyDeviceToDevice, st));
+    return last_error();
+}
+
+tgs_status tgs_blend_forward(tgs_ctx *c, const float *splats, const uint32_t *sorted_ids,
+                             const uint32_t *ranges, const tgs_camera *cams, int32_t V,
+                             const tgs_view_out *outs, tgs_stream stream) {
+    if (!c || !splats || !ranges || !outs) return TGS_ERR_INVALID_ARG;
+    CamBatch cb;
+    TGS_TRY(make_batch(c->cfg, cams, V, cb));
+    for (int v = 0; v < V; v++)
+        if (!outs[v].image) return TGS_ERR_INVALID_ARG;
+    PixPtrs px = pix_for(outs, V, nullptr);
+    launch_blend_forward(c->cfg.tile, c->cfg.ppt, reinterpret_cast<const float4 *>(splats), sorted_ids,
+                         reinterpret_cast<const uint2 *>(ranges), cb, px, c->cfg.bg, (cudaStream_t)stream);
+    return last_error();
+}
+
+tgs_status tgs_blend_backward(tgs_ctx *c, const float *splats, const uint32_t *sorted_ids,
+                              const uint32_t *ranges, const tgs_camera *cams, int32_t V,
+                              const tgs_view_out *outs, const float *const *dL_dimages,
+                              float *splat_grads, tgs_stream stream) {
+    if (!c || !splats || !ranges || !outs || !dL_dimages || !splat_grads) return TGS_ERR_INVALID_ARG;
+    CamBatch cb;
+    TGS_TRY(make_batch(c->cfg, cams, V, cb));
+    for (int v = 0; v < V; v++)
+        if (!outs[v].T_final || !outs[v].last || !dL_dimages[v]) return TGS_ERR_INVALID_ARG;
+    PixPtrs px = pix_for(outs, V, dL_dimages);
+    launch_blend_backward(c->cfg.tile, c->cfg.ppt, reinterpret_cast<const float4 *>(splats), sorted_ids,
+                          reinterpret_cast<const uint2 *>(ranges), cb, px, c->cfg.bg, splat_grads,
+                          (cudaStream_t)stream);
+    return last_error();
+}
+
+tgs_status tgs_preprocess_backward(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams,
+                                   int32_t V, const float *splat_grads, const int32_t *radii,
+                                   const tgs_grads *grads, const tgs_stats *stats, uint32_t flags,
+                                   tgs_stream stream) {
+    if (!c || !splat_grads || !radii) return TGS_ERR_INVALID_ARG;
+    CamBatch cb;
+    GaussPtrs gp;
+    TGS_TRY(make_batch(c->cfg, cams, V, cb));
+    TGS_TRY(make_gauss(c->cfg, g, gp));
+    GradPtrs o = grad_ptrs(grads, stats, (flags & TGS_ACCUMULATE) ? 1 : 0);
+    launch_preprocess_backward(gp, cb, reinterpret_cast<const float4 *>(splat_grads), radii, o,
+                               (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, (cudaStream_t)stream);
+    return last_error();
+}
+
+tgs_status tgs_l1_loss(const float *image, const float *target, int64_t count, float scale,
+                       float *loss_accum, float *grad, tgs_stream stream) {
+    if (!image || !target || count < 0) return TGS_ERR_INVALID_ARG;
+    launch_l1(image, target, count, scale, loss_accum, grad, (cudaStream_t)stream);
+    return last_error();
+}
+
+// ---- plain path ---------------------------------------------------------------------------
+
+static tgs_status plain_bin_view(tgs_ctx *c, const tgs_gaussians *g, const GaussPtrs &gp,
+                                 const tgs_camera *cam, CamBatch &cb, cudaStream_t st, uint32_t **ids) {
+    TGS_TRY(make_batch(c->cfg, cam, 1, cb));
+    TGS_TRY(ensure_records(c, g->n, st));
+    launch_preprocess(gp, cb, as<float4>(c->splats), as<int32_t>(c->radii), as<uint32_t>(c->tt),
+                      as<uint32_t>(c->dbits), nullptr, st);
+    TGS_TRY(bin_plain(c, g->n, cb, st, nullptr, -1, ids));
+    c->state_valid = true;
+    c->state_g = *g;
+    c->state_cam = *cam;
+    c->state_tile = c->cfg.tile;
+    c->state_ids = *ids;
+    return TGS_OK;
+}
+
+tgs_status tgs_forward(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                       const tgs_view_out *outs, uint32_t flags, tgs_stream stream) {
+    (void)flags;
+    if (!c || !outs || !cams || V <= 0) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    GaussPtrs gp;
+    TGS_TRY(make_gauss(c->cfg, g, gp));
+    for (int v = 0; v < V; v++) {
+        if (!outs[v].image) return TGS_ERR_INVALID_ARG;
+        CamBatch cb;
+        uint32_t *ids = nullptr;
+        TGS_TRY(plain_bin_view(c, g, gp, cams + v, cb, st, &ids));
+        PixPtrs px = pix_for(outs + v, 1, nullptr);
+        launch_blend_forward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb,
+                             px, c->cfg.bg, st);
+        if (outs[v].radii)
+            TGS_CHECK(cudaMemcpyAsync(outs[v].radii, c->radii.p, sizeof(int32_t) * (size_t)g->n,
+                                      cudaMemcpyDeviceToDevice, st));
+        TGS_TRY(last_error());
+    }
+    return TGS_OK;
+}
+
+tgs_status tgs_backward(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                        const tgs_view_out *outs, const float *const *dL_dimages,
+                        const tgs_grads *grads, const tgs_stats *stats, uint32_t flags,
+                        tgs_stream stream) {
+    if (!c || !outs || !cams || !dL_dimages || V <= 0) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    GaussPtrs gp;
+    TGS_TRY(make_gauss(c->cfg, g, gp));
+    for (int v = 0; v < V; v++) {
+        if (!outs[v].T_final || !outs[v].last || !dL_dimages[v]) return TGS_ERR_INVALID_ARG;
+        CamBatch cb;
+        uint32_t *ids = nullptr;
+        if (c->state_valid && same_g(c->state_g, *g) && same_cam(c->state_cam, cams[v]) &&
+            c->state_tile == c->cfg.tile) {
+            TGS_TRY(make_batch(c->cfg, cams + v, 1, cb));
+            ids = c->state_ids;
+        } else {
+            TGS_TRY(plain_bin_view(c, g, gp, cams + v, cb, st, &ids));
+        }
+        TGS_CHECK(cudaMemsetAsync(c->sgrads.p, 0, sizeof(float) * 12 * (size_t)g->n, st));
+        PixPtrs px = pix_for(outs + v, 1, dL_dimages + v);
+        launch_blend_backward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges),
+                              cb, px, c->cfg.bg, as<float>(c->sgrads), st);
+        const int acc = ((flags & TGS_ACCUMULATE) || v > 0) ? 1 : 0;
+        GradPtrs o = grad_ptrs(grads, stats, acc);
+        launch_preprocess_backward(gp, cb, as<float4>(c->sgrads), as<int32_t>(c->radii), o,
+                                   (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, st);
+        TGS_TRY(last_error());
+    }
+    return TGS_OK;
+}
+
+// ---- batched path --------------------------------------------------------------------------
+
+tgs_status tgs_plan(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                    double headroom, int64_t *keys_out) {
+    if (!c || headroom < 1.0) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = nullptr;
+    CamBatch cb;
+    GaussPtrs gp;
+    TGS_TRY(make_batch(c->cfg, cams, V, cb));
+    TGS_TRY(make_gauss(c->cfg, g, gp));
+    const int64_t nt = g->n * V;
+    TGS_TRY(ensure_records(c, nt, st));
+    launch_preprocess(gp, cb, as<float4>(c->splats), as<int32_t>(c->radii), as<uint32_t>(c->tt),
+                      as<uint32_t>(c->dbits), nullptr, st);
+    uint32_t *sorted = nullptr;
+    bin_front(c, nt, &sorted, st);
+    int64_t K = 0;
+    TGS_TRY(read_counts(c, st, nullptr, &K));
+    c->state_valid = false;
+    int64_t cap = (int64_t)std::ceil(headroom * (double)std::max<int64_t>(K, 1));
+    c->cfg.key_capacity = cap;
+    TGS_TRY(ensure_keys(c, cap, cb.total_tiles, st));
+    if (keys_out) *keys_out = K;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        c->graph_key.clear();
+    }
+    return last_error();
+}
+
+// The body of one batched step; issues only asynchronous work (capturable).
+static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPtrs &gp, const CamBatch &cb,
+                               const tgs_camera *cams, int V, const float *const *targets,
+                               float *const *images, const tgs_grads *grads, const tgs_stats *stats,
+                               float *loss_out, uint32_t flags, cudaStream_t st) {
+    const int64_t n = g->n, nt = n * V;
+    const int64_t cap = c->cfg.key_capacity;
+    // pixel buffers: images (if the caller gives none), T_final, last, dL/dimage
+    size_t pix = 0;
+    for (int v = 0; v < V; v++) pix += (size_t)cams[v].width * cams[v].height;
+    float *imgbuf = as<float>(c->images);
+    float *dimg = as<float>(c->dimg);
+    float *Tf = as<float>(c->pixstate);
+    int32_t *last = reinterpret_cast<int32_t *>(Tf + pix);
+    tgs_view_out outs[kMaxViews];
+    const float *dls[kMaxViews];
+    size_t off = 0;
+    for (int v = 0; v < V; v++) {
+        const size_t hw = (size_t)cams[v].width * cams[v].height;
+        outs[v].image = images && images[v] ? images[v] : imgbuf + 3 * off;
+        outs[v].T_final = Tf + off;
+        outs[v].last = last + off;
+        outs[v].n_examined = nullptr;
+        outs[v].radii = nullptr;
+        dls[v] = dimg + 3 * off;
+        off += hw;
+    }
+    const int64_t launches0 = g_launches;
+    mark(c, 0, "preprocess", st);
+    launch_preprocess(gp, cb, as<float4>(c->splats), as<int32_t>(c->radii), as<uint32_t>(c->tt),
+                      as<uint32_t>(c->dbits), as<float>(c->sgrads), st);
+    mark(c, 1, "bin", st);
+    uint32_t *sorted = nullptr;
+    bin_front(c, nt, &sorted, st);
+    uint32_t *ids = bin_back(c, nt, n, sorted, cb, cap, st);
+    mark(c, 2, "blend_forward", st);
+    PixPtrs px = pix_for(outs, V, dls);
+    launch_blend_forward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
+                         c->cfg.bg, st);
+    mark(c, 3, "l1_loss", st);
+    if (loss_out) TGS_CHECK(cudaMemsetAsync(loss_out, 0, sizeof(float), st));
+    for (int v = 0; v < V; v++) {
+        const int64_t cnt = 3 * (int64_t)cams[v].width * cams[v].height;
+        launch_l1(outs[v].image, targets[v], cnt, (float)(1.0 / ((double)cnt * V)), loss_out,
+                  const_cast<float *>(dls[v]), st);
+    }
+    mark(c, 4, "blend_backward", st);
+    launch_blend_backward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
+                          c->cfg.bg, as<float>(c->sgrads), st);
+    mark(c, 5, "preprocess_backward", st);
+    GradPtrs o = grad_ptrs(grads, stats, (flags & TGS_ACCUMULATE) ? 1 : 0);
+    launch_preprocess_backward(gp, cb, as<float4>(c->sgrads), as<int32_t>(c->radii), o,
+                               (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, st);
+    mark(c, 6, "end", st);
+    c->kernels_per_step = g_launches - launches0;
+    return last_error();
+}
+
+tgs_status tgs_train_step_batched(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                                  const float *const *targets, float *const *images, const tgs_grads *grads,
+                                  const tgs_stats *stats, float *loss_out, uint32_t flags, tgs_stream stream) {
+    if (!c || !targets || !cams || V <= 0 || V > kMaxViews) return TGS_ERR_INVALID_ARG;
+    for (int v = 0; v < V; v++)
+        if (!targets[v]) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CamBatch cb;
+    GaussPtrs gp;
+    TGS_TRY(make_batch(c->cfg, cams, V, cb));
+    TGS_TRY(make_gauss(c->cfg, g, gp));
+    if (c->cfg.key_capacity <= 0) {
+        if (capturing(st)) return TGS_ERR_CAPACITY;
+        TGS_TRY(tgs_plan(c, g, cams, V, 1.25, nullptr));
+        TGS_CHECK(cudaDeviceSynchronize());
+    }
+    const int64_t nt = g->n * V;
+    size_t pix = 0;
+    for (int v = 0; v < V; v++) pix += (size_t)cams[v].width * cams[v].height;
+    TGS_TRY(ensure_records(c, nt, st));
+    TGS_TRY(ensure_keys(c, c->cfg.key_capacity, cb.total_tiles, st));
+    TGS_TRY(ensure(c->images, sizeof(float) * 3 * pix, st));
+    TGS_TRY(ensure(c->dimg, sizeof(float) * 3 * pix, st));
+    TGS_TRY(ensure(c->pixstate, sizeof(float) * 2 * pix, st));
+    c->state_valid = false;
+
+    if (!(flags & TGS_USE_GRAPH) || st == nullptr || capturing(st))
+        return batched_body(c, g, gp, cb, cams, V, targets, images, grads, stats, loss_out, flags, st);
+
+    // key of the captured graph: every argument that the recorded launches depend on
+    std::vector<unsigned char> key;
+    auto put = [&key](const void *p, size_t n) {
+        const unsigned char *b = (const unsigned char *)p;
+        key.insert(key.end(), b, b + n);
+    };
+    put(g, sizeof *g);
+    put(cams, sizeof(tgs_camera) * V);
+    put(&V, sizeof V);
+    put(targets, sizeof(float *) * V);
+    for (int v = 0; v < V; v++) {
+        const float *im = images ? images[v] : nullptr;
+        put(&im, sizeof im);
+    }
+    tgs_grads gz{};
+    tgs_stats sz{};
+    put(grads ? grads : &gz, sizeof gz);
+    put(stats ? stats : &sz, sizeof sz);
+    put(&loss_out, sizeof loss_out);
+    put(&flags, sizeof flags);
+    put(&c->cfg, sizeof c->cfg);
+    void *arena[] = {c->splats.p, c->tk0.p, c->hist.p, c->images.p, c->pixstate.p};
+    put(arena, sizeof arena);
+    if (!c->graph || key != c->graph_key) {
+        if (c->graph) {
+            cudaGraphExecDestroy(c->graph);
+            c->graph = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        TGS_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        tgs_status s = batched_body(c, g, gp, cb, cams, V, targets, images, grads, stats, loss_out, flags, st);
+        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (s != TGS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        TGS_CHECK(e);
+        e = cudaGraphInstantiate(&c->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        TGS_CHECK(e);
+        c->graph_key = key;
+    }
+    TGS_CHECK(cudaGraphLaunch(c->graph, st));
+    return TGS_OK;
+}
+
+tgs_status tgs_set_profiling(tgs_ctx *c, int32_t on) {
+    if (!c) return TGS_ERR_INVALID_ARG;
+    if (on && !c->stage_ev[0])
+        for (auto &e : c->stage_ev) TGS_CHECK(cudaEventCreate(&e));
+    if ((bool)on != c->profiling && c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+        c->graph_key.clear();
+    }
+    c->profiling = on != 0;
+    return TGS_OK;
+}
+
+tgs_status tgs_stage_times(tgs_ctx *c, float *ms, int32_t max, int32_t *n_out) {
+    if (!c || !ms || !c->profiling) return TGS_ERR_INVALID_ARG;
+    const int n = c->n_stages;
+    TGS_CHECK(cudaEventSynchronize(c->stage_ev[n]));
+    for (int i = 0; i < n && i < max; i++) TGS_CHECK(cudaEventElapsedTime(ms + i, c->stage_ev[i], c->stage_ev[i + 1]));
+    if (n_out) *n_out = n;
+    return TGS_OK;
+}
+
+const char *tgs_stage_name(tgs_ctx *c, int32_t i) {
+    if (!c || i < 0 || i >= c->n_stages || i >= TGS_MAX_STAGES) return "";
+    return c->stage_names[i] ? c->stage_names[i] : "";
+}
+
+int64_t tgs_kernels_per_step(const tgs_ctx *c) { return c ? c->kernels_per_step : -1; }
+
+tgs_status tgs_autotune(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                        const float *const *targets, const char *cache_path, tgs_stream stream) {
+    if (!c || !g || !cams || !targets) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // cache key: n, V and the view sizes
+    std::string key = "n" + std::to_string(g->n) + "_V" + std::to_string(V);
+    for (int v = 0; v < V; v++) key += "_" + std::to_string(cams[v].width) + "x" + std::to_string(cams[v].height);
+    std::vector<std::pair<std::string, std::pair<int, int>>> cache;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char line[1024];
+            while (fgets(line, sizeof line, f)) {
+                char k[900];
+                int tl = 0, pp = 0;
+                if (sscanf(line, " \"%899[^\"]\" : { \"tile\" : %d , \"ppt\" : %d", k, &tl, &pp) == 3)
+                    cache.push_back({k, {tl, pp}});
+            }
+            fclose(f);
+        }
+        for (auto &e : cache)
+            if (e.first == key) {
+                tgs_config cf = c->cfg;
+                cf.tile = e.second.first;
+                cf.ppt = e.second.second;
+                if (!valid_cfg(cf)) break;
+                TGS_TRY(tgs_set_config(c, &cf));
+                return tgs_plan(c, g, cams, V, 1.25, nullptr);
+            }
+    }
+    const int tiles[3] = {8, 16, 32}, ppts[3] = {1, 2, 4};
+    float best = 1e30f;
+    tgs_config best_cfg = c->cfg, base = c->cfg;
+    cudaEvent_t e0, e1;
+    TGS_CHECK(cudaEventCreate(&e0));
+    TGS_CHECK(cudaEventCreate(&e1));
+    for (int tl : tiles)
+        for (int pp : ppts) {
+            tgs_config cf = base;
+            cf.tile = tl;
+            cf.ppt = pp;
+            if (!valid_cfg(cf)) continue;
+            cf.key_capacity = 0;
+            TGS_TRY(tgs_set_config(c, &cf));
+            TGS_TRY(tgs_plan(c, g, cams, V, 1.25, nullptr));
+            for (int w = 0; w < 2; w++)
+                TGS_TRY(tgs_train_step_batched(c, g, cams, V, targets, nullptr, nullptr, nullptr, nullptr, 0, st));
+            TGS_CHECK(cudaEventRecord(e0, st));
+            const int reps = 3;
+            for (int r = 0; r < reps; r++)
+                TGS_TRY(tgs_train_step_batched(c, g, cams, V, targets, nullptr, nullptr, nullptr, nullptr, 0, st));
+            TGS_CHECK(cudaEventRecord(e1, st));
+            TGS_CHECK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            TGS_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_cfg = cf;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    best_cfg.key_capacity = 0;
+    TGS_TRY(tgs_set_config(c, &best_cfg));
+    TGS_TRY(tgs_plan(c, g, cams, V, 1.25, nullptr));
+    if (cache_path) {
+        bool found = false;
+        for (auto &e : cache)
+            if (e.first == key) {
+                e.second = {best_cfg.tile, best_cfg.ppt};
+                found = true;
+            }
+        if (!found) cache.push_back({key, {best_cfg.tile, best_cfg.ppt}});
+        FILE *f = fopen(cache_path, "w");
+        if (f) {
+            fprintf(f, "{\n");
+            for (size_t i = 0; i < cache.size(); i++)
+                fprintf(f, "  \"%s\": {\"tile\": %d, \"ppt\": %d}%s\n", cache[i].first.c_str(),
+                        cache[i].second.first, cache[i].second.second, i + 1 < cache.size() ? "," : "");
+            fprintf(f, "}\n");
+            fclose(f);
+        }
+    }
+    return TGS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,367 @@
+"""Torch-facing wrappers of libtgs: device tensors in, device tensors out.
+
+This module only marshals arguments (tensor pointers, camera structs, the current stream)
+into the C ABI of include/tgs.h; all arithmetic runs in the library's kernels. PyTorch is
+used for device memory and streams.
+
+``RasterizeViews`` is a ``torch.autograd.Function`` over V views. Its forward keeps, per
+view, only the pixel state the backward needs (final transmittance and the position of the
+last contributor); the per-view Gaussian lists are rebuilt in the backward (per-view
+checkpointing), except for the last view rendered, whose binning the library keeps.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import numpy as np
+import torch
+
+from . import _binding as B
+
+PARAM_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh_dc", "sh_rest",
+              "mask_logits", "sh_mask_logits")
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check_tensor(t, name, dtype=torch.float32):
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+
+
+@dataclasses.dataclass
+class Gaussians:
+    """Gaussian parameters as CUDA tensors (layout of include/tgs.h)."""
+    means: torch.Tensor
+    log_scales: torch.Tensor
+    quats: torch.Tensor
+    opacity_logits: torch.Tensor
+    sh_dc: torch.Tensor
+    sh_rest: torch.Tensor | None = None
+    mask_logits: torch.Tensor | None = None
+    sh_mask_logits: torch.Tensor | None = None
+    sh_degree: torch.Tensor | None = None       # uint8 [N]
+    sh_degree_max: int | None = None
+
+    @property
+    def n(self):
+        return self.means.shape[0]
+
+    def struct(self):
+        for k in PARAM_KEYS:
+            _check_tensor(getattr(self, k), k)
+        _check_tensor(self.sh_degree, "sh_degree", torch.uint8)
+        deg = self.sh_degree_max
+        if deg is None:
+            deg = 3 if self.sh_rest is not None else 0
+        return B.tgs_gaussians(self.n, deg, 0, _p(self.means), _p(self.log_scales),
+                               _p(self.quats), _p(self.opacity_logits), _p(self.sh_dc),
+                               _p(self.sh_rest), _p(self.sh_degree), _p(self.mask_logits),
+                               _p(self.sh_mask_logits))
+
+    @staticmethod
+    def from_numpy(scene, device="cuda"):
+        def t(k, dtype=torch.float32):
+            v = scene.get(k)
+            if v is None:
+                return None
+            return torch.from_numpy(np.ascontiguousarray(v)).to(device=device, dtype=dtype)
+        return Gaussians(t("means"), t("log_scales"), t("quats"), t("opacity_logits"),
+                         t("sh_dc"), t("sh_rest"), t("mask_logits"), t("sh_mask_logits"),
+                         t("sh_degree", torch.uint8), scene.get("deg_max"))
+
+    def params(self):
+        return {k: getattr(self, k) for k in PARAM_KEYS if getattr(self, k) is not None}
+
+
+def camera_struct(cam, low_pass=0.0):
+    c = B.tgs_camera()
+    vm = np.asarray(cam.viewmat, dtype=np.float32).reshape(-1)
+    for i in range(16):
+        c.viewmat[i] = float(vm[i])
+    cp = np.asarray(cam.campos, dtype=np.float32)
+    for i in range(3):
+        c.campos[i] = float(cp[i])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.low_pass = float(low_pass)
+    return c
+
+
+def cameras_array(cams):
+    arr = (B.tgs_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i] = c if isinstance(c, B.tgs_camera) else camera_struct(c)
+    return arr
+
+
+def _ptr_array(tensors):
+    arr = (C.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        arr[i] = None if t is None else t.data_ptr()
+    return arr
+
+
+class Rasterizer:
+    """One libtgs context (its settings and its scratch arena) on the current device."""
+
+    def __init__(self, tile=16, ppt=1, support=B.TGS_SUPPORT_BOX3, low_pass=0.3, eps_mask=0.05,
+                 eps_sh=0.1, near=0.2, bg=(0.0, 0.0, 0.0), key_capacity=0):
+        cfg = B.tgs_config()
+        B.lib.tgs_default_config(C.byref(cfg))
+        cfg.tile, cfg.ppt, cfg.support = tile, ppt, support
+        cfg.low_pass, cfg.eps_mask, cfg.eps_sh, cfg.near_plane = low_pass, eps_mask, eps_sh, near
+        for i in range(3):
+            cfg.bg[i] = bg[i]
+        cfg.key_capacity = key_capacity
+        h = C.c_void_p()
+        B.check(B.lib.tgs_create(C.byref(h), C.byref(cfg)), "tgs_create")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and B is not None and B.lib is not None:
+            B.lib.tgs_destroy(h)
+            self._h = None
+
+    @property
+    def config(self):
+        cfg = B.tgs_config()
+        B.check(B.lib.tgs_get_config(self._h, C.byref(cfg)), "tgs_get_config")
+        return cfg
+
+    def set(self, **kw):
+        cfg = self.config
+        for k, v in kw.items():
+            if k == "bg":
+                for i in range(3):
+                    cfg.bg[i] = v[i]
+            else:
+                setattr(cfg, k, v)
+        B.check(B.lib.tgs_set_config(self._h, C.byref(cfg)), "tgs_set_config")
+
+    def poll(self):
+        B.check(B.lib.tgs_poll_status(self._h, _stream()), "device status")
+
+    # ---- plain path ----------------------------------------------------------------------
+
+    def _alloc_views(self, cams, n, want_state=True, want_examined=False, want_radii=False):
+        outs = []
+        for c in cams:
+            H, W = c.height, c.width
+            d = dict(image=torch.empty((3, H, W), device="cuda"))
+            if want_state:
+                d["T_final"] = torch.empty((H, W), device="cuda")
+                d["last"] = torch.empty((H, W), device="cuda", dtype=torch.int32)
+            if want_examined:
+                d["n_examined"] = torch.empty((H, W), device="cuda", dtype=torch.int32)
+            if want_radii:
+                d["radii"] = torch.empty((n,), device="cuda", dtype=torch.int32)
+            outs.append(d)
+        return outs
+
+    @staticmethod
+    def _out_structs(outs):
+        arr = (B.tgs_view_out * len(outs))()
+        for i, d in enumerate(outs):
+            arr[i] = B.tgs_view_out(_p(d.get("image")), _p(d.get("T_final")), _p(d.get("last")),
+                                    _p(d.get("n_examined")), _p(d.get("radii")))
+        return arr
+
+    def forward(self, g: Gaussians, cams, want_state=True, want_examined=False,
+                want_radii=False, outs=None):
+        outs = outs or self._alloc_views(cams, g.n, want_state, want_examined, want_radii)
+        B.check(B.lib.tgs_forward(self._h, C.byref(g.struct()), cameras_array(cams), len(cams),
+                                  self._out_structs(outs), 0, _stream()), "tgs_forward")
+        return outs
+
+    @staticmethod
+    def alloc_grads(g: Gaussians, no_sh_rest=False):
+        d = {}
+        for k, v in g.params().items():
+            if k == "sh_rest" and no_sh_rest:
+                continue
+            d[k] = torch.zeros_like(v)
+        return d
+
+    @staticmethod
+    def alloc_stats(n):
+        return dict(grad_norm_accum=torch.zeros(n, device="cuda"),
+                    vis_count=torch.zeros(n, device="cuda", dtype=torch.int32),
+                    max_radius=torch.zeros(n, device="cuda", dtype=torch.int32))
+
+    @staticmethod
+    def _grad_struct(grads):
+        grads = grads or {}
+        return B.tgs_grads(*[_p(grads.get(k)) for k in PARAM_KEYS])
+
+    @staticmethod
+    def _stats_struct(stats):
+        stats = stats or {}
+        return B.tgs_stats(_p(stats.get("grad_norm_accum")), _p(stats.get("vis_count")),
+                           _p(stats.get("max_radius")))
+
+    def backward(self, g: Gaussians, cams, outs, dL_dimages, grads=None, stats=None,
+                 accumulate=False, no_sh_rest=False):
+        if grads is None:
+            grads = self.alloc_grads(g, no_sh_rest)
+        if stats is None:
+            stats = self.alloc_stats(g.n)
+        flags = (B.TGS_ACCUMULATE if accumulate else 0) | (B.TGS_NO_SH_REST_GRAD if no_sh_rest else 0)
+        dl = [d.contiguous() for d in dL_dimages]
+        B.check(B.lib.tgs_backward(self._h, C.byref(g.struct()), cameras_array(cams), len(cams),
+                                   self._out_structs(outs), _ptr_array(dl),
+                                   C.byref(self._grad_struct(grads)),
+                                   C.byref(self._stats_struct(stats)), flags, _stream()),
+                "tgs_backward")
+        return grads, stats
+
+    @staticmethod
+    def l1_loss(image, target, scale, loss_accum, grad):
+        B.check(B.lib.tgs_l1_loss(_p(image), _p(target), image.numel(), float(scale),
+                                  _p(loss_accum), _p(grad), _stream()), "tgs_l1_loss")
+
+    # ---- individual steps -----------------------------------------------------------------
+
+    def preprocess(self, g: Gaussians, cams):
+        V = len(cams)
+        splats = torch.empty((V * g.n, 12), device="cuda")
+        radii = torch.empty((V * g.n,), device="cuda", dtype=torch.int32)
+        B.check(B.lib.tgs_preprocess(self._h, C.byref(g.struct()), cameras_array(cams), V,
+                                     _p(splats), _p(radii), _stream()), "tgs_preprocess")
+        return splats, radii
+
+    def num_tiles(self, cams):
+        return int(B.lib.tgs_num_tiles(self._h, cameras_array(cams), len(cams)))
+
+    def bin(self, splats, radii, n, cams, capacity=None, want_keys=True):
+        """Returns (sorted record ids, sorted 64-bit keys as int64, ranges [tiles,2], K)."""
+        V = len(cams)
+        T = self.num_tiles(cams)
+        ranges = torch.empty((T, 2), device="cuda", dtype=torch.int32)
+        K = C.c_int64(0)
+        cap = capacity
+        if cap is None:
+            # first pass only counts
+            dummy = torch.empty((1,), device="cuda", dtype=torch.int32)
+            st = B.lib.tgs_bin(self._h, _p(splats), _p(radii), n, cameras_array(cams), V,
+                               _p(dummy), None, _p(ranges), 0, C.byref(K), _stream())
+            if st not in (B.TGS_OK, B.TGS_ERR_CAPACITY):
+                B.check(st, "tgs_bin")
+            cap = max(int(K.value), 1)
+        ids = torch.empty((cap,), device="cuda", dtype=torch.int32)
+        keys = torch.empty((cap,), device="cuda", dtype=torch.int64) if want_keys else None
+        B.check(B.lib.tgs_bin(self._h, _p(splats), _p(radii), n, cameras_array(cams), V, _p(ids),
+                              _p(keys), _p(ranges), cap, C.byref(K), _stream()), "tgs_bin")
+        k = int(K.value)
+        return ids[:k], (keys[:k] if keys is not None else None), ranges, k
+
+    def blend_forward(self, splats, ids, ranges, cams, want_examined=True):
+        outs = self._alloc_views(cams, 0, True, want_examined)
+        B.check(B.lib.tgs_blend_forward(self._h, _p(splats), _p(ids), _p(ranges),
+                                        cameras_array(cams), len(cams), self._out_structs(outs),
+                                        _stream()), "tgs_blend_forward")
+        return outs
+
+    def blend_backward(self, splats, ids, ranges, cams, outs, dL_dimages):
+        sg = torch.zeros((splats.shape[0], 12), device="cuda")
+        dl = [d.contiguous() for d in dL_dimages]
+        B.check(B.lib.tgs_blend_backward(self._h, _p(splats), _p(ids), _p(ranges),
+                                         cameras_array(cams), len(cams), self._out_structs(outs),
+                                         _ptr_array(dl), _p(sg), _stream()), "tgs_blend_backward")
+        return sg
+
+    def preprocess_backward(self, g: Gaussians, cams, splat_grads, radii, grads=None, stats=None,
+                            accumulate=False, no_sh_rest=False):
+        if grads is None:
+            grads = self.alloc_grads(g, no_sh_rest)
+        if stats is None:
+            stats = self.alloc_stats(g.n)
+        flags = (B.TGS_ACCUMULATE if accumulate else 0) | (B.TGS_NO_SH_REST_GRAD if no_sh_rest else 0)
+        B.check(B.lib.tgs_preprocess_backward(self._h, C.byref(g.struct()), cameras_array(cams),
+                                              len(cams), _p(splat_grads), _p(radii),
+                                              C.byref(self._grad_struct(grads)),
+                                              C.byref(self._stats_struct(stats)), flags,
+                                              _stream()), "tgs_preprocess_backward")
+        return grads, stats
+
+    # ---- batched path ----------------------------------------------------------------------
+
+    def plan(self, g: Gaussians, cams, headroom=1.25):
+        K = C.c_int64(0)
+        B.check(B.lib.tgs_plan(self._h, C.byref(g.struct()), cameras_array(cams), len(cams),
+                               float(headroom), C.byref(K)), "tgs_plan")
+        return int(K.value)
+
+    def train_step_batched(self, g: Gaussians, cams, targets, grads, stats=None, loss=None,
+                           images=None, graph=False, accumulate=False, no_sh_rest=False,
+                           cams_struct=None):
+        flags = ((B.TGS_USE_GRAPH if graph else 0) | (B.TGS_ACCUMULATE if accumulate else 0) |
+                 (B.TGS_NO_SH_REST_GRAD if no_sh_rest else 0))
+        camarr = cams_struct if cams_struct is not None else cameras_array(cams)
+        B.check(B.lib.tgs_train_step_batched(
+            self._h, C.byref(g.struct()), camarr, len(camarr), _ptr_array(targets),
+            _ptr_array(images) if images is not None else None, C.byref(self._grad_struct(grads)),
+            C.byref(self._stats_struct(stats)), _p(loss), flags, _stream()),
+            "tgs_train_step_batched")
+
+    def set_profiling(self, on=True):
+        B.check(B.lib.tgs_set_profiling(self._h, int(on)), "tgs_set_profiling")
+
+    def stage_times(self):
+        """{stage name: milliseconds} of the most recent batched step (profiling on)."""
+        ms = (C.c_float * B.TGS_MAX_STAGES)()
+        n = C.c_int32(0)
+        B.check(B.lib.tgs_stage_times(self._h, ms, B.TGS_MAX_STAGES, C.byref(n)), "tgs_stage_times")
+        return {B.lib.tgs_stage_name(self._h, i).decode(): float(ms[i]) for i in range(n.value)}
+
+    def kernels_per_step(self):
+        return int(B.lib.tgs_kernels_per_step(self._h))
+
+    def autotune(self, g: Gaussians, cams, targets, cache_path=None):
+        B.check(B.lib.tgs_autotune(self._h, C.byref(g.struct()), cameras_array(cams), len(cams),
+                                   _ptr_array(targets),
+                                   None if cache_path is None else cache_path.encode(),
+                                   _stream()), "tgs_autotune")
+        cfg = self.config
+        return dict(tile=cfg.tile, ppt=cfg.ppt, key_capacity=cfg.key_capacity)
+
+
+class RasterizeViews(torch.autograd.Function):
+    """images = RasterizeViews.apply(rasterizer, gaussians, cams, *params).
+
+    ``params`` are the differentiable tensors of ``gaussians`` in PARAM_KEYS order (None
+    entries skipped). Returns one [3,H,W] image per view."""
+
+    @staticmethod
+    def forward(ctx, rast: Rasterizer, g: Gaussians, cams, *params):
+        outs = rast.forward(g, cams, want_state=True)
+        ctx.rast, ctx.g, ctx.cams = rast, g, cams
+        ctx.keys = [k for k in PARAM_KEYS if getattr(g, k) is not None]
+        # per-view checkpoint: T_final and last only
+        ctx.state = [dict(T_final=o["T_final"], last=o["last"]) for o in outs]
+        return tuple(o["image"] for o in outs)
+
+    @staticmethod
+    def backward(ctx, *dL):
+        outs = [dict(image=None, **s) for s in ctx.state]
+        dL = [torch.zeros_like(o["T_final"]).expand(3, -1, -1).contiguous() if d is None else d
+              for d, o in zip(dL, outs)]
+        grads, stats = ctx.rast.backward(ctx.g, ctx.cams, outs, dL)
+        ctx.stats = stats
+        return (None, None, None) + tuple(grads.get(k) for k in ctx.keys)
+
+
+def rasterize(rast: Rasterizer, g: Gaussians, cams):
+    """Differentiable rendering of V views; gradients flow into ``g``'s tensors."""
+    params = [getattr(g, k) for k in PARAM_KEYS if getattr(g, k) is not None]
+    return RasterizeViews.apply(rast, g, cams, *params)

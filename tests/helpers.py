@@ -1,0 +1,44 @@
+"""Helpers shared by the GPU parity tests: conversions between the library's splat records
+and the oracle's per-Gaussian arrays, and the comparison rules.
+
+Comparison rules (tolerances of the parity tests):
+  - keys, values, ranges, radii and rects: bit-exact, except a radius or rect that the FP64
+    oracle puts within 1e-5 relative of an integer boundary (counted);
+  - images: max |gpu - oracle| <= 1e-4 over pixels whose every blend decision is clear of its
+    threshold by more than the float32 uncertainty (the oracle's per-pixel margin >= 1);
+  - gradients: per tensor ||g - g*|| / ||g*|| <= 1e-3.
+"""
+import numpy as np
+
+import oracle
+
+IMAGE_ATOL = 1e-4
+GRAD_RTOL = 1e-3
+
+
+def splats_to_oracle(rec, radii):
+    """Library splat records [n,12] float32 (numpy) -> oracle per-Gaussian arrays."""
+    rec = np.asarray(rec, dtype=np.float32)
+    bits = rec.view(np.uint32)
+    rx, ry = bits[:, 9], bits[:, 10]
+    rect = np.stack([rx & 0xFFFF, rx >> 16, ry & 0xFFFF, ry >> 16], axis=1).astype(np.int32)
+    radii = np.asarray(radii, dtype=np.int32)
+    vis = radii > 0
+    z = lambda a: np.where(vis.reshape((-1,) + (1,) * (a.ndim - 1)), a, 0)
+    return oracle.splats_from(z(rec[:, 0:2]), z(rec[:, 11]), z(rec[:, 2:5]), z(rec[:, 5]),
+                              z(rec[:, 6:9]), radii, np.where(vis[:, None], rect, 0))
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    d = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (d if d > 0 else 1.0)
+
+
+def image_compare(gpu, ref, margin):
+    """Returns (max abs diff over clear pixels, fraction of pixels excluded)."""
+    clear = margin >= 1.0
+    diff = np.abs(np.asarray(gpu, np.float64) - ref).max(axis=0)
+    m = float(diff[clear].max()) if clear.any() else 0.0
+    return m, 1.0 - clear.mean()

@@ -1,0 +1,442 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, step by step and end to
+end, on seeded synthetic scenes that span several tiles and a ragged image border."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_14534_gb300 import synth
+
+from helpers import GRAD_RTOL, IMAGE_ATOL, image_compare, rel_err, splats_to_oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA is not available: the GPU tests cannot run")
+    from paper_2501_14534_gb300 import build
+    build.build()
+    from paper_2501_14534_gb300 import rasterizer as R
+    return R
+
+
+def settings_for(tile=16, eps=(0.05, 0.1), support=0, bg=(0.0, 0.0, 0.0)):
+    return oracle.Settings(tile=tile, eps_mask=eps[0], eps_sh=eps[1], support=support, bg=bg)
+
+
+def make_rast(R, st, ppt=1, cap=0):
+    return R.Rasterizer(tile=st.tile, ppt=ppt, support=st.support, low_pass=st.low_pass,
+                        eps_mask=st.eps_mask, eps_sh=st.eps_sh, near=st.near, bg=st.bg,
+                        key_capacity=cap)
+
+
+def c1_case():
+    w = synth.workload(1)
+    return w["scene"], w["cams"], settings_for(eps=(w["eps_mask"], w["eps_sh"]))
+
+
+def masked_case(n=3000, views=((61, 45, 0.2), (96, 80, 2.0)), degree=False, seed=5):
+    scene = synth.blob_scene(n, 8, seed, log_scale=(-3.0, 0.5), per_gaussian_degree=degree,
+                             masks=not degree)
+    cams = [synth.ring_cameras(1, [(w, h)], radius=4.0, height=0.5, phase=a)[0]
+            for (w, h, a) in views]
+    return scene, cams, settings_for(eps=(0.5, 0.5))
+
+
+CASES = {
+    "c1_uniform_10k": c1_case,
+    "masked_blobs_2views": lambda: masked_case(),
+    "per_gaussian_degree": lambda: masked_case(2000, ((70, 50, 1.0),), degree=True, seed=6),
+}
+
+
+def gpu_scene(R, scene):
+    return R.Gaussians.from_numpy(scene)
+
+
+def np_(t):
+    return t.detach().cpu().numpy()
+
+
+# ------------------------------------------------------------------------------------
+# (a) preprocess
+# ------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("support", [0, 1])
+def test_preprocess_matches_oracle(R, case, support):
+    scene, cams, st = CASES[case]()
+    st.support = support
+    rast = make_rast(R, st)
+    g = gpu_scene(R, scene)
+    splats, radii = rast.preprocess(g, cams)
+    splats, radii = np_(splats), np_(radii)
+    n = g.n
+    total_mism = 0
+    for v, cam in enumerate(cams):
+        ref = oracle.preprocess(scene, cam, st)
+        rec = splats[v * n:(v + 1) * n]
+        rad = radii[v * n:(v + 1) * n]
+        gs = splats_to_oracle(rec, rad)
+        both = (rad > 0) & (ref["radius"] > 0)
+        mism = (rad != ref["radius"]) | np.any(gs["rect"] != ref["rect"], axis=1)
+        # every integer mismatch must sit on an FP64 decision boundary
+        assert np.all(np.minimum(ref["m_edge"], ref["m_all"])[mism] < 100.0)
+        total_mism += int(mism.sum())
+        ok = both & ~mism
+        assert ok.sum() > 0.5 * (ref["radius"] > 0).sum()
+        np.testing.assert_allclose(gs["mean2d"][ok], ref["mean2d"][ok], rtol=1e-5, atol=2e-4)
+        np.testing.assert_allclose(gs["depth"][ok], ref["depth"][ok], rtol=2e-6)
+        np.testing.assert_allclose(gs["opacity"][ok], ref["opacity"][ok], rtol=2e-6, atol=1e-7)
+        np.testing.assert_allclose(gs["rgb"][ok], ref["rgb"][ok], atol=2e-5)
+        cscale = np.abs(ref["conic"][ok]).max(axis=1, keepdims=True)
+        assert np.all(np.abs(gs["conic"][ok] - ref["conic"][ok]) <= 1e-4 * cscale + 1e-7)
+    assert total_mism <= max(2, 1e-3 * n * len(cams))
+
+
+# ------------------------------------------------------------------------------------
+# (b) keys, sort and ranges: bit-exact
+# ------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_keys_sort_ranges_bit_exact(R, tile):
+    scene, cams, st = masked_case(4000, ((61, 45, 0.2), (96, 80, 2.0), (33, 17, 4.0)))
+    st.tile = tile
+    rast = make_rast(R, st, ppt=2)
+    g = gpu_scene(R, scene)
+    splats, radii = rast.preprocess(g, cams)
+    ids, keys, ranges, K = rast.bin(splats, radii, g.n, cams)
+    ids, keys, ranges = np_(ids).view(np.uint32), np_(keys).view(np.uint64), np_(ranges).view(np.uint32)
+    rec, rad = np_(splats), np_(radii)
+    n = g.n
+    ek, ev, er = [], [], []
+    toff = 0
+    for v, cam in enumerate(cams):
+        gs = splats_to_oracle(rec[v * n:(v + 1) * n], rad[v * n:(v + 1) * n])
+        k, vv, r = oracle.keys(gs["radius"], gs["rect"], rec[v * n:(v + 1) * n, 11], cam.width,
+                               cam.height, tile, tile_offset=toff, value_offset=v * n)
+        base = sum(len(x) for x in ek)
+        nz = r[:, 1] > 0
+        r = r.copy()
+        r[nz] += base
+        ek.append(k)
+        ev.append(vv)
+        er.append(r)
+        toff += r.shape[0]
+    ek, ev, er = np.concatenate(ek), np.concatenate(ev), np.concatenate(er)
+    assert K == len(ek) and K > 1000
+    assert np.array_equal(keys, ek)
+    assert np.array_equal(ids, ev)
+    assert np.array_equal(ranges, er)
+
+
+# ------------------------------------------------------------------------------------
+# (c) blend forward
+# ------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_blend_forward_matches_oracle_on_same_records(R, case):
+    scene, cams, st = CASES[case]()
+    st.bg = (0.1, 0.2, 0.3)
+    rast = make_rast(R, st)
+    g = gpu_scene(R, scene)
+    splats, radii = rast.preprocess(g, cams)
+    ids, _, ranges, K = rast.bin(splats, radii, g.n, cams, want_keys=False)
+    outs = rast.blend_forward(splats, ids, ranges, cams)
+    rec, rad = np_(splats), np_(radii)
+    n = g.n
+    for v, cam in enumerate(cams):
+        gs = splats_to_oracle(rec[v * n:(v + 1) * n], rad[v * n:(v + 1) * n])
+        ref = oracle.blend(gs, cam.width, cam.height, st.tile, st.bg, margins=True)
+        img = np_(outs[v]["image"])
+        m, excl = image_compare(img, ref["image"], ref["margin"])
+        assert m <= IMAGE_ATOL, (m, excl)
+        assert excl < 2e-3
+        clear = ref["margin"] >= 1.0
+        assert np.array_equal(np_(outs[v]["last"])[clear], ref["last"][clear])
+        assert np.array_equal(np_(outs[v]["n_examined"])[clear], ref["n_examined"][clear])
+        np.testing.assert_allclose(np_(outs[v]["T_final"])[clear], ref["T_final"][clear],
+                                   rtol=1e-4, atol=1e-7)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_forward_end_to_end_matches_fp64_oracle(R, case):
+    scene, cams, st = CASES[case]()
+    rast = make_rast(R, st)
+    g = gpu_scene(R, scene)
+    outs = rast.forward(g, cams, want_radii=True)
+    for v, cam in enumerate(cams):
+        ref = oracle.render(scene, cam, st, margins=True)
+        m, excl = image_compare(np_(outs[v]["image"]), ref["image"], ref["margin"])
+        assert m <= IMAGE_ATOL, (m, excl)
+        assert excl < 0.05, excl
+        assert np.array_equal(np_(outs[v]["radii"]) > 0, ref["splats"]["radius"] > 0) or \
+            np.sum((np_(outs[v]["radii"]) > 0) != (ref["splats"]["radius"] > 0)) <= 2
+
+
+def test_image_invariant_to_tile_size_and_pixels_per_thread(R):
+    scene, cams, st = masked_case(3000, ((77, 53, 0.9),))
+    g = gpu_scene(R, scene)
+    ref = None
+    for tile, ppt in [(8, 1), (8, 2), (16, 1), (16, 2), (16, 4), (32, 2), (32, 4)]:
+        st.tile = tile
+        rast = make_rast(R, st, ppt=ppt)
+        img = np_(rast.forward(g, cams)[0]["image"])
+        if ref is None:
+            ref = img
+        assert np.array_equal(img, ref), (tile, ppt)
+
+
+# ------------------------------------------------------------------------------------
+# (d) backward
+# ------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_blend_backward_matches_oracle_on_same_records(R, case):
+    scene, cams, st = CASES[case]()
+    st.bg = (0.3, 0.1, 0.2)
+    rast = make_rast(R, st)
+    g = gpu_scene(R, scene)
+    splats, radii = rast.preprocess(g, cams)
+    ids, _, ranges, K = rast.bin(splats, radii, g.n, cams, want_keys=False)
+    outs = rast.blend_forward(splats, ids, ranges, cams)
+    rng = np.random.default_rng(7)
+    dls = [rng.normal(size=(3, c.height, c.width)).astype(np.float32) for c in cams]
+    sg = np_(rast.blend_backward(splats, ids, ranges, cams, outs,
+                                 [torch.from_numpy(d).cuda() for d in dls]))
+    rec, rad = np_(splats), np_(radii)
+    n = g.n
+    for v, cam in enumerate(cams):
+        gs = splats_to_oracle(rec[v * n:(v + 1) * n], rad[v * n:(v + 1) * n])
+        ref = oracle.blend_backward(gs, cam.width, cam.height, dls[v], st.tile, st.bg)
+        got = sg[v * n:(v + 1) * n, :9]
+        for name, cols in [("mean2d", [0, 1]), ("conic", [2, 3, 4]), ("opacity", [5]),
+                           ("rgb", [6, 7, 8])]:
+            e = rel_err(got[:, cols], ref[:, cols])
+            assert e <= GRAD_RTOL, (name, e)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_preprocess_backward_matches_oracle_on_same_splat_grads(R, case):
+    scene, cams, st = CASES[case]()
+    rast = make_rast(R, st)
+    g = gpu_scene(R, scene)
+    splats, radii = rast.preprocess(g, cams)
+    n = g.n
+    rng = np.random.default_rng(3)
+    sg = rng.normal(size=(len(cams) * n, 12)).astype(np.float32)
+    sg[:, 9:] = 0
+    grads, stats = rast.preprocess_backward(g, cams, torch.from_numpy(sg).cuda(), radii)
+    rad = np_(radii)
+    ref = oracle.zero_grads(scene)
+    rstats = oracle.new_stats(n)
+    for v, cam in enumerate(cams):
+        g9 = sg[v * n:(v + 1) * n, :9].astype(np.float64)
+        g9[rad[v * n:(v + 1) * n] == 0] = 0.0
+        oracle.preprocess_backward(scene, cam, st, g9, ref, rstats)
+    for k, t in grads.items():
+        e = rel_err(np_(t), ref[k])
+        assert e <= 1e-4, (k, e)
+    assert np.array_equal(np_(stats["vis_count"]), rstats["count"])
+    assert np.array_equal(np_(stats["max_radius"]), rstats["max_radius"])
+    np.testing.assert_allclose(np_(stats["grad_norm_accum"]), rstats["accum"], rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_backward_end_to_end_matches_fp64_oracle(R, case):
+    scene, cams, st = CASES[case]()
+    rast = make_rast(R, st)
+    g = gpu_scene(R, scene)
+    outs = rast.forward(g, cams)
+    rng = np.random.default_rng(11)
+    dls = [rng.normal(size=(3, c.height, c.width)).astype(np.float32) for c in cams]
+    grads, stats = rast.backward(g, cams, outs, [torch.from_numpy(d).cuda() for d in dls])
+    ref, rstats, _ = oracle.grad(scene, cams, st, [d.astype(np.float64) for d in dls])
+    for k, t in grads.items():
+        e = rel_err(np_(t), ref[k])
+        assert e <= GRAD_RTOL, (k, e)
+    cnt = np_(stats["vis_count"])
+    assert np.sum(cnt != rstats["count"]) <= 2
+    same = cnt == rstats["count"]
+    assert rel_err(np_(stats["grad_norm_accum"])[same], rstats["accum"][same]) <= GRAD_RTOL
+
+
+def test_no_sh_rest_flag_leaves_other_grads_identical(R):
+    scene, cams, st = masked_case()
+    rast = make_rast(R, st)
+    g = gpu_scene(R, scene)
+    outs = rast.forward(g, cams)
+    dl = [torch.ones((3, c.height, c.width), device="cuda") for c in cams]
+    a, _ = rast.backward(g, cams, outs, dl)
+    b, _ = rast.backward(g, cams, outs, dl, no_sh_rest=True)
+    assert "sh_rest" not in b
+    # float atomics make the summation order differ between two runs: compare norms
+    for k in b:
+        assert rel_err(np_(b[k]), np_(a[k])) <= 1e-5, k
+
+
+# ------------------------------------------------------------------------------------
+# autograd with per-view checkpointing; batched step; graphs; capacity
+# ------------------------------------------------------------------------------------
+
+def test_autograd_function_matches_oracle(R):
+    scene, cams, st = masked_case(2500)
+    rast = make_rast(R, st)
+    g = gpu_scene(R, scene)
+    for k in R.PARAM_KEYS:
+        t = getattr(g, k)
+        if t is not None:
+            t.requires_grad_(True)
+    imgs = R.rasterize(rast, g, cams)
+    rng = np.random.default_rng(5)
+    ws = [rng.normal(size=(3, c.height, c.width)) for c in cams]
+    loss = sum((im * torch.from_numpy(w).float().cuda()).sum() for im, w in zip(imgs, ws))
+    loss.backward()
+    ref, _, _ = oracle.grad(scene, cams, st, ws)
+    for k in R.PARAM_KEYS:
+        t = getattr(g, k)
+        if t is None:
+            continue
+        e = rel_err(np_(t.grad), ref[k])
+        assert e <= GRAD_RTOL, (k, e)
+
+
+def batched_case(n=4000):
+    scene = synth.blob_scene(n, 8, 9, log_scale=(-3.0, 0.5))
+    sizes = [(40, 26), (80, 52), (80, 52), (160, 104)]
+    cams = synth.ring_cameras(len(sizes), sizes)
+    targets = synth.target_images(17, sizes)
+    return scene, cams, targets, settings_for(eps=(0.5, 0.5))
+
+
+@pytest.mark.parametrize("tile,ppt", [(16, 1), (8, 2), (32, 4)])
+def test_batched_train_step_matches_oracle(R, tile, ppt):
+    scene, cams, targets, st = batched_case()
+    st.tile = tile
+    rast = make_rast(R, st, ppt=ppt)
+    g = gpu_scene(R, scene)
+    tg = [torch.from_numpy(t).cuda() for t in targets]
+    grads = rast.alloc_grads(g)
+    stats = rast.alloc_stats(g.n)
+    loss = torch.zeros(1, device="cuda")
+    images = [torch.empty((3, c.height, c.width), device="cuda") for c in cams]
+    rast.plan(g, cams)
+    rast.train_step_batched(g, cams, tg, grads, stats, loss, images=images)
+    rast.poll()
+    refs = [oracle.render(scene, c, st, margins=True) for c in cams]
+    for v in range(len(cams)):
+        m, excl = image_compare(np_(images[v]), refs[v]["image"], refs[v]["margin"])
+        assert m <= IMAGE_ATOL and excl < 0.05
+    ref_loss, dls = oracle.l1([r["image"] for r in refs], targets)
+    assert abs(float(loss.item()) - ref_loss) <= 1e-5 * abs(ref_loss)
+    ref, rstats, _ = oracle.grad(scene, cams, st, dls)
+    for k, t in grads.items():
+        e = rel_err(np_(t), ref[k])
+        assert e <= GRAD_RTOL, (k, e)
+    assert np.sum(np_(stats["vis_count"]) != rstats["count"]) <= 2
+
+
+def test_graph_replay_equals_direct_step(R):
+    scene, cams, targets, st = batched_case(3000)
+    rast = make_rast(R, st)
+    g = gpu_scene(R, scene)
+    tg = [torch.from_numpy(t).cuda() for t in targets]
+    rast.plan(g, cams)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        direct = rast.alloc_grads(g)
+        loss_d = torch.zeros(1, device="cuda")
+        rast.train_step_batched(g, cams, tg, direct, None, loss_d)
+        graphed = rast.alloc_grads(g)
+        loss_g = torch.zeros(1, device="cuda")
+        for _ in range(3):   # capture once, replay twice
+            rast.train_step_batched(g, cams, tg, graphed, None, loss_g, graph=True)
+    s.synchronize()
+    rast.poll()
+    assert abs(loss_d.item() - loss_g.item()) <= 1e-6 * abs(loss_d.item())
+    for k in direct:
+        np.testing.assert_allclose(np_(graphed[k]), np_(direct[k]), rtol=1e-4, atol=1e-7)
+
+
+def test_key_capacity_overflow_is_reported_then_recovered(R):
+    scene, cams, targets, st = batched_case(3000)
+    rast = make_rast(R, st, cap=64)
+    g = gpu_scene(R, scene)
+    tg = [torch.from_numpy(t).cuda() for t in targets]
+    grads = rast.alloc_grads(g)
+    loss = torch.zeros(1, device="cuda")
+    rast.train_step_batched(g, cams, tg, grads, None, loss)
+    from paper_2501_14534_gb300 import _binding as B
+    with pytest.raises(B.TgsError) as ei:
+        rast.poll()
+    assert ei.value.status == B.TGS_ERR_CAPACITY
+    K = rast.plan(g, cams)
+    assert K > 64
+    rast.train_step_batched(g, cams, tg, grads, None, loss)
+    rast.poll()
+
+
+# ------------------------------------------------------------------------------------
+# edge cases
+# ------------------------------------------------------------------------------------
+
+def test_empty_scene_and_all_culled(R):
+    st = settings_for()
+    rast = make_rast(R, st)
+    cam = synth.look_at_camera((0.0, -4.0, 0.0), 37, 21, focal=40.0)
+    empty = {k: (np.zeros((0,) + s, np.float32)) for k, s in
+             [("means", (3,)), ("log_scales", (3,)), ("quats", (4,)), ("opacity_logits", ()),
+              ("sh_dc", (3,)), ("sh_rest", (15, 3))]}
+    g = gpu_scene(R, empty)
+    out = rast.forward(g, [cam])[0]
+    assert np.all(np_(out["image"]) == 0.0) and np.all(np_(out["T_final"]) == 1.0)
+    # everything behind the camera
+    sc = synth.uniform_scene(500, 3)
+    sc["means"] = (sc["means"] * 0.5 + np.array([0.0, -9.0, 0.0], np.float32)).astype(np.float32)
+    g = gpu_scene(R, sc)
+    out = rast.forward(g, [cam], want_radii=True)[0]
+    assert np.all(np_(out["radii"]) == 0) and np.all(np_(out["image"]) == 0.0)
+    grads, _ = rast.backward(g, [cam], [out], [torch.ones((3, 21, 37), device="cuda")])
+    for t in grads.values():
+        assert torch.all(t == 0)
+
+
+def test_tiny_images_and_one_huge_gaussian(R):
+    st = settings_for()
+    rast = make_rast(R, st)
+    sc = synth.uniform_scene(1, 4)
+    sc["means"][:] = 0.0
+    sc["log_scales"][:] = -0.5
+    sc["opacity_logits"][:] = 1.0
+    g = gpu_scene(R, sc)
+    for (w, h) in [(1, 1), (3, 2), (130, 70)]:
+        cam = synth.look_at_camera((0.0, -4.0, 0.0), w, h, focal=max(w, h))
+        out = rast.forward(g, [cam])[0]
+        ref = oracle.render(sc, cam, st, margins=True)
+        m, excl = image_compare(np_(out["image"]), ref["image"], ref["margin"])
+        assert m <= IMAGE_ATOL
+
+
+def test_non_finite_parameters_are_culled(R):
+    scene, cams, st = masked_case(500, ((48, 40, 0.5),))
+    scene["means"][::7, 1] = np.nan
+    scene["log_scales"][3::11, 0] = np.inf
+    scene["quats"][5::13] = 0.0
+    rast = make_rast(R, st)
+    g = gpu_scene(R, scene)
+    out = rast.forward(g, cams, want_radii=True)[0]
+    img = np_(out["image"])
+    assert np.all(np.isfinite(img))
+    bad = np.zeros(500, bool)
+    bad[::7] = True
+    bad[3::11] = True
+    bad[5::13] = True
+    assert np.all(np_(out["radii"])[bad] == 0)
+    ref = oracle.render(scene, cams[0], st, margins=True)
+    m, _ = image_compare(img, ref["image"], ref["margin"])
+    assert m <= IMAGE_ATOL
