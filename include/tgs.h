@@ -74,6 +74,7 @@ typedef int32_t tgs_status;
 #define TGS_ERR_TIMEOUT 4       /* a bounded device wait ran out; the results are invalid */
 #define TGS_ERR_OOM 5           /* device memory for the scratch arena could not be had */
 #define TGS_ERR_NOT_SUPPORTED 6 /* e.g. a tile size or launch shape that is not compiled */
+#define TGS_ERR_SCRATCH_LIMIT 7 /* input larger than the fixed scratch of tgs_bin_noalloc */
 
 #define TGS_SUPPORT_BOX3 0      /* 3-sigma square box (3DGS) */
 #define TGS_SUPPORT_ALPHA 1     /* smallest box outside which a < 1/255 */
@@ -228,6 +229,34 @@ tgs_status tgs_preprocess_backward(tgs_ctx *ctx, const tgs_gaussians *g, const t
                                    int32_t V, const float *splat_grads, const int32_t *radii,
                                    const tgs_grads *grads, const tgs_stats *stats,
                                    uint32_t flags, tgs_stream stream);
+
+/* --- binning without any device allocation ------------------------------------------ */
+
+/* Limits of tgs_bin_noalloc: (view, Gaussian) records (n * V) and (Gaussian, tile) keys. */
+#define TGS_NOALLOC_MAX_RECORDS 131072
+#define TGS_NOALLOC_MAX_KEYS 524288
+
+/* The same binning as tgs_bin -- same outputs, bit for bit -- for callers that cannot call
+   cudaMalloc: a host application that hands all device memory to its own allocator or
+   memory pool, a real-time loop that must not pay for an allocation, or code under a fixed
+   device-memory budget. The paper has no counterpart; this is a deployment variant.
+   It needs no tgs_ctx and allocates nothing. Its scratch is one fixed array of about 12.2 MB
+   of device memory that is part of the library image, so every GPU that loads libtgs holds
+   it until the process exits. The caller still allocates every output: sorted_ids
+   [capacity], sorted_keys [capacity] (or NULL) and ranges [tiles,2]. tile is 8, 16 or 32.
+   Limits: n * V <= TGS_NOALLOC_MAX_RECORDS, else TGS_ERR_SCRATCH_LIMIT without launching
+   anything; K <= TGS_NOALLOC_MAX_KEYS, else TGS_ERR_SCRATCH_LIMIT after counting the keys
+   (*K_out is set); K > capacity gives TGS_ERR_CAPACITY (*K_out is set).
+   The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+   once per device, under a lock) and caches it; make that first call before any stream
+   capture. Like tgs_bin it synchronises the stream once to read K.
+   All calls share the one array, which keeps the previous call's contents (the call clears
+   what must start at zero). Calls that overlap on the GPU -- on two streams, or from two
+   host threads -- race on it and give wrong results: serialise them. */
+tgs_status tgs_bin_noalloc(const float *splats, const int32_t *radii, int64_t n,
+                           const tgs_camera *cams, int32_t V, int32_t tile, uint32_t *sorted_ids,
+                           uint64_t *sorted_keys, uint32_t *ranges, int64_t capacity,
+                           int64_t *K_out, tgs_stream stream);
 
 /* --- measurement ------------------------------------------------------------------------ */
 

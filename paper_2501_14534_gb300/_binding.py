@@ -16,6 +16,9 @@ TGS_ERR_CAPACITY = 3
 TGS_ERR_TIMEOUT = 4
 TGS_ERR_OOM = 5
 TGS_ERR_NOT_SUPPORTED = 6
+TGS_ERR_SCRATCH_LIMIT = 7
+TGS_NOALLOC_MAX_RECORDS = 131072
+TGS_NOALLOC_MAX_KEYS = 524288
 TGS_SUPPORT_BOX3 = 0
 TGS_SUPPORT_ALPHA = 1
 TGS_MAX_VIEWS = 64
@@ -96,6 +99,8 @@ SIGNATURES = {
                                        _vp, _vp]),
     "tgs_preprocess_backward": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _vp, _vp, _gradp,
                                             _statp, C.c_uint32, _vp]),
+    "tgs_bin_noalloc": (C.c_int32, [_vp, _vp, C.c_int64, _camp, C.c_int32, C.c_int32, _vp, _vp,
+                                    _vp, C.c_int64, C.POINTER(C.c_int64), _vp]),
     "tgs_set_profiling": (C.c_int32, [_ctx_p, C.c_int32]),
     "tgs_stage_times": (C.c_int32, [_ctx_p, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),
     "tgs_stage_name": (C.c_char_p, [_ctx_p, C.c_int32]),

@@ -346,6 +346,7 @@ const char *tgs_status_string(tgs_status s) {
         case TGS_ERR_TIMEOUT: return "bounded device wait ran out";
         case TGS_ERR_OOM: return "out of device memory";
         case TGS_ERR_NOT_SUPPORTED: return "not supported";
+        case TGS_ERR_SCRATCH_LIMIT: return "input exceeds the fixed scratch of tgs_bin_noalloc";
         default: return "unknown status";
     }
 }
