@@ -270,6 +270,23 @@ def main():
     value = V * world / (ms_step / 1000.0)
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
 
+    # ---- A/B: the same step with separate forward, loss and backward kernels ----
+    rast.set_profiling(False)
+    unfused = None
+    try:
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                rast.train_step_batched(g, cams, targets, grads, stats, loss, graph=True, fused=False)
+            u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            u0.record(stream)
+            for _ in range(3):
+                rast.train_step_batched(g, cams, targets, grads, stats, loss, graph=True, fused=False)
+            u1.record(stream)
+        stream.synchronize()
+        unfused = V * world / (u0.elapsed_time(u1) / 3 / 1000.0)
+    except Exception as e:  # reported, not fatal
+        print(f"[bench] unfused A/B failed: {e}", file=sys.stderr)
+
     # ---- e2e: inputs from pinned host memory each step, loss read back ----
     host = {k: t.detach().cpu().pin_memory() for k, t in g.params().items()}
     host_t = [t.cpu().pin_memory() for t in targets]
@@ -344,6 +361,8 @@ def main():
     bytes_pre = n * 252 + V * n * (48 + 4 + 4 + 4 + 48)
     bytes_pbwd = n * (252 + 252 + 12 * 2) + V * n * (48 + 4)
     work = {
+        "fused_blend": ("alu", (P_fwd * PAIR_OPS_FWD + P_bwd * PAIR_OPS_BWD) / 1e12, ALU_PEAK_TOPS,
+                        "Tops/s"),
         "preprocess": ("hbm", bytes_pre / 1e9, hbm_gbs, "GB/s"),
         "preprocess_backward": ("hbm", bytes_pbwd / 1e9, hbm_gbs, "GB/s"),
         "blend_forward": ("alu", P_fwd * PAIR_OPS_FWD / 1e12, ALU_PEAK_TOPS, "Tops/s"),
@@ -376,6 +395,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms},
             "plain_views_per_s": plain_vps, "render_fps": render_fps,
+            "unfused_views_per_s": unfused,
             "speedup_vs_plain": value / world / plain_vps,
             "stage_ms": stage_ms, "pairs": {"forward": P_fwd, "backward": P_bwd},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),

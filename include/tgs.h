@@ -85,6 +85,7 @@ typedef int32_t tgs_status;
 #define TGS_ACCUMULATE 1u       /* add parameter gradients into the outputs instead of overwriting */
 #define TGS_NO_SH_REST_GRAD 2u  /* skip dL/d sh_rest (SH rest bands updated every 16 steps) */
 #define TGS_USE_GRAPH 4u        /* batched step: replay a captured CUDA graph when arguments repeat */
+#define TGS_UNFUSED 8u          /* batched step: separate forward, loss and backward kernels (A/B) */
 
 typedef struct tgs_ctx tgs_ctx;
 typedef void *tgs_stream; /* a cudaStream_t; NULL is the legacy default stream */
@@ -185,8 +186,9 @@ tgs_status tgs_l1_loss(const float *image, const float *target, int64_t count, f
 tgs_status tgs_plan(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
                     double headroom, int64_t *keys_out);
 /* One training step over V views of any sizes: preprocess of all views, one key sort, a
-   persistent fused forward + L1 loss + backward over (view, tile) work items heaviest first,
-   and the preprocess backward. loss_out (device float) = mean over views of mean |C - t|.
+   persistent fused forward + L1 loss + backward over (view, tile) work items heaviest first
+   (TGS_UNFUSED: one forward launch, V loss launches and one backward launch instead), and
+   the preprocess backward. loss_out (device float) = mean over views of mean |C - t|.
    images (optional, host array of V device pointers) receives the rendered views.
    Never synchronises; with TGS_USE_GRAPH the whole step is captured once into a CUDA graph
    and replayed while g, cams, targets, images, grads, stats and loss_out are unchanged.

@@ -26,6 +26,7 @@ TGS_MAX_STAGES = 8
 TGS_ACCUMULATE = 1
 TGS_NO_SH_REST_GRAD = 2
 TGS_USE_GRAPH = 4
+TGS_UNFUSED = 8
 
 _fp = C.POINTER(C.c_float)
 _vp = C.c_void_p

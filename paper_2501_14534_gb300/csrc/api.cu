@@ -34,7 +34,7 @@ struct tgs_ctx {
     int device = 0;
     // scratch arena
     Buf splats, radii, tt, dbits, pos, ck0, cv0, ck1, cv1, offsets, tk0, tv0, tk1, tv1, ranges,
-        hist, partials, sgrads, counts, status, pixstate, dimg, images, keys64;
+        hist, partials, sgrads, counts, status, pixstate, dimg, images, items;
     uint32_t *h_counts = nullptr;   // pinned host copy of (visible, K)
     // binning kept from the last plain forward
     bool state_valid = false;
@@ -383,7 +383,7 @@ void tgs_destroy(tgs_ctx *c) {
     Buf *bufs[] = {&c->splats, &c->radii, &c->tt, &c->dbits, &c->pos, &c->ck0, &c->cv0, &c->ck1,
                    &c->cv1, &c->offsets, &c->tk0, &c->tv0, &c->tk1, &c->tv1, &c->ranges, &c->hist,
                    &c->partials, &c->sgrads, &c->counts, &c->status, &c->pixstate, &c->dimg,
-                   &c->images, &c->keys64};
+                   &c->images, &c->items};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_counts) cudaFreeHost(c->h_counts);
@@ -683,25 +683,41 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
     uint32_t *sorted = nullptr;
     bin_front(c, nt, &sorted, st);
     uint32_t *ids = bin_back(c, nt, n, sorted, cb, cap, st);
-    mark(c, 2, "blend_forward", st);
     PixPtrs px = pix_for(outs, V, dls);
-    launch_blend_forward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
-                         c->cfg.bg, st);
-    mark(c, 3, "l1_loss", st);
+    for (int v = 0; v < V; v++) px.target[v] = targets[v];
     if (loss_out) TGS_CHECK(cudaMemsetAsync(loss_out, 0, sizeof(float), st));
-    for (int v = 0; v < V; v++) {
-        const int64_t cnt = 3 * (int64_t)cams[v].width * cams[v].height;
-        launch_l1(outs[v].image, targets[v], cnt, (float)(1.0 / ((double)cnt * V)), loss_out,
-                  const_cast<float *>(dls[v]), st);
+    int stage = 2;
+    if (flags & TGS_UNFUSED) {
+        mark(c, stage++, "blend_forward", st);
+        launch_blend_forward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
+                             c->cfg.bg, st);
+        mark(c, stage++, "l1_loss", st);
+        for (int v = 0; v < V; v++) {
+            const int64_t cnt = 3 * (int64_t)cams[v].width * cams[v].height;
+            launch_l1(outs[v].image, targets[v], cnt, (float)(1.0 / ((double)cnt * V)), loss_out,
+                      const_cast<float *>(dls[v]), st);
+        }
+        mark(c, stage++, "blend_backward", st);
+        launch_blend_backward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
+                              c->cfg.bg, as<float>(c->sgrads), st);
+    } else {
+        mark(c, stage++, "item_order", st);
+        uint32_t *it = as<uint32_t>(c->items);
+        const size_t T = (size_t)cb.total_tiles;
+        uint32_t *order = nullptr;
+        build_item_order(as<uint2>(c->ranges), cb.total_tiles, it, it + T, it + 2 * T, it + 3 * T, &order,
+                         as<uint32_t>(c->hist), as<uint32_t>(c->partials), st);
+        int *counter = reinterpret_cast<int *>(as<uint32_t>(c->counts) + 2);
+        TGS_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), st));
+        mark(c, stage++, "fused_blend", st);
+        launch_fused_l1(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), order, counter,
+                        cb, px, c->cfg.bg, as<float>(c->sgrads), loss_out, st);
     }
-    mark(c, 4, "blend_backward", st);
-    launch_blend_backward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
-                          c->cfg.bg, as<float>(c->sgrads), st);
-    mark(c, 5, "preprocess_backward", st);
+    mark(c, stage++, "preprocess_backward", st);
     GradPtrs o = grad_ptrs(grads, stats, (flags & TGS_ACCUMULATE) ? 1 : 0);
     launch_preprocess_backward(gp, cb, as<float4>(c->sgrads), as<int32_t>(c->radii), o,
                                (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, st);
-    mark(c, 6, "end", st);
+    mark(c, stage, "end", st);
     c->kernels_per_step = g_launches - launches0;
     return last_error();
 }
@@ -730,6 +746,7 @@ tgs_status tgs_train_step_batched(tgs_ctx *c, const tgs_gaussians *g, const tgs_
     TGS_TRY(ensure(c->images, sizeof(float) * 3 * pix, st));
     TGS_TRY(ensure(c->dimg, sizeof(float) * 3 * pix, st));
     TGS_TRY(ensure(c->pixstate, sizeof(float) * 2 * pix, st));
+    TGS_TRY(ensure(c->items, sizeof(uint32_t) * 4 * (size_t)std::max(cb.total_tiles, 1), st));
     c->state_valid = false;
 
     if (!(flags & TGS_USE_GRAPH) || st == nullptr || capturing(st))

@@ -1,0 +1,379 @@
+// Per-tile forward and backward blending (Eq. 2 of the paper), as device functions shared by
+// the one-CTA-per-tile kernels (blend.cu) and the persistent fused kernel (fused.cu).
+//
+// Pixel layout: each warp owns a compact block of BW x BH pixels of the tile (PPT pixels per
+// lane), so that a splat whose pixel rect misses a warp's block is skipped by that warp with
+// one warp-uniform test (sub-tile skipping), and a splat that covers the whole block needs no
+// per-pixel rect test.
+//
+// The forward and the backward evaluate each fragment with the same function on the same
+// staged values, so their skip decisions (alpha < 1/255, the rect) agree bit for bit.
+#pragma once
+
+#include "tgs_internal.cuh"
+
+namespace tgs {
+
+template <int TILE, int PPT>
+struct BlendLayout {
+    static constexpr int NT = TILE * TILE / PPT;  // threads per CTA
+    static constexpr int NW = NT / 32;            // warps per CTA
+    static constexpr int BW = (PPT == 4) ? 16 : 8;  // warp block width
+    static constexpr int BH = 32 * PPT / BW;        // warp block height
+    static constexpr int WX = TILE / BW;            // warp blocks per tile row
+    static constexpr int RS = 32 / BW;              // rows covered by one pass of 32 lanes
+    static_assert(NT % 32 == 0, "at least one warp");
+    static_assert((TILE / BW) * (TILE / BH) == NW, "warp blocks tile the tile");
+};
+
+template <int NT>
+struct BlendSmem {
+    float4 a[NT];     // mean2d x, y; scaled conic A, B
+    float4 b[NT];     // scaled conic C; opacity; r, g
+    float c[NT];      // b
+    int4 rect[NT];    // inclusive pixel rect x_lo, x_hi, y_lo, y_hi
+    uint32_t id[NT];  // splat record index
+    uint32_t hit[NT]; // bit w: the rect meets warp w's pixel block
+    uint32_t cov[NT]; // bit w: the rect covers warp w's pixel block
+    int maxlast;
+};
+
+// Stage one splat record: conic pre-scaled so that alpha = o * 2^q with
+// q = log2(e) * power, power = -1/2 (a dx^2 + c dy^2) - b dx dy.
+// Bits of the warp blocks (WX x WY of BW x BH pixels, row-major) of the tile at (tx0, ty0)
+// that the inclusive rect [xl, xh] x [yl, yh] meets, and those it covers entirely.
+template <int TILE, int PPT>
+__device__ __forceinline__ void block_masks(int xl, int xh, int yl, int yh, int tx0, int ty0,
+                                            uint32_t &hit, uint32_t &cov) {
+    using L = BlendLayout<TILE, PPT>;
+    constexpr int WX = L::WX, WY = TILE / L::BH;
+    hit = cov = 0u;
+    const int x0 = xl - tx0, x1 = xh - tx0, y0 = yl - ty0, y1 = yh - ty0;  // tile-local
+    if (x1 < 0 || y1 < 0 || x0 > TILE - 1 || y0 > TILE - 1) return;
+    const int cl = max(x0, 0) / L::BW, ch = min(x1, TILE - 1) / L::BW;
+    const int rl = max(y0, 0) / L::BH, rh = min(y1, TILE - 1) / L::BH;
+    const uint32_t cols = ((1u << (ch - cl + 1)) - 1u) << cl;
+    // fully covered columns / rows: block start >= x0 and block end <= x1
+    const int ccl = x0 <= 0 ? 0 : (x0 + L::BW - 1) / L::BW;
+    const int cch = (x1 + 1) / L::BW - 1;
+    const int crl = y0 <= 0 ? 0 : (y0 + L::BH - 1) / L::BH;
+    const int crh = (y1 + 1) / L::BH - 1;
+    const uint32_t ccols = (cch >= ccl) ? (((1u << (min(cch, WX - 1) - ccl + 1)) - 1u) << ccl) : 0u;
+#pragma unroll
+    for (int r = 0; r < WY; r++) {
+        if (r >= rl && r <= rh) hit |= cols << (r * WX);
+        if (r >= crl && r <= crh) cov |= ccols << (r * WX);
+    }
+}
+
+template <int TILE, int PPT, int NT>
+__device__ __forceinline__ void stage_splat(BlendSmem<NT> &sm, int slot,
+                                            const float4 *__restrict__ splats, uint32_t id,
+                                            int tx0, int ty0) {
+    const float4 s0 = __ldg(splats + 3 * (size_t)id);
+    const float4 s1 = __ldg(splats + 3 * (size_t)id + 1);
+    const float4 s2 = __ldg(splats + 3 * (size_t)id + 2);
+    sm.a[slot] = make_float4(s0.x, s0.y, __fmul_rn(-0.5f * kLog2e, s0.z), __fmul_rn(-kLog2e, s0.w));
+    sm.b[slot] = make_float4(__fmul_rn(-0.5f * kLog2e, s1.x), s1.y, s1.z, s1.w);
+    sm.c[slot] = s2.x;
+    const uint32_t rx = __float_as_uint(s2.y), ry = __float_as_uint(s2.z);
+    const int4 r = make_int4((int)(rx & 0xFFFFu), (int)(rx >> 16), (int)(ry & 0xFFFFu), (int)(ry >> 16));
+    sm.rect[slot] = r;
+    sm.id[slot] = id;
+    uint32_t hit, cov;
+    block_masks<TILE, PPT>(r.x, r.y, r.z, r.w, tx0, ty0, hit, cov);
+    sm.hit[slot] = hit;
+    sm.cov[slot] = cov;
+}
+
+// Exponent of one fragment, with explicit roundings (no contraction choices left to the
+// compiler) so that every kernel computes the same bits.
+__device__ __forceinline__ float frag_q(float A, float Bq, float Cq, float dx, float dy) {
+    const float u = __fmaf_rn(A, dx, __fmul_rn(Bq, dy));
+    const float w = __fmul_rn(__fmul_rn(Cq, dy), dy);
+    return __fmaf_rn(dx, u, w);
+}
+
+__device__ __forceinline__ bool pix_in(const int4 &r, int x, int y) {
+    return (unsigned)(x - r.x) <= (unsigned)(r.y - r.x) && (unsigned)(y - r.z) <= (unsigned)(r.w - r.z);
+}
+
+// Pixels of this thread in tile (tx, ty).
+template <int TILE, int PPT>
+struct TilePixels {
+    int x[PPT], y[PPT];
+    float fx[PPT], fy[PPT];
+    bool inside[PPT];
+    int bx0, bx1, by0, by1;  // the warp's pixel block
+    int tx0, ty0;            // the tile's first pixel
+    uint32_t wbit;           // this warp's bit in the hit / cover masks
+
+    __device__ __forceinline__ void init(int tx, int ty, int W, int H) {
+        using L = BlendLayout<TILE, PPT>;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        tx0 = tx * TILE;
+        ty0 = ty * TILE;
+        wbit = 1u << w;
+        bx0 = tx * TILE + (w % L::WX) * L::BW;
+        by0 = ty * TILE + (w / L::WX) * L::BH;
+        bx1 = bx0 + L::BW - 1;
+        by1 = by0 + L::BH - 1;
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            x[k] = bx0 + lane % L::BW;
+            y[k] = by0 + lane / L::BW + k * L::RS;
+            fx[k] = (float)x[k];
+            fy[k] = (float)y[k];
+            inside[k] = x[k] < W && y[k] < H;
+        }
+    }
+};
+
+// Forward state of this thread's pixels.
+template <int PPT>
+struct FwdState {
+    float T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
+    int last[PPT], exam[PPT];
+    bool done[PPT];
+};
+
+// Front-to-back blend of one tile's list [rg.x, rg.y). On return every pixel holds its
+// colour sum, transmittance, last contributor (1-based list position, 0 if none) and the
+// number of list entries it examined.
+template <int TILE, int PPT>
+__device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
+                                             const float4 *__restrict__ splats,
+                                             const uint32_t *__restrict__ ids, uint2 rg,
+                                             const TilePixels<TILE, PPT> &P, FwdState<PPT> &S) {
+    constexpr int NT = TILE * TILE / PPT;
+    const unsigned full = 0xffffffffu;
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        S.T[k] = 1.f;
+        S.Cr[k] = S.Cg[k] = S.Cb[k] = 0.f;
+        S.last[k] = 0;
+        S.exam[k] = 0;
+        S.done[k] = !P.inside[k];
+    }
+    for (uint32_t base = rg.x; base < rg.y; base += NT) {
+        bool mine = true;
+#pragma unroll
+        for (int k = 0; k < PPT; k++) mine = mine && S.done[k];
+        if (__syncthreads_count(mine) == NT) break;
+        const uint32_t j = base + t;
+        if (j < rg.y) stage_splat<TILE, PPT>(sm, t, splats, __ldg(ids + j), P.tx0, P.ty0);
+        __syncthreads();
+        if (__all_sync(full, mine)) continue;  // this warp is finished
+        const int cnt = min((uint32_t)NT, rg.y - base);
+        const int pos0 = (int)(base - rg.x);
+        bool warp_done = false;
+        for (int c0 = 0; c0 < cnt && !warp_done; c0 += 32) {
+          // the splats of this chunk of 32 that meet this warp's pixel block, in list order
+          uint32_t bits = __ballot_sync(full, (c0 + (t & 31) < cnt) && (sm.hit[c0 + (t & 31)] & P.wbit));
+          while (bits) {
+            const int m = c0 + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const int4 r = sm.rect[m];
+            const bool cover = (sm.cov[m] & P.wbit) != 0u;
+            const float4 a = sm.a[m], b = sm.b[m];
+            const float cbl = sm.c[m];
+            bool fin = false;
+#pragma unroll
+            for (int k = 0; k < PPT; k++) {
+                if (S.done[k]) continue;
+                if (!cover && !pix_in(r, P.x[k], P.y[k])) continue;
+                const float dx = a.x - P.fx[k], dy = a.y - P.fy[k];
+                const float q = frag_q(a.z, a.w, b.x, dx, dy);
+                if (q > 0.f) continue;
+                const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, ex2_approx(q)));
+                if (alpha < kAlphaMin) continue;
+                const float tT = __fmul_rn(S.T[k], __fsub_rn(1.f, alpha));
+                if (tT < kTMin) {
+                    S.done[k] = true;
+                    S.exam[k] = pos0 + m + 1;
+                    fin = true;
+                    continue;
+                }
+                const float w = __fmul_rn(alpha, S.T[k]);
+                S.Cr[k] = __fmaf_rn(b.z, w, S.Cr[k]);
+                S.Cg[k] = __fmaf_rn(b.w, w, S.Cg[k]);
+                S.Cb[k] = __fmaf_rn(cbl, w, S.Cb[k]);
+                S.T[k] = tT;
+                S.last[k] = pos0 + m + 1;
+            }
+            if (__any_sync(full, fin)) {
+                bool all = true;
+#pragma unroll
+                for (int k = 0; k < PPT; k++) all = all && S.done[k];
+                if (__all_sync(full, all)) {
+                    warp_done = true;
+                    break;
+                }
+            }
+          }
+        }
+    }
+    const int len = (int)(rg.y - rg.x);
+#pragma unroll
+    for (int k = 0; k < PPT; k++)
+        if (P.inside[k] && S.exam[k] == 0) S.exam[k] = len;   // never stopped: saw the whole list
+}
+
+// Sums v[0..7] over the warp; afterwards lanes with (lane & 3) == 0 hold the total of
+// value (lane >> 2). Four levels of halving exchange instead of eight full butterflies.
+__device__ __forceinline__ void warp_transpose_reduce8(float v[8], int lane) {
+    const unsigned full = 0xffffffffu;
+    {
+        const bool up = lane & 16;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const float send = up ? v[i] : v[i + 4];
+            const float keep = up ? v[i + 4] : v[i];
+            v[i] = keep + __shfl_xor_sync(full, send, 16);
+        }
+    }
+    {
+        const bool up = lane & 8;
+#pragma unroll
+        for (int i = 0; i < 2; i++) {
+            const float send = up ? v[i] : v[i + 2];
+            const float keep = up ? v[i + 2] : v[i];
+            v[i] = keep + __shfl_xor_sync(full, send, 8);
+        }
+    }
+    {
+        const bool up = lane & 4;
+        const float send = up ? v[0] : v[1];
+        const float keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(full, send, 4);
+    }
+    v[0] += __shfl_xor_sync(full, v[0], 2);
+    v[0] += __shfl_xor_sync(full, v[0], 1);
+}
+
+__device__ __forceinline__ float warp_sum(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// What the backward needs per pixel.
+template <int PPT>
+struct BwdInput {
+    int last[PPT];   // 1-based list position of the last contributor, 0 = none
+    float Tfin[PPT]; // final transmittance
+    float dR[PPT], dG[PPT], dB[PPT];  // dL/d pixel colour
+};
+
+// Reverse walk of one tile's list from each pixel's last contributor. The transmittance in
+// front of fragment i is recovered as T_i = T_{i+1} / (1 - a_i) from T_final; the colour behind
+// fragment i is accumulated from the back. Per fragment the gradients of the pixels of a warp
+// are summed (transposed reduction) and added with one atomic per value per warp into the
+// splat gradient record: dL/d mean2d (2), dL/d conic a, b, c, dL/d opacity, dL/d rgb (3).
+template <int TILE, int PPT>
+__device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
+                                              const float4 *__restrict__ splats,
+                                              const uint32_t *__restrict__ ids, uint2 rg,
+                                              const TilePixels<TILE, PPT> &P, const BwdInput<PPT> &in,
+                                              float bg0, float bg1, float bg2,
+                                              float *__restrict__ sgrads) {
+    constexpr int NT = TILE * TILE / PPT;
+    const unsigned full = 0xffffffffu;
+    const int t = threadIdx.x, lane = t & 31;
+    float T[PPT], acR[PPT], acG[PPT], acB[PPT], la[PPT], lR[PPT], lG[PPT], lB[PPT], bgdot[PPT];
+    int mymax = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; k++) {
+        T[k] = in.Tfin[k];
+        acR[k] = acG[k] = acB[k] = 0.f;
+        la[k] = 0.f;
+        lR[k] = lG[k] = lB[k] = 0.f;
+        bgdot[k] = bg0 * in.dR[k] + bg1 * in.dG[k] + bg2 * in.dB[k];
+        mymax = max(mymax, in.last[k]);
+    }
+    const int wmax = __reduce_max_sync(full, mymax);
+    __syncthreads();  // smem of a previous use is free
+    if (t == 0) sm.maxlast = 0;
+    __syncthreads();
+    if (lane == 0) atomicMax(&sm.maxlast, wmax);
+    __syncthreads();
+    const uint32_t end = min(rg.y, rg.x + (uint32_t)sm.maxlast);
+
+    for (uint32_t bend = end; bend > rg.x;) {
+        const uint32_t bstart = (bend - rg.x > (uint32_t)NT) ? bend - NT : rg.x;
+        const int cnt = (int)(bend - bstart);
+        __syncthreads();
+        if (t < cnt)  // slot t holds list position bend-1-t
+            stage_splat<TILE, PPT>(sm, t, splats, __ldg(ids + bend - 1 - t), P.tx0, P.ty0);
+        __syncthreads();
+        const int top = (int)(bend - rg.x);   // 1-based position of slot 0
+        const int m0 = max(0, top - wmax);    // positions beyond this warp's last contributors
+        for (int c0 = (m0 / 32) * 32; c0 < cnt; c0 += 32) {
+          const int mi = c0 + lane;
+          uint32_t bits = __ballot_sync(full, mi >= m0 && mi < cnt && (sm.hit[mi] & P.wbit));
+          while (bits) {
+            const int m = c0 + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const int pos = top - m;
+            const int4 r = sm.rect[m];
+            const bool cover = (sm.cov[m] & P.wbit) != 0u;
+            const float4 a = sm.a[m], b = sm.b[m];
+            const float cbl = sm.c[m];
+            float g[9];
+#pragma unroll
+            for (int e = 0; e < 9; e++) g[e] = 0.f;
+            bool contrib = false;
+#pragma unroll
+            for (int k = 0; k < PPT; k++) {
+                if (pos > in.last[k]) continue;
+                if (!cover && !pix_in(r, P.x[k], P.y[k])) continue;
+                const float dx = a.x - P.fx[k], dy = a.y - P.fy[k];
+                const float q = frag_q(a.z, a.w, b.x, dx, dy);
+                if (q > 0.f) continue;
+                const float G = ex2_approx(q);
+                const float x = __fmul_rn(b.y, G);
+                const float alpha = fminf(kAlphaMax, x);
+                if (alpha < kAlphaMin) continue;
+                contrib = true;
+                const float inv = __fdividef(1.f, 1.f - alpha);
+                T[k] *= inv;                         // transmittance in front of this fragment
+                const float w = alpha * T[k];
+                g[6] = fmaf(w, in.dR[k], g[6]);
+                g[7] = fmaf(w, in.dG[k], g[7]);
+                g[8] = fmaf(w, in.dB[k], g[8]);
+                acR[k] = fmaf(la[k], lR[k] - acR[k], acR[k]);   // colour behind this fragment
+                acG[k] = fmaf(la[k], lG[k] - acG[k], acG[k]);
+                acB[k] = fmaf(la[k], lB[k] - acB[k], acB[k]);
+                float dLda = (b.z - acR[k]) * in.dR[k] + (b.w - acG[k]) * in.dG[k] + (cbl - acB[k]) * in.dB[k];
+                dLda = dLda * T[k] - in.Tfin[k] * inv * bgdot[k];
+                la[k] = alpha;
+                lR[k] = b.z;
+                lG[k] = b.w;
+                lB[k] = cbl;
+                if (x <= kAlphaMax) {
+                    // dL/dpower = dL/da * o G; -a dx - b dy = ln2 (2A dx + B dy) in the scaled conic
+                    const float dLdp = dLda * x;
+                    const float s = dLdp * kLn2;
+                    const float h = -0.5f * dLdp;
+                    g[5] = fmaf(dLda, G, g[5]);
+                    g[0] = fmaf(s, fmaf(2.f * a.z, dx, a.w * dy), g[0]);
+                    g[1] = fmaf(s, fmaf(2.f * b.x, dy, a.w * dx), g[1]);
+                    g[2] = fmaf(h * dx, dx, g[2]);
+                    g[3] = fmaf(-dLdp * dx, dy, g[3]);
+                    g[4] = fmaf(h * dy, dy, g[4]);
+                }
+            }
+            if (__ballot_sync(full, contrib) == 0u) continue;
+            float *dst = sgrads + 12 * (size_t)sm.id[m];
+            warp_transpose_reduce8(g, lane);
+            const float gb = warp_sum(g[8]);
+            if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), g[0]);
+            if (lane == 0) atomicAdd(dst + 8, gb);
+          }
+        }
+        bend = bstart;
+    }
+}
+
+}  // namespace tgs

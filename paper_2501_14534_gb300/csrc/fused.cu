@@ -1,4 +1,161 @@
-// Persistent fused forward + L1 + backward over (view, tile) work items (batched path).
-#include "tgs_internal.cuh"
+// Persistent fused forward + L1 loss + backward over (view, tile) work items.
+//
+// The batched training step renders many views of any sizes with one launch: a grid of
+// (SM count x resident CTAs per SM) CTAs takes work items -- one (view, tile) each -- from an
+// atomic counter, heaviest first, and for each item runs the forward blend, the L1 loss and
+// its gradient (pixel-local, so it needs nothing from other tiles), and the backward blend,
+// keeping every pixel's state in registers between the two passes.
+//
+// Heaviest first: items are ordered by a log-scale key of their list length (8 buckets per
+// doubling), descending, with one stable 8-bit radix pass; ties keep tile order.
+#include <mutex>
 
-namespace tgs {}  // namespace tgs
+#include "blend_common.cuh"
+
+namespace tgs {
+namespace {
+
+__global__ void k_item_keys(const uint2 *__restrict__ ranges, int n, uint32_t *__restrict__ keys,
+                            uint32_t *__restrict__ vals) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint2 r = ranges[i];
+    const uint32_t len = r.y - r.x;
+    uint32_t key = 255u;  // empty tiles last
+    if (len > 0u) {
+        const int e = 31 - __clz(len);                      // floor(log2 len)
+        const uint32_t frac = e >= 3 ? (len >> (e - 3)) & 7u : (len << (3 - e)) & 7u;
+        const uint32_t lg8 = min(254u, (uint32_t)(e * 8) + frac);
+        key = 254u - lg8;                                   // descending length
+    }
+    keys[i] = key;
+    vals[i] = (uint32_t)i;
+}
+
+template <int TILE, int PPT>
+__global__ void __launch_bounds__(TILE * TILE / PPT)
+k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
+           const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, int n_items,
+           int *__restrict__ counter, const __grid_constant__ CamBatch cb,
+           const __grid_constant__ PixPtrs px, float bg0, float bg1, float bg2,
+           float *__restrict__ sgrads, float *__restrict__ loss) {
+    constexpr int NT = TILE * TILE / PPT;
+    constexpr int NW = NT / 32;
+    __shared__ BlendSmem<NT> sm;
+    __shared__ int s_item;
+    __shared__ float s_loss[NW];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    for (;;) {
+        __syncthreads();
+        if (t == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int gt = (int)order[it];
+        const int v = view_of_tile(cb, gt);
+        const DevCam &cam = cb.c[v];
+        const int lt = gt - cam.tile_offset;
+        TilePixels<TILE, PPT> P;
+        P.init(lt % cam.gx, lt / cam.gx, cam.W, cam.H);
+        const uint2 rg = ranges[gt];
+        FwdState<PPT> S;
+        tile_forward<TILE, PPT>(sm, splats, ids, rg, P, S);
+
+        // L1 loss: L = mean over views of mean over 3HW |C - target|; dL/dC = sign / (3HWV)
+        const int HW = cam.W * cam.H;
+        const float scale = 1.f / (3.f * (float)HW * (float)cb.V);
+        const float *tg = px.target[v];
+        float *img = px.image[v];
+        BwdInput<PPT> in;
+        float lsum = 0.f;
+#pragma unroll
+        for (int k = 0; k < PPT; k++) {
+            in.last[k] = S.last[k];
+            in.Tfin[k] = S.T[k];
+            in.dR[k] = in.dG[k] = in.dB[k] = 0.f;
+            if (!P.inside[k]) continue;
+            const int pix = P.y[k] * cam.W + P.x[k];
+            const float cr = S.Cr[k] + S.T[k] * bg0;
+            const float cg = S.Cg[k] + S.T[k] * bg1;
+            const float cbv = S.Cb[k] + S.T[k] * bg2;
+            if (img) {
+                img[pix] = cr;
+                img[HW + pix] = cg;
+                img[2 * HW + pix] = cbv;
+            }
+            const float er = cr - tg[pix], eg = cg - tg[HW + pix], eb = cbv - tg[2 * HW + pix];
+            lsum += fabsf(er) + fabsf(eg) + fabsf(eb);
+            in.dR[k] = er > 0.f ? scale : (er < 0.f ? -scale : 0.f);
+            in.dG[k] = eg > 0.f ? scale : (eg < 0.f ? -scale : 0.f);
+            in.dB[k] = eb > 0.f ? scale : (eb < 0.f ? -scale : 0.f);
+        }
+        lsum = warp_sum(lsum);
+        if (lane == 0) s_loss[w] = lsum;
+        tile_backward<TILE, PPT>(sm, splats, ids, rg, P, in, bg0, bg1, bg2, sgrads);
+        // s_loss was written before the barriers inside tile_backward
+        if (t == 0 && loss) {
+            float x = 0.f;
+#pragma unroll
+            for (int q = 0; q < NW; q++) x += s_loss[q];
+            atomicAdd(loss, x * scale);
+        }
+    }
+}
+
+template <int TILE, int PPT>
+int fused_blocks_per_sm() {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_l1<TILE, PPT>, TILE * TILE / PPT, 0) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        b = 1;
+    }
+    return b < 1 ? 1 : b;
+}
+
+template <int TILE, int PPT>
+void fused_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const uint32_t *order,
+                  int *counter, const CamBatch &cb, const PixPtrs &px, const float *bg, float *sgrads,
+                  float *loss, cudaStream_t st) {
+    static std::once_flag once;
+    static int per_sm = 1, sms = 1;
+    std::call_once(once, [] {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        per_sm = fused_blocks_per_sm<TILE, PPT>();
+    });
+    int grid = sms * per_sm;
+    if (grid > cb.total_tiles) grid = cb.total_tiles;
+    if (grid < 1) grid = 1;
+    count_launch();
+    k_fused_l1<TILE, PPT><<<grid, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, order, cb.total_tiles, counter,
+                                                              cb, px, bg[0], bg[1], bg[2], sgrads, loss);
+}
+
+}  // namespace
+
+void build_item_order(const uint2 *ranges, int total_tiles, uint32_t *k0, uint32_t *v0, uint32_t *k1,
+                      uint32_t *v1, uint32_t **order, uint32_t *hist, uint32_t *partials, cudaStream_t st) {
+    if (total_tiles <= 0) return;
+    count_launch();
+    k_item_keys<<<(total_tiles + 255) / 256, 256, 0, st>>>(ranges, total_tiles, k0, v0);
+    uint32_t *k = k0, *v = v0;
+    radix_sort_pairs(k, v, k1, v1, nullptr, total_tiles, 0, 8, hist, partials, st);
+    *order = v;
+}
+
+void launch_fused_l1(int tile, int ppt, const float4 *splats, const uint32_t *ids, const uint2 *ranges,
+                     const uint32_t *order, int *counter, const CamBatch &cb, const PixPtrs &px,
+                     const float *bg, float *sgrads, float *loss, cudaStream_t st) {
+    if (cb.total_tiles <= 0) return;
+    if (tile == 8 && ppt == 1) fused_launch<8, 1>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
+    else if (tile == 8 && ppt == 2) fused_launch<8, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
+    else if (tile == 16 && ppt == 1) fused_launch<16, 1>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
+    else if (tile == 16 && ppt == 2) fused_launch<16, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
+    else if (tile == 16 && ppt == 4) fused_launch<16, 4>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
+    else if (tile == 32 && ppt == 2) fused_launch<32, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
+    else if (tile == 32 && ppt == 4) fused_launch<32, 4>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
+}
+
+}  // namespace tgs

@@ -140,4 +140,11 @@ void launch_blend_backward(int tile, int ppt, const float4 *splats, const uint32
 void launch_l1(const float *img, const float *tgt, int64_t count, float scale, float *loss,
                float *grad, cudaStream_t st);
 
+// fused.cu
+void build_item_order(const uint2 *ranges, int total_tiles, uint32_t *k0, uint32_t *v0, uint32_t *k1,
+                      uint32_t *v1, uint32_t **order, uint32_t *hist, uint32_t *partials, cudaStream_t st);
+void launch_fused_l1(int tile, int ppt, const float4 *splats, const uint32_t *ids, const uint2 *ranges,
+                     const uint32_t *order, int *counter, const CamBatch &cb, const PixPtrs &px,
+                     const float *bg, float *sgrads, float *loss, cudaStream_t st);
+
 }  // namespace tgs

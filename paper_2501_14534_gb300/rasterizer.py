@@ -304,9 +304,9 @@ class Rasterizer:
 
     def train_step_batched(self, g: Gaussians, cams, targets, grads, stats=None, loss=None,
                            images=None, graph=False, accumulate=False, no_sh_rest=False,
-                           cams_struct=None):
+                           cams_struct=None, fused=True):
         flags = ((B.TGS_USE_GRAPH if graph else 0) | (B.TGS_ACCUMULATE if accumulate else 0) |
-                 (B.TGS_NO_SH_REST_GRAD if no_sh_rest else 0))
+                 (B.TGS_NO_SH_REST_GRAD if no_sh_rest else 0) | (0 if fused else B.TGS_UNFUSED))
         camarr = cams_struct if cams_struct is not None else cameras_array(cams)
         B.check(B.lib.tgs_train_step_batched(
             self._h, C.byref(g.struct()), camarr, len(camarr), _ptr_array(targets),

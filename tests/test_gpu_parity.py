@@ -314,8 +314,10 @@ def batched_case(n=4000):
     return scene, cams, targets, settings_for(eps=(0.5, 0.5))
 
 
-@pytest.mark.parametrize("tile,ppt", [(16, 1), (8, 2), (32, 4)])
-def test_batched_train_step_matches_oracle(R, tile, ppt):
+@pytest.mark.parametrize("tile,ppt,fused", [(16, 1, True), (8, 2, True), (32, 4, True),
+                                            (16, 2, True), (32, 2, True), (16, 4, False),
+                                            (32, 4, False)])
+def test_batched_train_step_matches_oracle(R, tile, ppt, fused):
     scene, cams, targets, st = batched_case()
     st.tile = tile
     rast = make_rast(R, st, ppt=ppt)
@@ -326,7 +328,7 @@ def test_batched_train_step_matches_oracle(R, tile, ppt):
     loss = torch.zeros(1, device="cuda")
     images = [torch.empty((3, c.height, c.width), device="cuda") for c in cams]
     rast.plan(g, cams)
-    rast.train_step_batched(g, cams, tg, grads, stats, loss, images=images)
+    rast.train_step_batched(g, cams, tg, grads, stats, loss, images=images, fused=fused)
     rast.poll()
     refs = [oracle.render(scene, c, st, margins=True) for c in cams]
     for v in range(len(cams)):
