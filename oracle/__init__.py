@@ -83,9 +83,10 @@ def _declare(L):
                            C.c_uint32, _u64p, _u32p, _u32p]
     L.orc_keys.restype = C.c_int64
     L.orc_blend.argtypes = [C.c_int64, C.POINTER(_Splats), C.c_int, C.c_int, C.c_int, _dp,
-                            C.c_int, C.c_int, C.c_int, _u8p, _dp, _dp, _i32p, _i32p, _i32p, _dp]
+                            C.c_int, C.c_int, C.c_int, _u8p, _u32p, _u32p, _dp, _dp, _i32p,
+                            _i32p, _i32p, _dp]
     L.orc_blend_backward.argtypes = [C.c_int64, C.POINTER(_Splats), C.c_int, C.c_int, C.c_int,
-                                     _dp, _dp, C.c_int, _u8p, _dp]
+                                     _dp, _dp, C.c_int, _u8p, _u32p, _u32p, _dp]
     L.orc_preprocess_backward.argtypes = [C.POINTER(_Params), _dp, _dp, _dp, C.POINTER(_Grads),
                                           _dp, _i32p, _i32p]
     L.orc_l1.argtypes = [C.c_int64, _dp, _dp, C.c_double, _dp]
@@ -211,12 +212,21 @@ def _mask(tile_mask):
     return None if tile_mask is None else np.ascontiguousarray(tile_mask, dtype=np.uint8)
 
 
+def _lists(lists):
+    if lists is None:
+        return C.cast(None, _u32p), C.cast(None, _u32p), None
+    vals = np.ascontiguousarray(lists[0], dtype=np.uint32)
+    ranges = np.ascontiguousarray(lists[1], dtype=np.uint32)
+    return _ptr(vals, _u32p), _ptr(ranges, _u32p), (vals, ranges)
+
+
 def blend(splats, W, H, tile=16, bg=(0.0, 0.0, 0.0), brute=False, nthreads=1,
-          margins=False, depth_margin=False, tile_mask=None):
+          margins=False, depth_margin=False, tile_mask=None, lists=None):
     """Front-to-back blending of one view (Eq. 2). Returns image [3,H,W], T_final, last
     (1-based position in the tile list of the last contributor, 0 if none), n_contrib,
     n_examined and, if requested, the per-pixel decision margin. ``tile_mask`` (one byte per
-    tile, row-major) restricts the work to the tiles marked 1; other pixels stay 0."""
+    tile, row-major) restricts the work to the tiles marked 1; other pixels stay 0. ``lists``
+    = (values, ranges) from ``keys`` of the same records skips building the tile lists."""
     n = splats["radius"].shape[0]
     out = dict(image=np.zeros((3, H, W)), T_final=np.zeros((H, W)),
                last=np.zeros((H, W), np.int32), n_contrib=np.zeros((H, W), np.int32),
@@ -225,8 +235,9 @@ def blend(splats, W, H, tile=16, bg=(0.0, 0.0, 0.0), brute=False, nthreads=1,
         out["margin"] = np.zeros((H, W))
     bgv = np.asarray(bg, dtype=np.float64)
     tm = _mask(tile_mask)
+    lv, lr, _keep = _lists(lists)
     lib().orc_blend(n, C.byref(_splats_struct(splats)), W, H, tile, _ptr(bgv), int(brute),
-                    nthreads, int(depth_margin), _ptr(tm, _u8p), _ptr(out["image"]),
+                    nthreads, int(depth_margin), _ptr(tm, _u8p), lv, lr, _ptr(out["image"]),
                     _ptr(out["T_final"]),
                     _ptr(out["last"], _i32p), _ptr(out["n_contrib"], _i32p),
                     _ptr(out["n_examined"], _i32p), _ptr(out.get("margin")))
@@ -234,15 +245,16 @@ def blend(splats, W, H, tile=16, bg=(0.0, 0.0, 0.0), brute=False, nthreads=1,
 
 
 def blend_backward(splats, W, H, dL_dimg, tile=16, bg=(0.0, 0.0, 0.0), nthreads=1,
-                   tile_mask=None):
+                   tile_mask=None, lists=None):
     """dL/d(mean2d[2], conic[3], opacity, rgb[3]) per Gaussian, [n,9]."""
     n = splats["radius"].shape[0]
     g9 = np.zeros((n, 9))
     d = np.ascontiguousarray(dL_dimg, dtype=np.float64)
     bgv = np.asarray(bg, dtype=np.float64)
     tm = _mask(tile_mask)
+    lv, lr, _keep = _lists(lists)
     lib().orc_blend_backward(n, C.byref(_splats_struct(splats)), W, H, tile, _ptr(bgv), _ptr(d),
-                             nthreads, _ptr(tm, _u8p), _ptr(g9))
+                             nthreads, _ptr(tm, _u8p), lv, lr, _ptr(g9))
     return g9
 
 

@@ -741,7 +741,9 @@ static int run_blend(blend_job *J) {
     uint32_t *vals = NULL, *ranges = NULL, *order = NULL;
     J->gx = (J->W + J->tile - 1) / J->tile;
     J->gy = (J->H + J->tile - 1) / J->tile;
-    if (J->brute) {
+    if (J->vals && J->ranges) {
+        /* lists given by the caller (from orc_keys of the same records) */
+    } else if (J->brute) {
         did_t *d = (did_t *)malloc(sizeof(did_t) * (size_t)(J->n > 0 ? J->n : 1));
         int64_t m = 0;
         for (int64_t i = 0; i < J->n; i++)
@@ -756,6 +758,51 @@ static int run_blend(blend_job *J) {
         free(d);
         J->order = order;
         J->n_order = m;
+    } else if (J->tile_mask) {
+        /* Only the marked tiles: each one's list is the (depth bits, id) order of the visible
+           Gaussians whose rect covers it -- the same lists a full key sort gives them. */
+        const int ntile = J->gx * J->gy;
+        ranges = (uint32_t *)calloc(2 * (size_t)ntile, sizeof(uint32_t));
+        int64_t total = 0;
+        for (int pass = 0; pass < 2; pass++) {
+            if (pass == 1) {
+                uint32_t acc = 0;
+                for (int t = 0; t < ntile; t++) {
+                    uint32_t c = ranges[2 * t + 1];
+                    ranges[2 * t] = acc;
+                    ranges[2 * t + 1] = acc;  /* becomes the end while filling */
+                    acc += c;
+                }
+                total = acc;
+                vals = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(total > 0 ? total : 1));
+            }
+            for (int64_t i = 0; i < J->n; i++) {
+                if (J->S->radius[i] <= 0) continue;
+                const int32_t *rc = J->S->rect + 4 * i;
+                for (int ty = rc[2] / J->tile; ty <= rc[3] / J->tile; ty++)
+                    for (int tx = rc[0] / J->tile; tx <= rc[1] / J->tile; tx++) {
+                        int t = ty * J->gx + tx;
+                        if (!J->tile_mask[t]) continue;
+                        if (pass == 0) ranges[2 * t + 1]++;
+                        else vals[ranges[2 * t + 1]++] = (uint32_t)i;
+                    }
+            }
+        }
+        for (int t = 0; t < ntile; t++) {
+            uint32_t a = ranges[2 * t], b = ranges[2 * t + 1];
+            if (b - a < 2) continue;
+            did_t *d = (did_t *)malloc(sizeof(did_t) * (b - a));
+            for (uint32_t k = a; k < b; k++) {
+                d[k - a].db = f32_bits(J->S->depth[vals[k]]);
+                d[k - a].id = vals[k];
+            }
+            qsort(d, b - a, sizeof(did_t), did_cmp);
+            for (uint32_t k = a; k < b; k++) vals[k] = d[k - a].id;
+            free(d);
+        }
+        (void)total;
+        J->vals = vals;
+        J->ranges = ranges;
     } else {
         int64_t K = orc_count_keys(J->n, J->S->radius, J->S->rect, J->tile);
         vals = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(K > 0 ? K : 1));
@@ -792,11 +839,14 @@ static int run_blend(blend_job *J) {
    instead of the tile lists. Any output pointer may be NULL. */
 int orc_blend(int64_t n, const orc_splats *S, int W, int H, int tile, const double *bg,
               int brute, int nthreads, int use_depth_margin, const uint8_t *tile_mask,
+              const uint32_t *list_vals, const uint32_t *list_ranges,
               double *image, double *T_final, int32_t *last, int32_t *n_contrib,
               int32_t *n_examined, double *margin) {
     blend_job J;
     memset(&J, 0, sizeof J);
     J.tile_mask = tile_mask;
+    J.vals = list_vals;
+    J.ranges = list_ranges;
     J.S = S;
     J.n = n;
     J.W = W;
@@ -818,10 +868,13 @@ int orc_blend(int64_t n, const orc_splats *S, int W, int H, int tile, const doub
 /* Backward of the blend of one view: writes dL/d(mean2d[2], conic[3], opacity, rgb[3]) per
    Gaussian into g9 [n,9] (overwritten). */
 int orc_blend_backward(int64_t n, const orc_splats *S, int W, int H, int tile, const double *bg,
-                       const double *dL_dimg, int nthreads, const uint8_t *tile_mask, double *g9) {
+                       const double *dL_dimg, int nthreads, const uint8_t *tile_mask,
+                       const uint32_t *list_vals, const uint32_t *list_ranges, double *g9) {
     blend_job J;
     memset(&J, 0, sizeof J);
     J.tile_mask = tile_mask;
+    J.vals = list_vals;
+    J.ranges = list_ranges;
     J.S = S;
     J.n = n;
     J.W = W;

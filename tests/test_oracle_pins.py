@@ -612,3 +612,39 @@ def test_straight_through_sh_band_masks():
                                        atol=1e-9)
             checked += 1
     assert checked >= 60
+
+
+@pytest.mark.parametrize("tile", [8, 16])
+def test_tile_masked_blend_equals_full_blend_on_those_tiles(tile):
+    scene = tiny_scene(600, 41)
+    cam = tiny_cam(75, 53, 0.6)
+    st = oracle.Settings(tile=tile, eps_mask=0.5, eps_sh=0.5, bg=(0.1, 0.0, 0.3))
+    sp = oracle.preprocess(scene, cam, st)
+    full = oracle.blend(sp, 75, 53, tile, st.bg, margins=True)
+    gx, gy = (75 + tile - 1) // tile, (53 + tile - 1) // tile
+    mask = np.zeros(gx * gy, np.uint8)
+    mask[np.random.default_rng(0).choice(gx * gy, size=gx * gy // 3, replace=False)] = 1
+    part = oracle.blend(sp, 75, 53, tile, st.bg, margins=True, tile_mask=mask)
+    pix = np.repeat(np.repeat(mask.reshape(gy, gx), tile, 0), tile, 1)[:53, :75].astype(bool)
+    for k in ("T_final", "last", "n_contrib", "n_examined", "margin"):
+        assert np.array_equal(part[k][pix], full[k][pix]), k
+    assert np.array_equal(part["image"][:, pix], full["image"][:, pix])
+    w = np.random.default_rng(1).normal(size=(3, 53, 75)) * pix[None]
+    g_full = oracle.blend_backward(sp, 75, 53, w, tile, st.bg)
+    g_part = oracle.blend_backward(sp, 75, 53, w, tile, st.bg, tile_mask=mask)
+    np.testing.assert_allclose(g_part, g_full, rtol=1e-12, atol=1e-15)
+
+
+def test_blend_with_given_lists_equals_blend():
+    scene = tiny_scene(500, 43)
+    cam = tiny_cam(70, 50, 1.3)
+    st = oracle.Settings(tile=16, eps_mask=0.5, eps_sh=0.5)
+    sp = oracle.preprocess(scene, cam, st)
+    _, vals, ranges = oracle.keys(sp["radius"], sp["rect"], sp["depth"], 70, 50, 16)
+    a = oracle.blend(sp, 70, 50, 16)
+    b = oracle.blend(sp, 70, 50, 16, lists=(vals, ranges))
+    for k in ("image", "T_final", "last", "n_examined"):
+        assert np.array_equal(a[k], b[k]), k
+    w = np.random.default_rng(0).normal(size=(3, 50, 70))
+    np.testing.assert_array_equal(oracle.blend_backward(sp, 70, 50, w, 16),
+                                  oracle.blend_backward(sp, 70, 50, w, 16, lists=(vals, ranges)))
