@@ -30,6 +30,10 @@
  *     the image does not depend on the tile size;
  *   - blending: a = min(0.99, o' G'(p)); fragments with a < 1/255 are skipped; a pixel stops
  *     before the fragment that would bring T below 1e-4; out = C + T_final * bg;
+ *   - keys: a Gaussian emits a key for a tile of its rect only if some point of (tile x rect)
+ *     has Q = (p - mean2d)^T conic (p - mean2d) <= tau (float32 test, fixed steps, in
+ *     tgs_internal.cuh); since tau carries a 1e-3 margin, a dropped tile holds no pixel with
+ *     a >= 1/255, so the image is the same as with every tile of the rect;
  *   - colour: c = max(0, 1/2 + sum_l M^l sum_m Y_lm(d) f_lm), d = unit(mean - campos);
  *   - mask thresholds: M = 1 iff logit > float32(log(eps / (1 - eps))).
  *
@@ -40,9 +44,10 @@
  *   (optional), sh_mask_logits [N,3] (optional).
  *   Images: [3,H,W] planar RGB. T_final [H,W]. last [H,W] int32: 1-based position, within
  *   the pixel's tile list, of its last contributing Gaussian (0: none).
- *   Splat record (one per (view, Gaussian), 12 x 32 bit, index v * N + g):
+ *   Splat record (one per (view, Gaussian), 16 x 32 bit, index v * N + g):
  *     [0..1] mean2d, [2..4] conic a, b, c of Sigma'^-1 = [[a, b], [b, c]], [5] opacity o',
- *     [6..8] rgb, [9] uint32 x_lo | x_hi << 16, [10] uint32 y_lo | y_hi << 16, [11] depth t_z.
+ *     [6..8] rgb, [9] uint32 x_lo | x_hi << 16, [10] uint32 y_lo | y_hi << 16, [11] depth t_z,
+ *     [12] cull threshold tau = 2 ln(255 o' / (1 - 1e-3)), [13] b / c, [14] b / a, [15] zero.
  *   Splat gradient record (12 floats, same index): dL/d mean2d [0..1], conic a, b, c [2..4]
  *     (with respect to the scalar b of power = -1/2 (a dx^2 + c dy^2) - b dx dy), opacity [5],
  *     rgb [6..8]; [9..11] unused.
@@ -205,7 +210,7 @@ tgs_status tgs_autotune(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *
 
 /* --- the individual steps (caller-owned buffers) --------------------------------------- */
 
-/* (a) Writes splat records [V*n,12] and radii [V*n] (0 = culled). */
+/* (a) Writes splat records [V*n,16] and radii [V*n] (0 = culled). */
 tgs_status tgs_preprocess(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams,
                           int32_t V, float *splats, int32_t *radii, tgs_stream stream);
 /* (b) From splat records and radii: sorted Gaussian record indices (v*n + g) in tile order,
@@ -245,7 +250,8 @@ tgs_status tgs_preprocess_backward(tgs_ctx *ctx, const tgs_gaussians *g, const t
    It needs no tgs_ctx and allocates nothing. Its scratch is one fixed array of about 12.2 MB
    of device memory that is part of the library image, so every GPU that loads libtgs holds
    it until the process exits. The caller still allocates every output: sorted_ids
-   [capacity], sorted_keys [capacity] (or NULL) and ranges [tiles,2]. tile is 8, 16 or 32.
+   [capacity], sorted_keys [capacity] (or NULL) and ranges [tiles,2]; splats are [n*V,16]
+   records as tgs_preprocess writes them. tile is 8, 16 or 32.
    Limits: n * V <= TGS_NOALLOC_MAX_RECORDS, else TGS_ERR_SCRATCH_LIMIT without launching
    anything; K <= TGS_NOALLOC_MAX_KEYS, else TGS_ERR_SCRATCH_LIMIT after counting the keys
    (*K_out is set); K > capacity gives TGS_ERR_CAPACITY (*K_out is set).

@@ -54,6 +54,7 @@ _i32p = C.POINTER(C.c_int32)
 _u32p = C.POINTER(C.c_uint32)
 _u64p = C.POINTER(C.c_uint64)
 _u8p = C.POINTER(C.c_uint8)
+_f32p = C.POINTER(C.c_float)
 
 
 class _Params(C.Structure):
@@ -77,10 +78,10 @@ class _Splats(C.Structure):
 def _declare(L):
     L.orc_sh_basis.argtypes = [C.c_int64, _dp, _dp, _dp]
     L.orc_preprocess.argtypes = [C.POINTER(_Params), _dp, _dp, C.POINTER(_Splats)]
-    L.orc_count_keys.argtypes = [C.c_int64, _i32p, _i32p, C.c_int]
+    L.orc_count_keys.argtypes = [C.c_int64, _i32p, _i32p, _f32p, C.c_int, C.c_int, C.c_int]
     L.orc_count_keys.restype = C.c_int64
-    L.orc_keys.argtypes = [C.c_int64, _i32p, _i32p, _dp, C.c_int, C.c_int, C.c_int, C.c_uint64,
-                           C.c_uint32, _u64p, _u32p, _u32p]
+    L.orc_keys.argtypes = [C.c_int64, _i32p, _i32p, _dp, _f32p, C.c_int, C.c_int, C.c_int,
+                           C.c_uint64, C.c_uint32, _u64p, _u32p, _u32p]
     L.orc_keys.restype = C.c_int64
     L.orc_blend.argtypes = [C.c_int64, C.POINTER(_Splats), C.c_int, C.c_int, C.c_int, _dp,
                             C.c_int, C.c_int, C.c_int, _u8p, _u32p, _u32p, _dp, _dp, _i32p,
@@ -191,20 +192,23 @@ def splats_from(mean2d, depth, conic, opacity, rgb, radius, rect):
                 m_all=None, m_edge=None)
 
 
-def keys(radius, rect, depth, W, H, tile, tile_offset=0, value_offset=0):
-    """Key emission, stable sort and tile ranges of one view."""
+def keys(radius, rect, depth, W, H, tile, tile_offset=0, value_offset=0, cull=None):
+    """Key emission, stable sort and tile ranges of one view. ``cull`` (float32 [n,8]: mean2d
+    x, y, conic a, b, c, threshold tau, b / c, b / a) applies the float32 tile cull test of the
+    key definition; without it every tile of each rect gets a key."""
     radius = np.ascontiguousarray(radius, np.int32)
     rect = np.ascontiguousarray(rect, np.int32)
     depth = np.ascontiguousarray(depth, np.float64)
+    cull = None if cull is None else np.ascontiguousarray(cull, np.float32)
     n = radius.shape[0]
     L = lib()
-    K = L.orc_count_keys(n, _ptr(radius, _i32p), _ptr(rect, _i32p), tile)
+    K = L.orc_count_keys(n, _ptr(radius, _i32p), _ptr(rect, _i32p), _ptr(cull, _f32p), W, H, tile)
     gx, gy = (W + tile - 1) // tile, (H + tile - 1) // tile
     k = np.zeros(max(K, 1), np.uint64)
     v = np.zeros(max(K, 1), np.uint32)
     r = np.zeros((gx * gy, 2), np.uint32)
-    L.orc_keys(n, _ptr(radius, _i32p), _ptr(rect, _i32p), _ptr(depth), W, H, tile, tile_offset,
-               value_offset, _ptr(k, _u64p), _ptr(v, _u32p), _ptr(r, _u32p))
+    L.orc_keys(n, _ptr(radius, _i32p), _ptr(rect, _i32p), _ptr(depth), _ptr(cull, _f32p), W, H,
+               tile, tile_offset, value_offset, _ptr(k, _u64p), _ptr(v, _u32p), _ptr(r, _u32p))
     return k[:K], v[:K], r
 
 

@@ -475,13 +475,70 @@ static uint32_t f32_bits(double d) {
     return u;
 }
 
-int64_t orc_count_keys(int64_t n, const int32_t *radius, const int32_t *rect, int tile) {
+/*
+ * Tile cull test of the key definition, in float32. g = (mx, my, a, b, c, tau, b / c, b / a)
+ * of one splat as the float32 values of its record. A tile is kept when the minimum over the pixel-centre rectangle
+ * [x0, x1] x [y0, y1] (the tile clipped to the splat's rect) of
+ * Q(p) = (p - m)^T [[a, b], [b, c]] (p - m) is <= tau. When the centre m is outside the
+ * rectangle the minimum lies on an edge facing m; on a vertical edge x = xe the minimiser is
+ * y = my - (b / c) (xe - mx) clamped to the edge (a convex 1D quadratic), on a horizontal
+ * edge x = mx - (b / a) (ye - my) clamped; the two ratios come from the record. Every step is one float32 operation in the order written
+ * (the file is compiled without contraction), as the definition states.
+ */
+static float quad_f32(float a, float b, float c, float dx, float dy) {
+    float q1 = (a * dx) * dx;
+    float q2 = ((2.0f * b) * dx) * dy;
+    float q3 = (c * dy) * dy;
+    return (q1 + q2) + q3;
+}
+
+static int tile_keep_f32(const float *g, int x0, int x1, int y0, int y1) {
+    float mx = g[0], my = g[1], a = g[2], b = g[3], c = g[4], tau = g[5], bc = g[6], ba = g[7];
+    float fx0 = (float)x0, fx1 = (float)x1, fy0 = (float)y0, fy1 = (float)y1;
+    if (mx >= fx0 && mx <= fx1 && my >= fy0 && my <= fy1) return 0.0f <= tau;
+    float q = INFINITY;
+    if (mx < fx0 || mx > fx1) {
+        float xe = mx < fx0 ? fx0 : fx1;
+        float dx = xe - mx;
+        float ys = my - bc * dx;
+        float dy = fminf(fmaxf(ys, fy0), fy1) - my;
+        q = fminf(q, quad_f32(a, b, c, dx, dy));
+    }
+    if (my < fy0 || my > fy1) {
+        float ye = my < fy0 ? fy0 : fy1;
+        float dy = ye - my;
+        float xs = mx - ba * dy;
+        float dx = fminf(fmaxf(xs, fx0), fx1) - mx;
+        q = fminf(q, quad_f32(a, b, c, dx, dy));
+    }
+    return q <= tau;
+}
+
+/* Whether tile (tx, ty) of Gaussian i gets a key: always without cull data, else the test. */
+static int key_kept(const int32_t *rect, const float *cull, int64_t i, int tile, int tx, int ty) {
+    if (!cull) return 1;
+    const int32_t *rc = rect + 4 * i;
+    int x0 = tx * tile > rc[0] ? tx * tile : rc[0];
+    int x1 = tx * tile + tile - 1 < rc[1] ? tx * tile + tile - 1 : rc[1];
+    int y0 = ty * tile > rc[2] ? ty * tile : rc[2];
+    int y1 = ty * tile + tile - 1 < rc[3] ? ty * tile + tile - 1 : rc[3];
+    return tile_keep_f32(cull + 8 * i, x0, x1, y0, y1);
+}
+
+/* Rects are expected inside the image; any other rect is rejected (no keys) rather than
+   indexed outside the tile grid. */
+static int rect_ok(const int32_t *rc, int W, int H) {
+    return rc[0] >= 0 && rc[0] <= rc[1] && rc[1] < W && rc[2] >= 0 && rc[2] <= rc[3] && rc[3] < H;
+}
+
+int64_t orc_count_keys(int64_t n, const int32_t *radius, const int32_t *rect, const float *cull,
+                       int W, int H, int tile) {
     int64_t K = 0;
     for (int64_t i = 0; i < n; i++) {
-        if (radius[i] <= 0) continue;
-        int64_t tx = rect[4 * i + 1] / tile - rect[4 * i + 0] / tile + 1;
-        int64_t ty = rect[4 * i + 3] / tile - rect[4 * i + 2] / tile + 1;
-        K += tx * ty;
+        if (radius[i] <= 0 || !rect_ok(rect + 4 * i, W, H)) continue;
+        for (int ty = rect[4 * i + 2] / tile; ty <= rect[4 * i + 3] / tile; ty++)
+            for (int tx = rect[4 * i + 0] / tile; tx <= rect[4 * i + 1] / tile; tx++)
+                K += key_kept(rect, cull, i, tile, tx, ty);
     }
     return K;
 }
@@ -501,17 +558,18 @@ static int kv_cmp(const void *a, const void *b) {
 /* Emits and stably sorts the keys of one view. ranges [ntiles,2] gets [start, end) per tile
    (relative to the start of this view's keys), empty tiles [0, 0). Returns K. */
 int64_t orc_keys(int64_t n, const int32_t *radius, const int32_t *rect, const double *depth,
-                 int W, int H, int tile, uint64_t tile_offset, uint32_t value_offset,
-                 uint64_t *keys, uint32_t *vals, uint32_t *ranges) {
+                 const float *cull, int W, int H, int tile, uint64_t tile_offset,
+                 uint32_t value_offset, uint64_t *keys, uint32_t *vals, uint32_t *ranges) {
     int gx = (W + tile - 1) / tile, gy = (H + tile - 1) / tile;
-    int64_t K = orc_count_keys(n, radius, rect, tile);
+    int64_t K = orc_count_keys(n, radius, rect, cull, W, H, tile);
     kv_t *kv = (kv_t *)malloc(sizeof(kv_t) * (size_t)(K > 0 ? K : 1));
     int64_t e = 0;
     for (int64_t i = 0; i < n; i++) {
-        if (radius[i] <= 0) continue;
+        if (radius[i] <= 0 || !rect_ok(rect + 4 * i, W, H)) continue;
         uint32_t db = f32_bits(depth[i]);
         for (int ty = rect[4 * i + 2] / tile; ty <= rect[4 * i + 3] / tile; ty++)
             for (int tx = rect[4 * i + 0] / tile; tx <= rect[4 * i + 1] / tile; tx++) {
+                if (!key_kept(rect, cull, i, tile, tx, ty)) continue;
                 uint64_t t = tile_offset + (uint64_t)(ty * gx + tx);
                 kv[e].key = (t << 32) | db;
                 kv[e].val = value_offset + (uint32_t)i;
@@ -747,7 +805,7 @@ static int run_blend(blend_job *J) {
         did_t *d = (did_t *)malloc(sizeof(did_t) * (size_t)(J->n > 0 ? J->n : 1));
         int64_t m = 0;
         for (int64_t i = 0; i < J->n; i++)
-            if (J->S->radius[i] > 0) {
+            if (J->S->radius[i] > 0 && rect_ok(J->S->rect + 4 * i, J->W, J->H)) {
                 d[m].db = f32_bits(J->S->depth[i]);
                 d[m].id = (uint32_t)i;
                 m++;
@@ -777,7 +835,7 @@ static int run_blend(blend_job *J) {
                 vals = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(total > 0 ? total : 1));
             }
             for (int64_t i = 0; i < J->n; i++) {
-                if (J->S->radius[i] <= 0) continue;
+                if (J->S->radius[i] <= 0 || !rect_ok(J->S->rect + 4 * i, J->W, J->H)) continue;
                 const int32_t *rc = J->S->rect + 4 * i;
                 for (int ty = rc[2] / J->tile; ty <= rc[3] / J->tile; ty++)
                     for (int tx = rc[0] / J->tile; tx <= rc[1] / J->tile; tx++) {
@@ -804,11 +862,11 @@ static int run_blend(blend_job *J) {
         J->vals = vals;
         J->ranges = ranges;
     } else {
-        int64_t K = orc_count_keys(J->n, J->S->radius, J->S->rect, J->tile);
+        int64_t K = orc_count_keys(J->n, J->S->radius, J->S->rect, NULL, J->W, J->H, J->tile);
         vals = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(K > 0 ? K : 1));
         ranges = (uint32_t *)malloc(sizeof(uint32_t) * 2 * (size_t)J->gx * J->gy);
-        orc_keys(J->n, J->S->radius, J->S->rect, J->S->depth, J->W, J->H, J->tile, 0, 0, NULL,
-                 vals, ranges);
+        orc_keys(J->n, J->S->radius, J->S->rect, J->S->depth, NULL, J->W, J->H, J->tile, 0, 0,
+                 NULL, vals, ranges);
         J->vals = vals;
         J->ranges = ranges;
     }

@@ -179,7 +179,7 @@ int bits_for(int64_t x) {
 
 // Buffers for V views of n Gaussians (per-record arrays).
 tgs_status ensure_records(tgs_ctx *c, int64_t nt, cudaStream_t st) {
-    TGS_TRY(ensure(c->splats, sizeof(float) * 12 * (size_t)nt, st));
+    TGS_TRY(ensure(c->splats, sizeof(float) * kSplatWords * (size_t)nt, st));
     TGS_TRY(ensure(c->sgrads, sizeof(float) * 12 * (size_t)nt, st));
     TGS_TRY(ensure(c->radii, sizeof(int32_t) * (size_t)nt, st));
     TGS_TRY(ensure(c->tt, sizeof(uint32_t) * (size_t)nt, st));
@@ -217,7 +217,7 @@ void bin_front(tgs_ctx *c, int64_t nt, uint32_t **sorted, cudaStream_t st) {
     uint32_t *cnt = as<uint32_t>(c->counts);
     scan_flags(as<uint32_t>(c->tt), nt, as<uint32_t>(c->pos), cnt + 0, as<uint32_t>(c->partials), st);
     compact_visible(as<uint32_t>(c->tt), as<uint32_t>(c->dbits), as<uint32_t>(c->pos), nt,
-                    as<uint32_t>(c->ck0), as<uint32_t>(c->cv0), st);
+                    as<float4>(c->splats), c->cfg.tile, as<uint32_t>(c->ck0), as<uint32_t>(c->cv0), st);
     uint32_t *k = as<uint32_t>(c->ck0), *v = as<uint32_t>(c->cv0);
     radix_sort_pairs(k, v, as<uint32_t>(c->ck1), as<uint32_t>(c->cv1), cnt + 0, nt, 0, 32,
                      as<uint32_t>(c->hist), as<uint32_t>(c->partials), st);
@@ -441,7 +441,7 @@ size_t tgs_workspace_bytes(const tgs_ctx *c, int64_t n, const tgs_camera *cams, 
     size_t pix = 0;
     for (int v = 0; v < V; v++) pix += (size_t)cams[v].width * cams[v].height;
     const size_t cap = (size_t)c->cfg.key_capacity;
-    return nt * (12 * 4 * 2 + 4 * 9) + cap * 16 + (size_t)cb.total_tiles * 8 +
+    return nt * (kSplatWords * 4 + 12 * 4 + 4 * 9) + cap * 16 + (size_t)cb.total_tiles * 8 +
            radix_hist_needed((int64_t)std::max(nt, cap)) * 4 + pix * 4 * (3 + 2 + 3 + 3);
 }
 
@@ -473,7 +473,7 @@ tgs_status tgs_bin(tgs_ctx *c, const float *splats, const int32_t *radii, int64_
     const int64_t nt = n * V;
     TGS_TRY(ensure_records(c, nt, st));
     // records come from the caller: copy them in and derive tiles touched and depth bits
-    TGS_CHECK(cudaMemcpyAsync(c->splats.p, splats, sizeof(float) * 12 * (size_t)nt, cudaMemcpyDeviceToDevice, st));
+    TGS_CHECK(cudaMemcpyAsync(c->splats.p, splats, sizeof(float) * kSplatWords * (size_t)nt, cudaMemcpyDeviceToDevice, st));
     TGS_CHECK(cudaMemcpyAsync(c->radii.p, radii, sizeof(int32_t) * (size_t)nt, cudaMemcpyDeviceToDevice, st));
     derive_touched(as<float4>(c->splats), as<int32_t>(c->radii), nt, c->cfg.tile, as<uint32_t>(c->tt),
                    as<uint32_t>(c->dbits), st);

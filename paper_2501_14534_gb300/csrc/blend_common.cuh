@@ -70,9 +70,8 @@ template <int TILE, int PPT, int NT>
 __device__ __forceinline__ void stage_splat(BlendSmem<NT> &sm, int slot,
                                             const float4 *__restrict__ splats, uint32_t id,
                                             int tx0, int ty0) {
-    const float4 s0 = __ldg(splats + 3 * (size_t)id);
-    const float4 s1 = __ldg(splats + 3 * (size_t)id + 1);
-    const float4 s2 = __ldg(splats + 3 * (size_t)id + 2);
+    const float4 *rp = splats + (size_t)kSplatWords / 4 * id;
+    const float4 s0 = __ldg(rp), s1 = __ldg(rp + 1), s2 = __ldg(rp + 2);
     sm.a[slot] = make_float4(s0.x, s0.y, __fmul_rn(-0.5f * kLog2e, s0.z), __fmul_rn(-kLog2e, s0.w));
     sm.b[slot] = make_float4(__fmul_rn(-0.5f * kLog2e, s1.x), s1.y, s1.z, s1.w);
     sm.c[slot] = s2.x;

@@ -112,7 +112,8 @@ extern "C" tgs_status tgs_bin_noalloc(const float *splats, const int32_t *radii,
 
     derive_touched(reinterpret_cast<const float4 *>(splats), radii, nt, tile, w + oTT, w + oDB, st);
     scan_flags(w + oTT, nt, w + oPOS, cnt + 0, w + oPART, st);
-    compact_visible(w + oTT, w + oDB, w + oPOS, nt, w + oCK0, w + oCV0, st);
+    compact_visible(w + oTT, w + oDB, w + oPOS, nt, reinterpret_cast<const float4 *>(splats), tile,
+                    w + oCK0, w + oCV0, st);
     uint32_t *k = w + oCK0, *v = w + oCV0;
     radix_sort_pairs(k, v, w + oCK1, w + oCV1, cnt + 0, nt, 0, 32, w + oHIST, w + oPART, st);
     gather_tiles_scan(v, w + oTT, cnt + 0, nt, w + oOFF, cnt + 1, w + oPART, nullptr, st);

@@ -244,7 +244,6 @@ __global__ void __launch_bounds__(128) k_preprocess(GaussPtrs g, const __grid_co
     GaussState s = load_state(g, i);
     ShCoeffs sh;
     if (s.ok) load_sh(g, i, s, sh);
-    const int B = cb.tile;
     for (int v = 0; v < cb.V; v++) {
         const DevCam &c = cb.c[v];
         const int64_t r = (int64_t)v * n + i;
@@ -281,12 +280,19 @@ __global__ void __launch_bounds__(128) k_preprocess(GaussPtrs g, const __grid_co
                     isfinite(vg.ca + vg.cb + vg.cc)) {
                     int ix0 = (int)xlo, ix1 = (int)xhi, iy0 = (int)ylo, iy1 = (int)yhi;
                     rad = (int)rf;
-                    touched = (uint32_t)((ix1 / B - ix0 / B + 1) * (iy1 / B - iy0 / B + 1));
                     uint32_t rx = (uint32_t)ix0 | ((uint32_t)ix1 << 16);
                     uint32_t ry = (uint32_t)iy0 | ((uint32_t)iy1 << 16);
-                    splats[3 * r + 0] = make_float4(vg.mx, vg.my, vg.ca, vg.cb);
-                    splats[3 * r + 1] = make_float4(vg.cc, s.op, rgb.x, rgb.y);
-                    splats[3 * r + 2] = make_float4(rgb.z, __uint_as_float(rx), __uint_as_float(ry), vg.tz);
+                    // cull threshold: a tile is kept when some point of it has
+                    // Q <= tau = 2 ln(255 o' / (1 - margin)), i.e. alpha may reach 1/255
+                    const float tau = 2.f * logf(255.f * s.op / (1.f - kCullMargin));
+                    // visible; the binning counts the tiles that pass the cull test
+                    touched = 1u;
+                    splats[kSplatWords / 4 * r + 0] = make_float4(vg.mx, vg.my, vg.ca, vg.cb);
+                    splats[kSplatWords / 4 * r + 1] = make_float4(vg.cc, s.op, rgb.x, rgb.y);
+                    splats[kSplatWords / 4 * r + 2] =
+                        make_float4(rgb.z, __uint_as_float(rx), __uint_as_float(ry), vg.tz);
+                    splats[kSplatWords / 4 * r + 3] =
+                        make_float4(tau, __fdiv_rn(vg.cb, vg.cc), __fdiv_rn(vg.cb, vg.ca), 0.f);
                     depth_bits[r] = __float_as_uint(vg.tz);
                     if (zero_grads) {
                         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);

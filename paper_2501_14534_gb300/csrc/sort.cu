@@ -140,14 +140,18 @@ void scan_generic(Load ld, const uint32_t *n_dev, int64_t n_cap, uint32_t *out, 
     }
 }
 
-__global__ void k_compact(const uint32_t *__restrict__ tt, const uint32_t *__restrict__ db,
-                          const uint32_t *__restrict__ pos, int64_t n, uint32_t *__restrict__ keys,
-                          uint32_t *__restrict__ vals) {
+// Compacts the visible records for the depth sort and replaces each visibility flag by the
+// record's number of keys: the tiles of its rect that pass the cull test.
+__global__ void k_compact(uint32_t *__restrict__ tt, const uint32_t *__restrict__ db,
+                          const uint32_t *__restrict__ pos, int64_t n, const float4 *__restrict__ splats,
+                          int B, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || tt[i] == 0u) return;
     const uint32_t p = pos[i];
     keys[p] = db[i];
     vals[p] = (uint32_t)i;
+    const float4 *rp = splats + (size_t)kSplatWords / 4 * i;
+    tt[i] = (uint32_t)for_kept_tiles(rp[0], rp[1], rp[2], rp[3], B, [](int, int) {});
 }
 
 // ---- radix sort -------------------------------------------------------------------------
@@ -237,19 +241,16 @@ __global__ void k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *
     const uint32_t rec = sorted_ids[i];
     const int v = (int)(rec / n_gauss);
     const DevCam &c = cb.c[v];
-    const float4 s2 = splats[3 * (size_t)rec + 2];
-    const uint32_t rx = __float_as_uint(s2.y), ry = __float_as_uint(s2.z);
-    const int B = cb.tile;
-    const int x0 = (int)(rx & 0xFFFFu) / B, x1 = (int)(rx >> 16) / B;
-    const int y0 = (int)(ry & 0xFFFFu) / B, y1 = (int)(ry >> 16) / B;
+    const float4 *rp = splats + (size_t)kSplatWords / 4 * rec;
     int64_t k = offsets[i];
-    for (int ty = y0; ty <= y1; ty++)
-        for (int tx = x0; tx <= x1; tx++, k++) {
-            if (k >= key_cap) return;
-            const bool ok = tx < c.gx && ty < c.gy;
+    for_kept_tiles(rp[0], rp[1], rp[2], rp[3], cb.tile, [&](int tx, int ty) {
+        if (k < key_cap) {
+            const bool ok = tx < c.gx && ty < c.gy;   // records from outside may carry any rect
             tile_keys[k] = ok ? (uint32_t)(c.tile_offset + ty * c.gx + tx) : 0xffffffffu;
             tile_vals[k] = rec;
         }
+        k++;
+    });
 }
 
 __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *K_dev, int64_t cap,
@@ -269,7 +270,7 @@ __global__ void k_full_keys(const uint32_t *__restrict__ tk, const uint32_t *__r
     const int64_t K = count_of(K_dev, cap);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= K) return;
-    const float depth = splats[3 * (size_t)tv[i] + 2].w;
+    const float depth = splats[(size_t)kSplatWords / 4 * tv[i] + 2].w;
     out[i] = ((uint64_t)tk[i] << 32) | (uint64_t)__float_as_uint(depth);
 }
 
@@ -281,11 +282,9 @@ __global__ void k_derive_touched(const float4 *__restrict__ splats, const int32_
         tt[i] = 0u;
         return;
     }
-    const float4 s2 = splats[3 * (size_t)i + 2];
-    const uint32_t rx = __float_as_uint(s2.y), ry = __float_as_uint(s2.z);
-    tt[i] = (uint32_t)(((int)(rx >> 16) / B - (int)(rx & 0xFFFFu) / B + 1) *
-                       ((int)(ry >> 16) / B - (int)(ry & 0xFFFFu) / B + 1));
-    db[i] = __float_as_uint(s2.w);
+    // visibility flag; k_compact replaces it by the number of kept tiles
+    tt[i] = 1u;
+    db[i] = __float_as_uint(splats[(size_t)kSplatWords / 4 * i + 2].w);
 }
 
 inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -305,11 +304,13 @@ void scan_flags(const uint32_t *tiles_touched, int64_t n_cap, uint32_t *out, uin
     scan_generic(LoadVisible{tiles_touched}, nullptr, n_cap, out, total, partials, st);
 }
 
-void compact_visible(const uint32_t *tiles_touched, const uint32_t *depth_bits, const uint32_t *pos,
-                     int64_t n_cap, uint32_t *keys, uint32_t *vals, cudaStream_t st) {
+void compact_visible(uint32_t *tiles_touched, const uint32_t *depth_bits, const uint32_t *pos,
+                     int64_t n_cap, const float4 *splats, int tile, uint32_t *keys, uint32_t *vals,
+                     cudaStream_t st) {
     if (n_cap <= 0) return;
     count_launch();
-    k_compact<<<blocks_for(n_cap, 256), 256, 0, st>>>(tiles_touched, depth_bits, pos, n_cap, keys, vals);
+    k_compact<<<blocks_for(n_cap, 256), 256, 0, st>>>(tiles_touched, depth_bits, pos, n_cap, splats, tile,
+                                                      keys, vals);
 }
 
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint32_t *vals_alt,

@@ -88,6 +88,71 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// Words per splat record (see include/tgs.h): 12 used by the blend + the cull threshold.
+constexpr int kSplatWords = 16;
+// Margin of the tile cull test: a (Gaussian, tile) key is dropped only when every pixel of the
+// tile stays below (1 - kCullMargin) / 255 in exact arithmetic.
+constexpr float kCullMargin = 1e-3f;
+
+// Minimum over the pixel-centre rectangle [x0, x1] x [y0, y1] of the quadratic form
+// Q(p) = (p - m)^T [[a, b], [b, c]] (p - m) of a splat, compared with its threshold tau:
+// true when some point of the rectangle has Q <= tau (the tile may hold a pixel with
+// alpha >= 1/255), false when none has. Every operation is an explicitly rounded float32
+// operation in a fixed order, so any IEEE binary32 implementation of the same steps agrees
+// bit for bit.
+__device__ __forceinline__ float cull_quad(float a, float b, float c, float dx, float dy) {
+    const float q1 = __fmul_rn(__fmul_rn(a, dx), dx);
+    const float q2 = __fmul_rn(__fmul_rn(__fmul_rn(2.f, b), dx), dy);
+    const float q3 = __fmul_rn(__fmul_rn(c, dy), dy);
+    return __fadd_rn(__fadd_rn(q1, q2), q3);
+}
+__device__ __forceinline__ bool tile_keep(float mx, float my, float a, float b, float c, float tau,
+                                          float b_over_c, float b_over_a, int x0, int x1, int y0,
+                                          int y1) {
+    const float fx0 = (float)x0, fx1 = (float)x1, fy0 = (float)y0, fy1 = (float)y1;
+    if (mx >= fx0 && mx <= fx1 && my >= fy0 && my <= fy1) return 0.f <= tau;
+    float q = __int_as_float(0x7f800000);  // +inf
+    // the minimum lies on an edge facing the centre; on a vertical edge x = xe it is at
+    // y = my - (b / c) (xe - mx) clamped to the edge, on a horizontal edge symmetrically
+    // (b / c and b / a are stored in the record)
+    if (mx < fx0 || mx > fx1) {
+        const float xe = mx < fx0 ? fx0 : fx1;
+        const float dx = __fsub_rn(xe, mx);
+        const float ys = __fsub_rn(my, __fmul_rn(b_over_c, dx));
+        const float dy = __fsub_rn(fminf(fmaxf(ys, fy0), fy1), my);
+        q = fminf(q, cull_quad(a, b, c, dx, dy));
+    }
+    if (my < fy0 || my > fy1) {
+        const float ye = my < fy0 ? fy0 : fy1;
+        const float dy = __fsub_rn(ye, my);
+        const float xs = __fsub_rn(mx, __fmul_rn(b_over_a, dy));
+        const float dx = __fsub_rn(fminf(fmaxf(xs, fx0), fx1), mx);
+        q = fminf(q, cull_quad(a, b, c, dx, dy));
+    }
+    return q <= tau;
+}
+
+// Tiles of a splat record kept by the cull test; calls f(tx, ty) for each, row-major.
+template <class F>
+__device__ __forceinline__ int for_kept_tiles(const float4 &s0, const float4 &s1, const float4 &s2,
+                                              const float4 &s3, int B, F f) {
+    const uint32_t rx = __float_as_uint(s2.y), ry = __float_as_uint(s2.z);
+    const int ix0 = (int)(rx & 0xFFFFu), ix1 = (int)(rx >> 16);
+    const int iy0 = (int)(ry & 0xFFFFu), iy1 = (int)(ry >> 16);
+    int kept = 0;
+    for (int ty = iy0 / B; ty <= iy1 / B; ty++) {
+        const int y0 = max(ty * B, iy0), y1 = min(ty * B + B - 1, iy1);
+        for (int tx = ix0 / B; tx <= ix1 / B; tx++) {
+            const int x0 = max(tx * B, ix0), x1 = min(tx * B + B - 1, ix1);
+            if (tile_keep(s0.x, s0.y, s0.z, s0.w, s1.x, s3.x, s3.y, s3.z, x0, x1, y0, y1)) {
+                f(tx, ty);
+                kept++;
+            }
+        }
+    }
+    return kept;
+}
+
 // ---- launchers implemented in the .cu files --------------------------------------------
 
 // preprocess.cu
@@ -109,8 +174,8 @@ size_t radix_hist_needed(int64_t n_items);
 // out[i] = exclusive prefix of in_fn(i) for i < *n_dev; *total = sum. n_cap bounds the grid.
 void scan_flags(const uint32_t *tiles_touched, int64_t n_cap, uint32_t *out, uint32_t *total,
                 uint32_t *partials, cudaStream_t st);
-void compact_visible(const uint32_t *tiles_touched, const uint32_t *depth_bits,
-                     const uint32_t *pos, int64_t n_cap, uint32_t *keys, uint32_t *vals,
+void compact_visible(uint32_t *tiles_touched, const uint32_t *depth_bits, const uint32_t *pos,
+                     int64_t n_cap, const float4 *splats, int tile, uint32_t *keys, uint32_t *vals,
                      cudaStream_t st);
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       const uint32_t *n_dev, int64_t n_cap, int begin_bit, int end_bit,

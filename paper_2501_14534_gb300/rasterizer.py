@@ -19,6 +19,7 @@ import torch
 
 from . import _binding as B
 
+SPLAT_WORDS = 16   # words per splat record (include/tgs.h)
 PARAM_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh_dc", "sh_rest",
               "mask_logits", "sh_mask_logits")
 
@@ -234,7 +235,7 @@ class Rasterizer:
 
     def preprocess(self, g: Gaussians, cams):
         V = len(cams)
-        splats = torch.empty((V * g.n, 12), device="cuda")
+        splats = torch.empty((V * g.n, SPLAT_WORDS), device="cuda")
         radii = torch.empty((V * g.n,), device="cuda", dtype=torch.int32)
         B.check(B.lib.tgs_preprocess(self._h, C.byref(g.struct()), cameras_array(cams), V,
                                      _p(splats), _p(radii), _stream()), "tgs_preprocess")

@@ -29,6 +29,21 @@ def splats_to_oracle(rec, radii):
                               z(rec[:, 6:9]), radii, np.where(vis[:, None], rect, 0))
 
 
+def cull_data(rec):
+    """Float32 cull data of library splat records: mean2d, conic a, b, c, tau, b/c, b/a."""
+    rec = np.asarray(rec, dtype=np.float32)
+    return np.ascontiguousarray(rec[:, [0, 1, 2, 3, 4, 12, 13, 14]])
+
+
+def gpu_lists(rec, radii, W, H, tile):
+    """The key oracle's tile lists (values, ranges) of library records, culled as the library
+    culls them."""
+    gs = splats_to_oracle(rec, radii)
+    _, v, r = oracle.keys(gs["radius"], gs["rect"], np.asarray(rec, np.float32)[:, 11], W, H, tile,
+                          cull=cull_data(rec))
+    return v, r
+
+
 def rel_err(a, b):
     a = np.asarray(a, np.float64)
     b = np.asarray(b, np.float64)

@@ -10,15 +10,19 @@ tile (a tile's pixels depend only on that tile's list, so any subset of tiles is
 - 300K Gaussians with per-Gaussian SH degree at 1920x1080 (render only) and 500K Gaussians
   over 16 mixed-resolution views (batched): images on sampled tiles.
 """
+import os
+
 import numpy as np
 import pytest
 
 import oracle
 from paper_2501_14534_gb300 import synth
 
-from helpers import IMAGE_ATOL, rel_err, splats_to_oracle
+from helpers import IMAGE_ATOL, cull_data, rel_err, splats_to_oracle
 
 pytestmark = pytest.mark.gpu
+
+NTHREADS = max(1, min(16, len(os.sched_getaffinity(0))))
 
 torch = pytest.importorskip("torch")
 
@@ -113,11 +117,12 @@ def test_1m_16views_batched_step_sampled_tiles(R, c2, tile, ppt):
         rg = np_(ranges).view(np.uint32)
         mask = sample_tiles(cam, tile, rg, seed=v)
         ref = oracle.blend(gs, cam.width, cam.height, tile, st.bg, margins=True, tile_mask=mask,
-                           nthreads=8)
+                           nthreads=NTHREADS)
         check_tiles(np_(images[v]), ref, pixel_mask(mask, cam, tile))
         if v == 0:
             # binning of a full view: bit-exact against the key oracle
-            ek, ev, er = oracle.keys(gs["radius"], gs["rect"], rec[:, 11], cam.width, cam.height, tile)
+            ek, ev, er = oracle.keys(gs["radius"], gs["rect"], rec[:, 11], cam.width, cam.height, tile,
+                                     cull=cull_data(rec))
             assert np.array_equal(np_(keys).view(np.uint64), ek)
             assert np.array_equal(np_(ids).view(np.uint32), ev)
             assert np.array_equal(rg, er)
@@ -127,7 +132,7 @@ def test_1m_16views_batched_step_sampled_tiles(R, c2, tile, ppt):
             dl = (rng.normal(size=(3, cam.height, cam.width)) * pix[None]).astype(np.float32)
             outs = rast.blend_forward(splats, ids, ranges, [cam])
             sg = np_(rast.blend_backward(splats, ids, ranges, [cam], outs, [torch.from_numpy(dl).cuda()]))
-            rg9 = oracle.blend_backward(gs, cam.width, cam.height, dl, tile, st.bg, nthreads=8,
+            rg9 = oracle.blend_backward(gs, cam.width, cam.height, dl, tile, st.bg, nthreads=NTHREADS,
                                         tile_mask=mask)
             for name, cols in [("mean2d", [0, 1]), ("conic", [2, 3, 4]), ("opacity", [5]),
                                ("rgb", [6, 7, 8])]:
@@ -182,26 +187,33 @@ def test_3m_8views_checkpointed_gradients_against_fp64_fd(R):
     trect = [np.where(b["radius"][:, None] > 0, b["rect"] // 16, -1) for b in base]
 
     def blend_three(v, i, recs):
-        """Blends of view v with Gaussian i's record replaced by each of recs, on its tiles."""
+        """Blends of view v with Gaussian i's record replaced by each of recs, on its tiles:
+        the Gaussians with a key in those tiles, in an image cropped to them (shifted by whole
+        tiles, so every tile list and pixel value is unchanged)."""
         cam = cams[v]
         x0, x1, y0, y1 = (int(c) for c in recs[0]["rect"] // 16)
         tr = trect[v]
         sub = np.nonzero((tr[:, 1] >= x0) & (tr[:, 0] <= x1) & (tr[:, 3] >= y0) & (tr[:, 2] <= y1))[0]
         j = int(np.searchsorted(sub, i))
         assert sub[j] == i
-        gx, gy = tile_grid(cam, 16)
-        mask = np.zeros((gy, gx), np.uint8)
-        mask[y0:y1 + 1, x0:x1 + 1] = 1
+        ox, oy = 16 * x0, 16 * y0
+        Wc, Hc = min(cam.width, 16 * (x1 + 1)) - ox, min(cam.height, 16 * (y1 + 1)) - oy
         sp = {f: np.ascontiguousarray(base[v][f][sub]) for f in fields}
         sp["m_all"] = sp["m_edge"] = None
-        ys, xs = slice(y0 * 16, min((y1 + 1) * 16, cam.height)), slice(x0 * 16, min((x1 + 1) * 16, cam.width))
+        wv = ws[v][:, oy:oy + Hc, ox:ox + Wc]
         outs = []
         for r in recs:
             for f in fields:
                 sp[f][j] = r[f]
-            o = oracle.blend(sp, cam.width, cam.height, 16, st.bg, tile_mask=mask.reshape(-1))
-            outs.append((float((o["image"][:, ys, xs] * ws[v][:, ys, xs]).sum()),
-                         o["n_contrib"][ys, xs].copy(), o["last"][ys, xs].copy()))
+            # shift by whole tiles and clip each rect to the crop (a pixel of the crop is in
+            # the clipped rect exactly when it is in the original one)
+            rc = sp["rect"] - np.array([ox, ox, oy, oy], np.int32)
+            rc = np.column_stack([np.maximum(rc[:, 0], 0), np.minimum(rc[:, 1], Wc - 1),
+                                  np.maximum(rc[:, 2], 0), np.minimum(rc[:, 3], Hc - 1)])
+            cs = dict(sp, mean2d=sp["mean2d"] - np.array([ox, oy], float),
+                      rect=np.ascontiguousarray(rc, dtype=np.int32))
+            o = oracle.blend(cs, Wc, Hc, 16, st.bg, nthreads=NTHREADS)
+            outs.append((float((o["image"] * wv).sum()), o["n_contrib"].copy(), o["last"].copy()))
         return outs
 
     fd_vals, gpu_vals, tries = [], [], 0
@@ -255,7 +267,7 @@ def test_300k_1920x1080_render_sampled_tiles(R):
         mask = sample_tiles(cam, 16, seed=40 + v, n_rand=24)
         # end to end against the FP64 preprocess (decision-margin exclusion)
         ref = oracle.blend(oracle.preprocess(scene, cam, st), cam.width, cam.height, 16, st.bg,
-                           margins=True, depth_margin=True, tile_mask=mask, nthreads=8)
+                           margins=True, depth_margin=True, tile_mask=mask, nthreads=NTHREADS)
         pix = pixel_mask(mask, cam, 16)
         clear = (ref["margin"] >= 1.0) & pix
         diff = np.abs(np_(outs[v]["image"]) - ref["image"]).max(axis=0)
@@ -283,5 +295,5 @@ def test_500k_16_mixed_views_batched_sampled_tiles(R, tile, ppt):
         gs = splats_to_oracle(np_(splats), np_(radii))
         mask = sample_tiles(cam, tile, seed=70 + v, n_rand=16)
         ref = oracle.blend(gs, cam.width, cam.height, tile, st.bg, margins=True, tile_mask=mask,
-                           nthreads=8)
+                           nthreads=NTHREADS)
         check_tiles(np_(images[v]), ref, pixel_mask(mask, cam, tile))

@@ -8,7 +8,8 @@ import pytest
 import oracle
 from paper_2501_14534_gb300 import synth
 
-from helpers import GRAD_RTOL, IMAGE_ATOL, image_compare, rel_err, splats_to_oracle
+from helpers import (GRAD_RTOL, IMAGE_ATOL, cull_data, gpu_lists, image_compare, rel_err,
+                     splats_to_oracle)
 
 pytestmark = pytest.mark.gpu
 
@@ -119,7 +120,8 @@ def test_keys_sort_ranges_bit_exact(R, tile):
     for v, cam in enumerate(cams):
         gs = splats_to_oracle(rec[v * n:(v + 1) * n], rad[v * n:(v + 1) * n])
         k, vv, r = oracle.keys(gs["radius"], gs["rect"], rec[v * n:(v + 1) * n, 11], cam.width,
-                               cam.height, tile, tile_offset=toff, value_offset=v * n)
+                               cam.height, tile, tile_offset=toff, value_offset=v * n,
+                               cull=cull_data(rec[v * n:(v + 1) * n]))
         base = sum(len(x) for x in ek)
         nz = r[:, 1] > 0
         r = r.copy()
@@ -152,7 +154,9 @@ def test_blend_forward_matches_oracle_on_same_records(R, case):
     n = g.n
     for v, cam in enumerate(cams):
         gs = splats_to_oracle(rec[v * n:(v + 1) * n], rad[v * n:(v + 1) * n])
-        ref = oracle.blend(gs, cam.width, cam.height, st.tile, st.bg, margins=True)
+        lists = gpu_lists(rec[v * n:(v + 1) * n], rad[v * n:(v + 1) * n], cam.width, cam.height,
+                          st.tile)
+        ref = oracle.blend(gs, cam.width, cam.height, st.tile, st.bg, margins=True, lists=lists)
         img = np_(outs[v]["image"])
         m, excl = image_compare(img, ref["image"], ref["margin"])
         assert m <= IMAGE_ATOL, (m, excl)

@@ -648,3 +648,48 @@ def test_blend_with_given_lists_equals_blend():
     w = np.random.default_rng(0).normal(size=(3, 50, 70))
     np.testing.assert_array_equal(oracle.blend_backward(sp, 70, 50, w, 16),
                                   oracle.blend_backward(sp, 70, 50, w, 16, lists=(vals, ranges)))
+
+
+def _cull_of(sp):
+    """Float32 cull data (mean2d, conic, tau) of FP64 records, tau = 2 ln(255 o' / (1 - 1e-3))."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tau = 2.0 * np.log(255.0 * sp["opacity"] / (1.0 - 1e-3))
+        c32 = sp["conic"].astype(np.float32)
+        bc = c32[:, 1] / c32[:, 2]
+        ba = c32[:, 1] / c32[:, 0]
+    return np.column_stack([sp["mean2d"], sp["conic"], tau, bc, ba]).astype(np.float32)
+
+
+@pytest.mark.parametrize("tile", [8, 16, 32])
+def test_tile_cull_drops_only_tiles_without_a_visible_pixel(tile):
+    scene = tiny_scene(500, 47)
+    scene["log_scales"][:, 0] += 0.8          # strongly anisotropic footprints
+    cam = tiny_cam(90, 70, 0.4)
+    st = oracle.Settings(tile=tile, eps_mask=0.5, eps_sh=0.5)
+    sp = oracle.preprocess(scene, cam, st)
+    cull = _cull_of(sp)
+    k_all, _, _ = oracle.keys(sp["radius"], sp["rect"], sp["depth"], 90, 70, tile)
+    k_cul, v_cul, r_cul = oracle.keys(sp["radius"], sp["rect"], sp["depth"], 90, 70, tile, cull=cull)
+    assert 0 < len(k_cul) < 0.9 * len(k_all)
+    kept = set((int(k >> np.uint64(32)), int(v)) for k, v in zip(k_cul, oracle.keys(
+        sp["radius"], sp["rect"], sp["depth"], 90, 70, tile, cull=cull)[1]))
+    gx = (90 + tile - 1) // tile
+    py, px = np.mgrid[0:70, 0:90].astype(float)
+    for i in np.nonzero(sp["radius"] > 0)[0]:
+        x0, x1, y0, y1 = sp["rect"][i]
+        dx, dy = sp["mean2d"][i, 0] - px, sp["mean2d"][i, 1] - py
+        a, b, c = sp["conic"][i]
+        alpha = sp["opacity"][i] * np.exp(-0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy)
+        for ty in range(y0 // tile, y1 // tile + 1):
+            for tx in range(x0 // tile, x1 // tile + 1):
+                if (ty * gx + tx, i) in kept:
+                    continue
+                ys = slice(max(ty * tile, y0), min(ty * tile + tile - 1, y1) + 1)
+                xs = slice(max(tx * tile, x0), min(tx * tile + tile - 1, x1) + 1)
+                # a dropped tile holds no pixel that reaches alpha >= 1/255 (with the margin)
+                assert alpha[ys, xs].max() < (1.0 - 0.5e-3) / 255.0, (i, tx, ty)
+    # and the image, the transmittance and the contributor count are unchanged
+    full = oracle.blend(sp, 90, 70, tile)
+    cul = oracle.blend(sp, 90, 70, tile, lists=(v_cul, r_cul))
+    for k in ("image", "T_final", "n_contrib"):
+        assert np.array_equal(full[k], cul[k]), k
