@@ -33,8 +33,11 @@ N_GAUSS = 1_000_000
 N_VIEWS = 16
 W, H = 1280, 832
 METRIC = "fwd+bwd views/sec @1M Gaussians 1280x832 (batched step)"
-PAIR_OPS_FWD = 11   # float32 pipe ops per (pixel, fragment) alpha evaluation, from blend.cu
-PAIR_OPS_BWD = 11   # the same evaluation repeated in the backward (conservative: no gradient ops)
+# float32 operations per (pixel, fragment) pair, counted from blend_common.cuh:
+OPS_EVAL = 11        # offset, exponent, skip tests, ex2, alpha: every evaluated pair (forward)
+OPS_BLEND = 7        # 1 - a, T update, stop test, weight, 3 colour FMAs: contributing pairs
+OPS_BWD = 51         # evaluation again + T recovery, colour-behind update, dL/da and the 9
+                     # gradient terms: contributing pairs (skipped pairs not counted)
 # float32 lanes: 152 SMs x 128 lanes x 2.07 GHz max SM clock
 ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 
@@ -262,11 +265,8 @@ def main():
             e1.record(stream)
         stream.synchronize()
     barrier()
-    ms_total = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    from paper_2501_14534_gb300 import dist as tgs_dist
+    ms_total = tgs_dist.reduce_max(e0.elapsed_time(e1), device="cuda")   # max over ranks
     rast.poll()
     ms_step = ms_total / args.steps
     value = V * world / (ms_step / 1000.0)
@@ -353,22 +353,24 @@ def main():
     # of the batched step
     cfg = rast.config
     counter = R.Rasterizer(tile=cfg.tile, ppt=cfg.ppt, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
-    P_fwd = P_bwd = 0
+    P_exam = P_eval = P_contrib = 0
     for v in range(V):
-        o = counter.forward(g, [cams[v]], want_examined=True)[0]
-        P_fwd += int(o["n_examined"].sum().item())
-        P_bwd += int(o["last"].sum().item())
+        o = counter.forward(g, [cams[v]], want_examined=True, want_counts=True)[0]
+        P_exam += int(o["n_examined"].sum().item())
+        P_eval += int(o["n_eval"].sum().item())
+        P_contrib += int(o["n_contrib"].sum().item())
     hbm_gbs, peak_kind = load_peaks()
     n = g.n
     bytes_pre = n * 252 + V * n * (48 + 4 + 4 + 4 + 48)
     bytes_pbwd = n * (252 + 252 + 12 * 2) + V * n * (48 + 4)
+    ops_fwd = P_eval * OPS_EVAL + P_contrib * OPS_BLEND
+    ops_bwd = P_contrib * OPS_BWD
     work = {
-        "fused_blend": ("alu", (P_fwd * PAIR_OPS_FWD + P_bwd * PAIR_OPS_BWD) / 1e12, ALU_PEAK_TOPS,
-                        "Tops/s"),
+        "fused_blend": ("alu", (ops_fwd + ops_bwd) / 1e12, ALU_PEAK_TOPS, "Tops/s"),
         "preprocess": ("hbm", bytes_pre / 1e9, hbm_gbs, "GB/s"),
         "preprocess_backward": ("hbm", bytes_pbwd / 1e9, hbm_gbs, "GB/s"),
-        "blend_forward": ("alu", P_fwd * PAIR_OPS_FWD / 1e12, ALU_PEAK_TOPS, "Tops/s"),
-        "blend_backward": ("alu", P_bwd * PAIR_OPS_BWD / 1e12, ALU_PEAK_TOPS, "Tops/s"),
+        "blend_forward": ("alu", ops_fwd / 1e12, ALU_PEAK_TOPS, "Tops/s"),
+        "blend_backward": ("alu", ops_bwd / 1e12, ALU_PEAK_TOPS, "Tops/s"),
     }
     dom = max((k for k in stage_ms if k in work), key=lambda k: stage_ms[k])
     bound, units, peak, unit = work[dom]
@@ -399,7 +401,8 @@ def main():
             "plain_views_per_s": plain_vps, "render_fps": render_fps,
             "unfused_views_per_s": unfused,
             "speedup_vs_plain": value / world / plain_vps,
-            "stage_ms": stage_ms, "pairs": {"forward": P_fwd, "backward": P_bwd},
+            "stage_ms": stage_ms,
+            "pairs": {"examined": P_exam, "evaluated": P_eval, "contributing": P_contrib},
             "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
             "gpu_launches": kernels * args.steps,
         }

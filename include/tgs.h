@@ -137,6 +137,9 @@ typedef struct {
     int32_t *last;       /* [H,W] or NULL */
     int32_t *n_examined; /* [H,W] or NULL: list entries each pixel looked at */
     int32_t *radii;      /* [n] or NULL */
+    int32_t *n_contrib;  /* [H,W] or NULL: fragments blended into the pixel */
+    int32_t *n_eval;     /* [H,W] or NULL: fragments whose rect holds the pixel, evaluated
+                            before the pixel stopped (the blend's algorithmic work) */
 } tgs_view_out;
 
 typedef struct {
@@ -247,7 +250,7 @@ tgs_status tgs_preprocess_backward(tgs_ctx *ctx, const tgs_gaussians *g, const t
    cudaMalloc: a host application that hands all device memory to its own allocator or
    memory pool, a real-time loop that must not pay for an allocation, or code under a fixed
    device-memory budget. The paper has no counterpart; this is a deployment variant.
-   It needs no tgs_ctx and allocates nothing. Its scratch is one fixed array of about 12.2 MB
+   It needs no tgs_ctx and allocates nothing. Its scratch is one fixed array of about 13.4 MB
    of device memory that is part of the library image, so every GPU that loads libtgs holds
    it until the process exits. The caller still allocates every output: sorted_ids
    [capacity], sorted_keys [capacity] (or NULL) and ranges [tiles,2]; splats are [n*V,16]

@@ -85,7 +85,7 @@ def _declare(L):
     L.orc_keys.restype = C.c_int64
     L.orc_blend.argtypes = [C.c_int64, C.POINTER(_Splats), C.c_int, C.c_int, C.c_int, _dp,
                             C.c_int, C.c_int, C.c_int, _u8p, _u32p, _u32p, _dp, _dp, _i32p,
-                            _i32p, _i32p, _dp]
+                            _i32p, _i32p, _i32p, _dp]
     L.orc_blend_backward.argtypes = [C.c_int64, C.POINTER(_Splats), C.c_int, C.c_int, C.c_int,
                                      _dp, _dp, C.c_int, _u8p, _u32p, _u32p, _dp]
     L.orc_preprocess_backward.argtypes = [C.POINTER(_Params), _dp, _dp, _dp, C.POINTER(_Grads),
@@ -228,13 +228,14 @@ def blend(splats, W, H, tile=16, bg=(0.0, 0.0, 0.0), brute=False, nthreads=1,
           margins=False, depth_margin=False, tile_mask=None, lists=None):
     """Front-to-back blending of one view (Eq. 2). Returns image [3,H,W], T_final, last
     (1-based position in the tile list of the last contributor, 0 if none), n_contrib,
-    n_examined and, if requested, the per-pixel decision margin. ``tile_mask`` (one byte per
+    n_examined, n_eval (fragments whose rect holds the pixel, up to the stop) and, if
+    requested, the per-pixel decision margin. ``tile_mask`` (one byte per
     tile, row-major) restricts the work to the tiles marked 1; other pixels stay 0. ``lists``
     = (values, ranges) from ``keys`` of the same records skips building the tile lists."""
     n = splats["radius"].shape[0]
     out = dict(image=np.zeros((3, H, W)), T_final=np.zeros((H, W)),
                last=np.zeros((H, W), np.int32), n_contrib=np.zeros((H, W), np.int32),
-               n_examined=np.zeros((H, W), np.int32))
+               n_examined=np.zeros((H, W), np.int32), n_eval=np.zeros((H, W), np.int32))
     if margins:
         out["margin"] = np.zeros((H, W))
     bgv = np.asarray(bg, dtype=np.float64)
@@ -244,7 +245,8 @@ def blend(splats, W, H, tile=16, bg=(0.0, 0.0, 0.0), brute=False, nthreads=1,
                     nthreads, int(depth_margin), _ptr(tm, _u8p), lv, lr, _ptr(out["image"]),
                     _ptr(out["T_final"]),
                     _ptr(out["last"], _i32p), _ptr(out["n_contrib"], _i32p),
-                    _ptr(out["n_examined"], _i32p), _ptr(out.get("margin")))
+                    _ptr(out["n_examined"], _i32p), _ptr(out["n_eval"], _i32p),
+                    _ptr(out.get("margin")))
     return out
 
 

@@ -609,7 +609,7 @@ typedef struct {
     const uint8_t *tile_mask; /* NULL, or 1 for every tile to process */
     /* forward outputs */
     double *image, *T_final, *margin;
-    int32_t *last, *n_contrib, *n_examined;
+    int32_t *last, *n_contrib, *n_examined, *n_eval;
     /* backward */
     const double *dL_dimg;
     double *acc; /* [nthreads][n][9] */
@@ -630,12 +630,12 @@ typedef struct {
 /* Blend a single pixel; if frags != NULL, also records the contributing fragments. */
 static int blend_pixel(const blend_job *J, int px, int py, const uint32_t *list, int64_t len,
                        double C[3], double *T_out, int32_t *last, int32_t *ncontrib,
-                       int32_t *nexam, double *margin, frag_t *frags) {
+                       int32_t *nexam, int32_t *neval, double *margin, frag_t *frags) {
     const orc_splats *S = J->S;
     double T = 1.0;
     C[0] = C[1] = C[2] = 0.0;
     int nc = 0;
-    int32_t lst = 0, ex = 0;
+    int32_t lst = 0, ex = 0, ev = 0;
     double mg = INFINITY;
     double prev_depth = NAN;
     for (int64_t k = 0; k < len; k++) {
@@ -656,6 +656,7 @@ static int blend_pixel(const blend_job *J, int px, int py, const uint32_t *list,
             if (power <= 0.0 && x >= 1.0 / 255.0 && S->m_edge) mg = fmin(mg, S->m_edge[g]);
             continue;
         }
+        ev++;  /* the pixel is in the rect: this fragment is evaluated */
         if (power > 0.0) continue;
         double alpha = fmin(0.99, x);
         if (margin) mg = fmin(mg, fabs(x * 255.0 - 1.0) / 1e-5);
@@ -690,6 +691,7 @@ static int blend_pixel(const blend_job *J, int px, int py, const uint32_t *list,
     *last = lst;
     *ncontrib = nc;
     *nexam = ex;
+    *neval = ev;
     if (margin) *margin = mg;
     return nc;
 }
@@ -760,8 +762,8 @@ static void *blend_worker(void *p) {
             for (int px = tx * J->tile; px < (tx + 1) * J->tile && px < J->W; px++) {
                 int64_t pix = (int64_t)py * J->W + px;
                 double C[3], T, mg;
-                int32_t lst, nc, ex;
-                int ncf = blend_pixel(J, px, py, list, len, C, &T, &lst, &nc, &ex,
+                int32_t lst, nc, ex, ev;
+                int ncf = blend_pixel(J, px, py, list, len, C, &T, &lst, &nc, &ex, &ev,
                                       J->margin ? &mg : NULL, frags);
                 if (J->image)
                     for (int ch = 0; ch < 3; ch++)
@@ -770,6 +772,7 @@ static void *blend_worker(void *p) {
                 if (J->last) J->last[pix] = lst;
                 if (J->n_contrib) J->n_contrib[pix] = nc;
                 if (J->n_examined) J->n_examined[pix] = ex;
+                if (J->n_eval) J->n_eval[pix] = ev;
                 if (J->margin) J->margin[pix] = mg;
                 if (J->dL_dimg) {
                     double d[3];
@@ -899,7 +902,7 @@ int orc_blend(int64_t n, const orc_splats *S, int W, int H, int tile, const doub
               int brute, int nthreads, int use_depth_margin, const uint8_t *tile_mask,
               const uint32_t *list_vals, const uint32_t *list_ranges,
               double *image, double *T_final, int32_t *last, int32_t *n_contrib,
-              int32_t *n_examined, double *margin) {
+              int32_t *n_examined, int32_t *n_eval, double *margin) {
     blend_job J;
     memset(&J, 0, sizeof J);
     J.tile_mask = tile_mask;
@@ -919,6 +922,7 @@ int orc_blend(int64_t n, const orc_splats *S, int W, int H, int tile, const doub
     J.last = last;
     J.n_contrib = n_contrib;
     J.n_examined = n_examined;
+    J.n_eval = n_eval;
     J.margin = margin;
     return run_blend(&J);
 }

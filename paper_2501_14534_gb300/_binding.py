@@ -54,7 +54,7 @@ class tgs_camera(C.Structure):
 
 class tgs_view_out(C.Structure):
     _fields_ = [("image", _vp), ("T_final", _vp), ("last", _vp), ("n_examined", _vp),
-                ("radii", _vp)]
+                ("radii", _vp), ("n_contrib", _vp), ("n_eval", _vp)]
 
 
 class tgs_grads(C.Structure):

@@ -34,7 +34,7 @@ struct tgs_ctx {
     int device = 0;
     // scratch arena
     Buf splats, radii, tt, dbits, pos, ck0, cv0, ck1, cv1, offsets, tk0, tv0, tk1, tv1, ranges,
-        hist, partials, sgrads, counts, status, pixstate, dimg, images, items;
+        hist, partials, sgrads, counts, status, pixstate, dimg, images, items, kmask;
     uint32_t *h_counts = nullptr;   // pinned host copy of (visible, K)
     // binning kept from the last plain forward
     bool state_valid = false;
@@ -190,6 +190,7 @@ tgs_status ensure_records(tgs_ctx *c, int64_t nt, cudaStream_t st) {
     TGS_TRY(ensure(c->ck1, sizeof(uint32_t) * (size_t)nt, st));
     TGS_TRY(ensure(c->cv1, sizeof(uint32_t) * (size_t)nt, st));
     TGS_TRY(ensure(c->offsets, sizeof(uint32_t) * (size_t)nt, st));
+    TGS_TRY(ensure(c->kmask, sizeof(uint2) * (size_t)nt, st));
     TGS_TRY(ensure(c->counts, sizeof(uint32_t) * 4, st));
     size_t h = std::max(radix_hist_needed(nt), (size_t)16);
     TGS_TRY(ensure(c->hist, sizeof(uint32_t) * h, st));
@@ -217,7 +218,8 @@ void bin_front(tgs_ctx *c, int64_t nt, uint32_t **sorted, cudaStream_t st) {
     uint32_t *cnt = as<uint32_t>(c->counts);
     scan_flags(as<uint32_t>(c->tt), nt, as<uint32_t>(c->pos), cnt + 0, as<uint32_t>(c->partials), st);
     compact_visible(as<uint32_t>(c->tt), as<uint32_t>(c->dbits), as<uint32_t>(c->pos), nt,
-                    as<float4>(c->splats), c->cfg.tile, as<uint32_t>(c->ck0), as<uint32_t>(c->cv0), st);
+                    as<float4>(c->splats), c->cfg.tile, as<uint32_t>(c->ck0), as<uint32_t>(c->cv0),
+                    as<uint2>(c->kmask), st);
     uint32_t *k = as<uint32_t>(c->ck0), *v = as<uint32_t>(c->cv0);
     radix_sort_pairs(k, v, as<uint32_t>(c->ck1), as<uint32_t>(c->cv1), cnt + 0, nt, 0, 32,
                      as<uint32_t>(c->hist), as<uint32_t>(c->partials), st);
@@ -231,7 +233,8 @@ uint32_t *bin_back(tgs_ctx *c, int64_t nt, int64_t n, const uint32_t *sorted, co
                    int64_t cap, cudaStream_t st) {
     uint32_t *cnt = as<uint32_t>(c->counts);
     emit_keys(sorted, as<uint32_t>(c->offsets), cnt + 0, nt, as<float4>(c->splats), n, cb,
-              as<uint32_t>(c->tk0), as<uint32_t>(c->tv0), cnt + 1, cap, as<uint32_t>(c->status), st);
+              as<uint2>(c->kmask), as<uint32_t>(c->tk0), as<uint32_t>(c->tv0), cnt + 1, cap,
+              as<uint32_t>(c->status), st);
     uint32_t *k = as<uint32_t>(c->tk0), *v = as<uint32_t>(c->tv0);
     radix_sort_pairs(k, v, as<uint32_t>(c->tk1), as<uint32_t>(c->tv1), cnt + 1, cap, 0,
                      bits_for(cb.total_tiles), as<uint32_t>(c->hist), as<uint32_t>(c->partials), st);
@@ -275,6 +278,8 @@ PixPtrs pix_for(const tgs_view_out *outs, int V, const float *const *dL) {
         p.T_final[v] = outs[v].T_final;
         p.last[v] = outs[v].last;
         p.n_exam[v] = outs[v].n_examined;
+        p.n_contrib[v] = outs[v].n_contrib;
+        p.n_eval[v] = outs[v].n_eval;
         p.dL[v] = dL ? dL[v] : nullptr;
     }
     return p;
@@ -383,7 +388,7 @@ void tgs_destroy(tgs_ctx *c) {
     Buf *bufs[] = {&c->splats, &c->radii, &c->tt, &c->dbits, &c->pos, &c->ck0, &c->cv0, &c->ck1,
                    &c->cv1, &c->offsets, &c->tk0, &c->tv0, &c->tk1, &c->tv1, &c->ranges, &c->hist,
                    &c->partials, &c->sgrads, &c->counts, &c->status, &c->pixstate, &c->dimg,
-                   &c->images, &c->items};
+                   &c->images, &c->items, &c->kmask};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_counts) cudaFreeHost(c->h_counts);
@@ -672,6 +677,8 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
         outs[v].last = last + off;
         outs[v].n_examined = nullptr;
         outs[v].radii = nullptr;
+        outs[v].n_contrib = nullptr;
+        outs[v].n_eval = nullptr;
         dls[v] = dimg + 3 * off;
         off += hw;
     }

@@ -21,7 +21,7 @@
 namespace tgs {
 namespace {
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool COUNT>
 __global__ void __launch_bounds__(TILE * TILE / PPT)
 k_blend_fwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
             const uint2 *__restrict__ ranges, const __grid_constant__ CamBatch cb,
@@ -34,7 +34,7 @@ k_blend_fwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
     TilePixels<TILE, PPT> P;
     P.init(lt % cam.gx, lt / cam.gx, cam.W, cam.H);
     FwdState<PPT> S;
-    tile_forward<TILE, PPT>(sm, splats, ids, ranges[gt], P, S);
+    tile_forward<TILE, PPT, COUNT>(sm, splats, ids, ranges[gt], P, S);
     const int HW = cam.W * cam.H;
     float *img = px.image[v];
     float *Tf = px.T_final[v];
@@ -50,6 +50,10 @@ k_blend_fwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
         if (Tf) Tf[pix] = S.T[k];
         if (ls) ls[pix] = S.last[k];
         if (ex) ex[pix] = S.exam[k];
+        if (COUNT) {
+            if (px.n_contrib[v]) px.n_contrib[v][pix] = S.contrib[k];
+            if (px.n_eval[v]) px.n_eval[v][pix] = S.eval[k];
+        }
     }
 }
 
@@ -105,9 +109,15 @@ __global__ void k_l1(const float *__restrict__ img, const float *__restrict__ tg
 template <int TILE, int PPT>
 void fwd_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const CamBatch &cb,
                 const PixPtrs &px, const float *bg, cudaStream_t st) {
+    bool count = false;
+    for (int v = 0; v < cb.V; v++) count = count || px.n_contrib[v] || px.n_eval[v];
     count_launch();
-    k_blend_fwd<TILE, PPT><<<cb.total_tiles, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, cb, px,
-                                                                         bg[0], bg[1], bg[2]);
+    if (count)
+        k_blend_fwd<TILE, PPT, true><<<cb.total_tiles, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, cb, px,
+                                                                                   bg[0], bg[1], bg[2]);
+    else
+        k_blend_fwd<TILE, PPT, false><<<cb.total_tiles, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, cb, px,
+                                                                                    bg[0], bg[1], bg[2]);
 }
 
 template <int TILE, int PPT>

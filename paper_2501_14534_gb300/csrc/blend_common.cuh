@@ -35,6 +35,7 @@ struct BlendSmem {
     uint32_t id[NT];  // splat record index
     uint32_t hit[NT]; // bit w: the rect meets warp w's pixel block
     uint32_t cov[NT]; // bit w: the rect covers warp w's pixel block
+    float qmin[NT];   // q below this gives alpha < 1/255: -log2(255 o')
     int maxlast;
 };
 
@@ -75,6 +76,8 @@ __device__ __forceinline__ void stage_splat(BlendSmem<NT> &sm, int slot,
     sm.a[slot] = make_float4(s0.x, s0.y, __fmul_rn(-0.5f * kLog2e, s0.z), __fmul_rn(-kLog2e, s0.w));
     sm.b[slot] = make_float4(__fmul_rn(-0.5f * kLog2e, s1.x), s1.y, s1.z, s1.w);
     sm.c[slot] = s2.x;
+    // o' 2^q < 1/255  <=>  q < -log2(255 o'): the skip test before any exponential
+    sm.qmin[slot] = -log2f(__fmul_rn(255.f, s1.y));
     const uint32_t rx = __float_as_uint(s2.y), ry = __float_as_uint(s2.z);
     const int4 r = make_int4((int)(rx & 0xFFFFu), (int)(rx >> 16), (int)(ry & 0xFFFFu), (int)(ry >> 16));
     sm.rect[slot] = r;
@@ -133,13 +136,14 @@ template <int PPT>
 struct FwdState {
     float T[PPT], Cr[PPT], Cg[PPT], Cb[PPT];
     int last[PPT], exam[PPT];
+    int eval[PPT], contrib[PPT];  // with COUNT: fragments evaluated (pixel in rect), contributing
     bool done[PPT];
 };
 
 // Front-to-back blend of one tile's list [rg.x, rg.y). On return every pixel holds its
 // colour sum, transmittance, last contributor (1-based list position, 0 if none) and the
 // number of list entries it examined.
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool COUNT = false>
 __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
                                              const float4 *__restrict__ splats,
                                              const uint32_t *__restrict__ ids, uint2 rg,
@@ -153,6 +157,7 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
         S.Cr[k] = S.Cg[k] = S.Cb[k] = 0.f;
         S.last[k] = 0;
         S.exam[k] = 0;
+        S.eval[k] = S.contrib[k] = 0;
         S.done[k] = !P.inside[k];
     }
     for (uint32_t base = rg.x; base < rg.y; base += NT) {
@@ -176,17 +181,17 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
             const int4 r = sm.rect[m];
             const bool cover = (sm.cov[m] & P.wbit) != 0u;
             const float4 a = sm.a[m], b = sm.b[m];
-            const float cbl = sm.c[m];
+            const float cbl = sm.c[m], qmin = sm.qmin[m];
             bool fin = false;
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
                 if (S.done[k]) continue;
                 if (!cover && !pix_in(r, P.x[k], P.y[k])) continue;
+                if (COUNT) S.eval[k]++;
                 const float dx = a.x - P.fx[k], dy = a.y - P.fy[k];
                 const float q = frag_q(a.z, a.w, b.x, dx, dy);
-                if (q > 0.f) continue;
+                if (q > 0.f || q < qmin) continue;   // alpha < 1/255: skipped
                 const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, ex2_approx(q)));
-                if (alpha < kAlphaMin) continue;
                 const float tT = __fmul_rn(S.T[k], __fsub_rn(1.f, alpha));
                 if (tT < kTMin) {
                     S.done[k] = true;
@@ -194,6 +199,7 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
                     fin = true;
                     continue;
                 }
+                if (COUNT) S.contrib[k]++;
                 const float w = __fmul_rn(alpha, S.T[k]);
                 S.Cr[k] = __fmaf_rn(b.z, w, S.Cr[k]);
                 S.Cg[k] = __fmaf_rn(b.w, w, S.Cg[k]);
@@ -280,15 +286,14 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
     constexpr int NT = TILE * TILE / PPT;
     const unsigned full = 0xffffffffu;
     const int t = threadIdx.x, lane = t & 31;
-    float T[PPT], acR[PPT], acG[PPT], acB[PPT], la[PPT], lR[PPT], lG[PPT], lB[PPT], bgdot[PPT];
+    // acc = colour of the fragments behind the current one, blended among themselves
+    float T[PPT], acR[PPT], acG[PPT], acB[PPT], tbg[PPT];
     int mymax = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
         T[k] = in.Tfin[k];
         acR[k] = acG[k] = acB[k] = 0.f;
-        la[k] = 0.f;
-        lR[k] = lG[k] = lB[k] = 0.f;
-        bgdot[k] = bg0 * in.dR[k] + bg1 * in.dG[k] + bg2 * in.dB[k];
+        tbg[k] = in.Tfin[k] * (bg0 * in.dR[k] + bg1 * in.dG[k] + bg2 * in.dB[k]);
         mymax = max(mymax, in.last[k]);
     }
     const int wmax = __reduce_max_sync(full, mymax);
@@ -318,7 +323,11 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
             const int4 r = sm.rect[m];
             const bool cover = (sm.cov[m] & P.wbit) != 0u;
             const float4 a = sm.a[m], b = sm.b[m];
-            const float cbl = sm.c[m];
+            const float cbl = sm.c[m], qmin = sm.qmin[m];
+            // per-warp sums over the pixels of u = dL/da G (for the unclamped fragments):
+            // g[0] = sum u dx, g[1] = sum u dy, g[2] = sum u dx^2, g[3] = sum u dx dy,
+            // g[4] = sum u dy^2, g[5] = sum u, g[6..8] = dL/d rgb; turned into the gradients
+            // of mean2d, conic and opacity after the reduction
             float g[9];
 #pragma unroll
             for (int e = 0; e < 9; e++) g[e] = 0.f;
@@ -329,11 +338,10 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
                 if (!cover && !pix_in(r, P.x[k], P.y[k])) continue;
                 const float dx = a.x - P.fx[k], dy = a.y - P.fy[k];
                 const float q = frag_q(a.z, a.w, b.x, dx, dy);
-                if (q > 0.f) continue;
+                if (q > 0.f || q < qmin) continue;   // skipped in the forward too
                 const float G = ex2_approx(q);
                 const float x = __fmul_rn(b.y, G);
                 const float alpha = fminf(kAlphaMax, x);
-                if (alpha < kAlphaMin) continue;
                 contrib = true;
                 const float inv = __fdividef(1.f, 1.f - alpha);
                 T[k] *= inv;                         // transmittance in front of this fragment
@@ -341,33 +349,41 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
                 g[6] = fmaf(w, in.dR[k], g[6]);
                 g[7] = fmaf(w, in.dG[k], g[7]);
                 g[8] = fmaf(w, in.dB[k], g[8]);
-                acR[k] = fmaf(la[k], lR[k] - acR[k], acR[k]);   // colour behind this fragment
-                acG[k] = fmaf(la[k], lG[k] - acG[k], acG[k]);
-                acB[k] = fmaf(la[k], lB[k] - acB[k], acB[k]);
+                // dC/da = T (c - acc) - T_final / (1 - a) bg, acc = colour behind this fragment
                 float dLda = (b.z - acR[k]) * in.dR[k] + (b.w - acG[k]) * in.dG[k] + (cbl - acB[k]) * in.dB[k];
-                dLda = dLda * T[k] - in.Tfin[k] * inv * bgdot[k];
-                la[k] = alpha;
-                lR[k] = b.z;
-                lG[k] = b.w;
-                lB[k] = cbl;
+                dLda = fmaf(dLda, T[k], -tbg[k] * inv);
+                acR[k] = fmaf(alpha, b.z - acR[k], acR[k]);   // now includes this fragment
+                acG[k] = fmaf(alpha, b.w - acG[k], acG[k]);
+                acB[k] = fmaf(alpha, cbl - acB[k], acB[k]);
                 if (x <= kAlphaMax) {
-                    // dL/dpower = dL/da * o G; -a dx - b dy = ln2 (2A dx + B dy) in the scaled conic
-                    const float dLdp = dLda * x;
-                    const float s = dLdp * kLn2;
-                    const float h = -0.5f * dLdp;
-                    g[5] = fmaf(dLda, G, g[5]);
-                    g[0] = fmaf(s, fmaf(2.f * a.z, dx, a.w * dy), g[0]);
-                    g[1] = fmaf(s, fmaf(2.f * b.x, dy, a.w * dx), g[1]);
-                    g[2] = fmaf(h * dx, dx, g[2]);
-                    g[3] = fmaf(-dLdp * dx, dy, g[3]);
-                    g[4] = fmaf(h * dy, dy, g[4]);
+                    const float u = dLda * G;
+                    const float ux = u * dx, uy = u * dy;
+                    g[5] += u;
+                    g[0] += ux;
+                    g[1] += uy;
+                    g[2] = fmaf(ux, dx, g[2]);
+                    g[3] = fmaf(ux, dy, g[3]);
+                    g[4] = fmaf(uy, dy, g[4]);
                 }
             }
             if (__ballot_sync(full, contrib) == 0u) continue;
             float *dst = sgrads + 12 * (size_t)sm.id[m];
             warp_transpose_reduce8(g, lane);
             const float gb = warp_sum(g[8]);
-            if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), g[0]);
+            // lane 4j holds the total of value j. dL/dpower = o' u; with the scaled conic
+            // -a dx - b dy = ln2 (2A dx + B dy), -c dy - b dx = ln2 (2C dy + B dx)
+            const int j = lane >> 2;
+            const float Sx = __shfl_sync(full, g[0], 0), Sy = __shfl_sync(full, g[0], 4);
+            const float o = b.y;
+            // branch-free per lane: j = 0, 1 mean2d; 2, 3, 4 conic; 5 opacity; 6, 7 rgb
+            const float lin = (j == 0) ? fmaf(2.f * a.z, Sx, a.w * Sy) : fmaf(2.f * b.x, Sy, a.w * Sx);
+            const float sc = (j < 2) ? o * kLn2 : ((j == 3) ? -o : ((j == 2 || j == 4) ? -0.5f * o : 1.f));
+            const float val = sc * ((j < 2) ? lin : g[0]);
+            // lanes 0 and 16 collect values 0..3 and 4..7; three 16-byte atomics per splat
+            const float v1 = __shfl_down_sync(full, val, 4), v2 = __shfl_down_sync(full, val, 8),
+                        v3 = __shfl_down_sync(full, val, 12);
+            if ((lane & 15) == 0)
+                atomicAdd(reinterpret_cast<float4 *>(dst + (lane >> 2)), make_float4(val, v1, v2, v3));
             if (lane == 0) atomicAdd(dst + 8, gb);
           }
         }

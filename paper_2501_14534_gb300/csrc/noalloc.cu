@@ -20,17 +20,18 @@ constexpr int64_t kKeys = TGS_NOALLOC_MAX_KEYS;
 // same sizes as radix_hist_needed / scan_partials_needed in sort.cu (checked at set-up)
 constexpr int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 constexpr int64_t kItems = kRec > kKeys ? kRec : kKeys;
-constexpr int64_t kHist = 256 * ceil_div(kItems, 4096) + 1;
+constexpr int64_t kHist = 256 * ceil_div(kItems, 2048) + 1;
 constexpr int64_t kPartials = ceil_div(kHist > kItems ? kHist : kItems, 2048) + 1;
 // word offsets inside the scratch array
 constexpr int64_t oTT = 0, oDB = oTT + kRec, oPOS = oDB + kRec, oCK0 = oPOS + kRec,
                   oCV0 = oCK0 + kRec, oCK1 = oCV0 + kRec, oCV1 = oCK1 + kRec,
                   oOFF = oCV1 + kRec, oTK0 = oOFF + kRec, oTV0 = oTK0 + kKeys,
-                  oTK1 = oTV0 + kKeys, oTV1 = oTK1 + kKeys, oHIST = oTV1 + kKeys,
+                  oTK1 = oTV0 + kKeys, oTV1 = oTK1 + kKeys, oKM = oTV1 + kKeys,
+                  oHIST = oKM + 2 * kRec,
                   oPART = oHIST + kHist, oCNT = oPART + kPartials, oSTAT = oCNT + 4,
                   kWords = oSTAT + 4;
 
-// The scratch of every tgs_bin_noalloc call on a device (about 12.2 MB, held until exit).
+// The scratch of every tgs_bin_noalloc call on a device (about 13.4 MB, held until exit).
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kWords];
 
 constexpr int kMaxDevices = 64;
@@ -113,7 +114,7 @@ extern "C" tgs_status tgs_bin_noalloc(const float *splats, const int32_t *radii,
     derive_touched(reinterpret_cast<const float4 *>(splats), radii, nt, tile, w + oTT, w + oDB, st);
     scan_flags(w + oTT, nt, w + oPOS, cnt + 0, w + oPART, st);
     compact_visible(w + oTT, w + oDB, w + oPOS, nt, reinterpret_cast<const float4 *>(splats), tile,
-                    w + oCK0, w + oCV0, st);
+                    w + oCK0, w + oCV0, reinterpret_cast<uint2 *>(w + oKM), st);
     uint32_t *k = w + oCK0, *v = w + oCV0;
     radix_sort_pairs(k, v, w + oCK1, w + oCV1, cnt + 0, nt, 0, 32, w + oHIST, w + oPART, st);
     gather_tiles_scan(v, w + oTT, cnt + 0, nt, w + oOFF, cnt + 1, w + oPART, nullptr, st);
@@ -130,8 +131,8 @@ extern "C" tgs_status tgs_bin_noalloc(const float *splats, const int32_t *radii,
     if (K > capacity) return TGS_ERR_CAPACITY;
 
     const int64_t cap = K > 0 ? K : 1;
-    emit_keys(v, w + oOFF, cnt + 0, nt, reinterpret_cast<const float4 *>(splats), n, cb, w + oTK0,
-              w + oTV0, cnt + 1, cap, status, st);
+    emit_keys(v, w + oOFF, cnt + 0, nt, reinterpret_cast<const float4 *>(splats), n, cb,
+              reinterpret_cast<const uint2 *>(w + oKM), w + oTK0, w + oTV0, cnt + 1, cap, status, st);
     uint32_t *tk = w + oTK0, *tv = w + oTV0;
     radix_sort_pairs(tk, tv, w + oTK1, w + oTV1, cnt + 1, cap, 0, bits_for_tiles(cb.total_tiles),
                      w + oHIST, w + oPART, st);

@@ -313,7 +313,13 @@ __device__ __forceinline__ void out_write(float *p, int64_t idx, float v, int ac
     if (acc) p[idx] += v; else p[idx] = v;
 }
 
-__global__ void __launch_bounds__(128) k_preprocess_bwd(GaussPtrs g, const __grid_constant__ CamBatch cb,
+constexpr int kBwdThreads = 128;
+
+// Two forms of the same backward, chosen by the number of views of the launch: with many
+// views the 45 dL/d sh_rest accumulators and the coefficients stay in registers (fewer
+// instructions per view); with one or two views they live in shared memory and cache (fewer
+// registers, higher occupancy).
+__global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_reg(GaussPtrs g, const __grid_constant__ CamBatch cb,
                                                         const float4 *__restrict__ sgrads,
                                                         const int32_t *__restrict__ radii,
                                                         GradPtrs out, int no_sh_rest) {
@@ -517,6 +523,220 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(GaussPtrs g, const __gri
     for (int l = 0; l < 3; l++) out_write(out.shmask, 3 * i + l, g_shm[l], acc);
 }
 
+
+__global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_smem(GaussPtrs g, const __grid_constant__ CamBatch cb,
+                                                        const float4 *__restrict__ sgrads,
+                                                        const int32_t *__restrict__ radii,
+                                                        GradPtrs out, int no_sh_rest) {
+    // dL/d sh_rest accumulates in shared memory ([coefficient][thread]: no bank conflicts)
+    // and the SH coefficients are re-read per view from cache, to keep registers for the rest
+    __shared__ float s_gf[45][kBwdThreads];
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const int tid = threadIdx.x;
+    const int64_t n = g.n;
+    GaussState s = load_state(g, i);
+    float3 g_mu = make_float3(0.f, 0.f, 0.f);
+    float g_S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (full-matrix entries)
+    float g_op = 0.f;
+    float3 g_dc = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 45; j++) s_gf[j][tid] = 0.f;
+    const float *fr = g.sh_rest ? g.sh_rest + 45 * i : nullptr;
+    float g_band[4] = {0.f, 0.f, 0.f, 0.f};
+    float st_acc = 0.f;
+    int st_cnt = 0, st_max = 0;
+    bool any = false;
+    if (s.ok) {
+        const float3 dc = make_float3(g.sh_dc[3 * i], g.sh_dc[3 * i + 1], g.sh_dc[3 * i + 2]);
+        for (int v = 0; v < cb.V; v++) {
+            const int64_t r = (int64_t)v * n + i;
+            const int rad = radii[r];
+            if (rad <= 0) continue;
+            const DevCam &c = cb.c[v];
+            ViewGeom vg;
+            if (!view_geom(s, c, g.near_z, vg)) continue;  // cannot happen when rad > 0
+            any = true;
+            float4 ga = sgrads[3 * r], gb4 = sgrads[3 * r + 1], gc4 = sgrads[3 * r + 2];
+            float gmx = ga.x, gmy = ga.y, gca = ga.z, gcb = ga.w, gcc = gb4.x;
+            g_op += gb4.y;
+            float3 g_rgb = make_float3(gb4.z, gb4.w, gc4.x);
+            st_acc += sqrtf(gmx * gmx + gmy * gmy);
+            st_cnt += 1;
+            st_max = max(st_max, rad);
+
+            // ---- colour ----
+            float dx = s.mu.x - c.campos[0], dy = s.mu.y - c.campos[1], dz = s.mu.z - c.campos[2];
+            float dn = sqrtf(dx * dx + dy * dy + dz * dz);
+            float inv = 1.f / dn;
+            float x = dx * inv, y = dy * inv, z = dz * inv;
+            float Y[16];
+            sh_basis(x, y, z, Y);
+            float3 raw = make_float3(0.5f + Y[0] * dc.x, 0.5f + Y[0] * dc.y, 0.5f + Y[0] * dc.z);
+#pragma unroll
+            for (int k = 1; k < 16; k++) {
+                if (!fr || !s.band[band_of(k)]) continue;
+                raw.x += Y[k] * __ldg(fr + 3 * (k - 1));
+                raw.y += Y[k] * __ldg(fr + 3 * (k - 1) + 1);
+                raw.z += Y[k] * __ldg(fr + 3 * (k - 1) + 2);
+            }
+            float3 gr = make_float3(raw.x < 0.f ? 0.f : g_rgb.x, raw.y < 0.f ? 0.f : g_rgb.y,
+                                    raw.z < 0.f ? 0.f : g_rgb.z);
+            g_dc.x += Y[0] * gr.x;
+            g_dc.y += Y[0] * gr.y;
+            g_dc.z += Y[0] * gr.z;
+            float3 g_dir = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 1; k < 16; k++) {
+                const int l = band_of(k);
+                if (!fr || l > s.deg) continue;
+                const float f0 = __ldg(fr + 3 * (k - 1)), f1 = __ldg(fr + 3 * (k - 1) + 1),
+                            f2 = __ldg(fr + 3 * (k - 1) + 2);
+                const float sk = f0 * gr.x + f1 * gr.y + f2 * gr.z;
+                g_band[l] += Y[k] * sk;
+                if (!s.band[l]) continue;
+                s_gf[3 * (k - 1)][tid] += Y[k] * gr.x;
+                s_gf[3 * (k - 1) + 1][tid] += Y[k] * gr.y;
+                s_gf[3 * (k - 1) + 2][tid] += Y[k] * gr.z;
+                sh_basis_grad_add(k, x, y, z, sk, g_dir);
+            }
+            float dd = g_dir.x * x + g_dir.y * y + g_dir.z * z;
+            g_mu.x += (g_dir.x - x * dd) * inv;
+            g_mu.y += (g_dir.y - y * dd) * inv;
+            g_mu.z += (g_dir.z - z * dd) * inv;
+
+            // ---- conic -> Sigma': G = -Q dL/dQ Q, dL/dQ = [[ga, gb/2], [gb/2, gc]] ----
+            float a = vg.ca, b = vg.cb, cc = vg.cc;
+            float G00 = -(a * a * gca + a * b * gcb + b * b * gcc);
+            float G01 = -(a * b * gca + 0.5f * (b * b + a * cc) * gcb + b * cc * gcc);
+            float G11 = -(b * b * gca + b * cc * gcb + cc * cc * gcc);
+            // ---- Sigma' = T Sigma T^T: dL/dSigma = T^T G T ----
+            const float *T0 = vg.T0, *T1 = vg.T1;
+            // full-matrix entries (a,b) for a <= b: xx, xy, xz, yy, yz, zz
+            const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+            for (int e = 0; e < 6; e++) {
+                int p = ia[e], q = ib[e];
+                g_S[e] += T0[p] * T0[q] * G00 + (T0[p] * T1[q] + T1[p] * T0[q]) * G01 + T1[p] * T1[q] * G11;
+            }
+            // dL/dT = 2 G T Sigma
+            const float *S = s.S;
+            float sT0[3] = {S[0] * T0[0] + S[1] * T0[1] + S[2] * T0[2],
+                            S[1] * T0[0] + S[3] * T0[1] + S[4] * T0[2],
+                            S[2] * T0[0] + S[4] * T0[1] + S[5] * T0[2]};
+            float sT1[3] = {S[0] * T1[0] + S[1] * T1[1] + S[2] * T1[2],
+                            S[1] * T1[0] + S[3] * T1[1] + S[4] * T1[2],
+                            S[2] * T1[0] + S[4] * T1[1] + S[5] * T1[2]};
+            float GT0[3], GT1[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                GT0[k] = 2.f * (G00 * sT0[k] + G01 * sT1[k]);
+                GT1[k] = 2.f * (G01 * sT0[k] + G11 * sT1[k]);
+            }
+            // dL/dJ = dL/dT W^T (entries 00, 02, 11, 12)
+            const float *W = c.R;
+            float GJ00 = GT0[0] * W[0] + GT0[1] * W[1] + GT0[2] * W[2];
+            float GJ02 = GT0[0] * W[6] + GT0[1] * W[7] + GT0[2] * W[8];
+            float GJ11 = GT1[0] * W[3] + GT1[1] * W[4] + GT1[2] * W[5];
+            float GJ12 = GT1[0] * W[6] + GT1[1] * W[7] + GT1[2] * W[8];
+            float itz = vg.inv_tz, itz2 = itz * itz;
+            float g_tx = 0.f, g_ty = 0.f, g_tz = 0.f;
+            g_tz += -c.fx * itz2 * GJ00 - c.fy * itz2 * GJ11;
+            // J02 = -fx u / tz, u = clamp(tx / tz)
+            float du_dtx = vg.cx_on ? 0.f : itz, du_dtz = vg.cx_on ? 0.f : -vg.tx * itz2;
+            float dw_dty = vg.cy_on ? 0.f : itz, dw_dtz = vg.cy_on ? 0.f : -vg.ty * itz2;
+            g_tx += GJ02 * (-c.fx * itz) * du_dtx;
+            g_tz += GJ02 * (c.fx * vg.u * itz2 - c.fx * itz * du_dtz);
+            g_ty += GJ12 * (-c.fy * itz) * dw_dty;
+            g_tz += GJ12 * (c.fy * vg.w * itz2 - c.fy * itz * dw_dtz);
+            // mean2d = f t / tz + c - 1/2
+            g_tx += gmx * c.fx * itz;
+            g_ty += gmy * c.fy * itz;
+            g_tz += -(gmx * c.fx * vg.tx + gmy * c.fy * vg.ty) * itz2;
+            // t = W mu + tau
+            g_mu.x += W[0] * g_tx + W[3] * g_ty + W[6] * g_tz;
+            g_mu.y += W[1] * g_tx + W[4] * g_ty + W[7] * g_tz;
+            g_mu.z += W[2] * g_tx + W[5] * g_ty + W[8] * g_tz;
+        }
+    }
+    const int acc = out.accumulate;
+    // ---- statistics (always accumulated) ----
+    if (st_cnt > 0) {
+        if (out.stat_accum) out.stat_accum[i] += st_acc;
+        if (out.stat_count) out.stat_count[i] += st_cnt;
+        if (out.stat_maxr) out.stat_maxr[i] = max(out.stat_maxr[i], st_max);
+    }
+    float g_q[4] = {0.f, 0.f, 0.f, 0.f}, g_ls[3] = {0.f, 0.f, 0.f}, g_o = 0.f, g_m = 0.f;
+    float g_shm[3] = {0.f, 0.f, 0.f};
+    if (any) {
+        // ---- Sigma = (R S)(R S)^T: dL/d(RS) = (G + G^T)(RS), G symmetric here ----
+        const float *R = s.R;
+        float Gf[9] = {g_S[0], g_S[1], g_S[2], g_S[1], g_S[3], g_S[4], g_S[2], g_S[4], g_S[5]};
+        // Gf holds the full-matrix gradient with both off-diagonal entries equal to the
+        // gradient of one entry, so (G + G^T) = 2 Gf.
+        float g_s[3] = {0.f, 0.f, 0.f}, GR[9];
+#pragma unroll
+        for (int rr = 0; rr < 3; rr++)
+#pragma unroll
+            for (int cc = 0; cc < 3; cc++) {
+                float acc2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 3; k++) acc2 += 2.f * Gf[3 * rr + k] * R[3 * k + cc] * s.scale[cc];
+                g_s[cc] += acc2 * R[3 * rr + cc];
+                GR[3 * rr + cc] = acc2 * s.scale[cc];
+            }
+        // dR/dq for q = (w, x, y, z)
+        float w = s.qn[0], x = s.qn[1], y = s.qn[2], z = s.qn[3];
+        float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+        float gx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] + w * GR[7] - 2.f * x * GR[8]);
+        float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6] + z * GR[7] - 2.f * y * GR[8]);
+        float gz = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] + y * GR[5] + x * GR[6] + y * GR[7]);
+        float qd = gw * w + gx * x + gy * y + gz * z;
+        float iq = 1.f / s.qnorm;
+        g_q[0] = (gw - w * qd) * iq;
+        g_q[1] = (gx - x * qd) * iq;
+        g_q[2] = (gy - y * qd) * iq;
+        g_q[3] = (gz - z * qd) * iq;
+        float gM = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            g_ls[k] = g_s[k] * s.scale[k];
+            gM += g_s[k] * s.scale[k];  // exp(l_k) = scale_k since M = 1 here
+        }
+        g_o = g_op * s.M * s.sig_o * (1.f - s.sig_o);
+        gM += g_op * s.sig_o;
+        if (g.mask) {
+            float sm = sigmoidf_(g.mask[i]);
+            g_m = gM * sm * (1.f - sm);
+        }
+        if (g.shmask)
+#pragma unroll
+            for (int l = 1; l <= 3; l++) {
+                if (l > s.deg) continue;
+                float sm = sigmoidf_(g.shmask[3 * i + l - 1]);
+                g_shm[l - 1] = g_band[l] * sm * (1.f - sm);
+            }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        out_write(out.means, 3 * i + k, k == 0 ? g_mu.x : (k == 1 ? g_mu.y : g_mu.z), acc);
+        out_write(out.log_scales, 3 * i + k, g_ls[k], acc);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) out_write(out.quats, 4 * i + k, g_q[k], acc);
+    out_write(out.opac, i, g_o, acc);
+    out_write(out.sh_dc, 3 * i + 0, g_dc.x, acc);
+    out_write(out.sh_dc, 3 * i + 1, g_dc.y, acc);
+    out_write(out.sh_dc, 3 * i + 2, g_dc.z, acc);
+    if (out.sh_rest && !no_sh_rest) {
+#pragma unroll
+        for (int j = 0; j < 45; j++) out_write(out.sh_rest, 45 * i + j, s_gf[j][tid], acc);
+    }
+    out_write(out.mask, i, g_m, acc);
+#pragma unroll
+    for (int l = 0; l < 3; l++) out_write(out.shmask, 3 * i + l, g_shm[l], acc);
+}
+
 }  // namespace
 
 void launch_preprocess(const GaussPtrs &g, const CamBatch &cb, float4 *splats, int32_t *radii,
@@ -534,10 +754,13 @@ void launch_preprocess_backward(const GaussPtrs &g, const CamBatch &cb, const fl
                                 const int32_t *radii, const GradPtrs &out, int no_sh_rest,
                                 cudaStream_t st) {
     if (g.n <= 0) return;
-    const int bs = 128;
+    const int bs = kBwdThreads;
     const int64_t grid = (g.n + bs - 1) / bs;
     count_launch();
-    k_preprocess_bwd<<<(unsigned)grid, bs, 0, st>>>(g, cb, sgrads, radii, out, no_sh_rest);
+    if (cb.V <= 2)
+        k_preprocess_bwd_smem<<<(unsigned)grid, bs, 0, st>>>(g, cb, sgrads, radii, out, no_sh_rest);
+    else
+        k_preprocess_bwd_reg<<<(unsigned)grid, bs, 0, st>>>(g, cb, sgrads, radii, out, no_sh_rest);
 }
 
 }  // namespace tgs

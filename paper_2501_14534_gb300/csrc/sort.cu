@@ -19,8 +19,8 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;   // 2048
 constexpr int kRadixThreads = 256;
-constexpr int kRadixRounds = 16;
-constexpr int kRadixTile = kRadixThreads * kRadixRounds;  // 4096
+constexpr int kRadixRounds = 8;
+constexpr int kRadixTile = kRadixThreads * kRadixRounds;  // 2048
 constexpr int kRadixBins = 256;
 
 __device__ __forceinline__ int64_t count_of(const uint32_t *n_dev, int64_t n_cap) {
@@ -142,16 +142,26 @@ void scan_generic(Load ld, const uint32_t *n_dev, int64_t n_cap, uint32_t *out, 
 
 // Compacts the visible records for the depth sort and replaces each visibility flag by the
 // record's number of keys: the tiles of its rect that pass the cull test.
+// For rects of at most 64 tiles it also stores which tiles (row-major within the rect) passed,
+// so that the emission does not repeat the test.
 __global__ void k_compact(uint32_t *__restrict__ tt, const uint32_t *__restrict__ db,
                           const uint32_t *__restrict__ pos, int64_t n, const float4 *__restrict__ splats,
-                          int B, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                          int B, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                          uint2 *__restrict__ kmask) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || tt[i] == 0u) return;
     const uint32_t p = pos[i];
     keys[p] = db[i];
     vals[p] = (uint32_t)i;
     const float4 *rp = splats + (size_t)kSplatWords / 4 * i;
-    tt[i] = (uint32_t)for_kept_tiles(rp[0], rp[1], rp[2], rp[3], B, [](int, int) {});
+    const uint32_t rx = __float_as_uint(rp[2].y);
+    const int x0 = (int)(rx & 0xFFFFu) / B, nx = (int)(rx >> 16) / B - x0 + 1;
+    uint64_t m = 0;
+    tt[i] = (uint32_t)for_kept_tiles(rp[0], rp[1], rp[2], rp[3], B, [&](int tx, int ty) {
+        const int b = (ty - ((int)(__float_as_uint(rp[2].z) & 0xFFFFu) / B)) * nx + (tx - x0);
+        if (b < 64) m |= (uint64_t)1 << b;
+    });
+    if (kmask) kmask[i] = make_uint2((uint32_t)m, (uint32_t)(m >> 32));
 }
 
 // ---- radix sort -------------------------------------------------------------------------
@@ -173,9 +183,10 @@ k_radix_hist(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int64_t n
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_h[threadIdx.x];
 }
 
-// Stable scatter: items are ranked in index order. Within a round of 256 consecutive items
-// the rank of an item among equal digits is (equal digits in earlier rounds of this block)
-// + (equal digits in earlier warps of this round) + (equal digits in earlier lanes).
+// Stable scatter of one block of 2048 items. The block's items are first ranked into shared
+// memory in (digit, index) order -- rank = start of the digit in the block + equal digits in
+// earlier rounds + earlier warps of this round + earlier lanes -- and then written out in
+// that order, so that each digit's run of this block goes to consecutive global addresses.
 __global__ void __launch_bounds__(kRadixThreads)
 k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 const uint32_t *n_dev, int64_t n_cap, int shift, uint32_t mask,
@@ -183,74 +194,154 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
                 uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out) {
     constexpr int NW = kRadixThreads / 32;
     __shared__ uint32_t s_cnt[NW][kRadixBins];
-    __shared__ uint32_t s_base[kRadixBins];
+    __shared__ uint32_t s_run[kRadixBins];     // items of each digit placed so far
+    __shared__ uint32_t s_start[kRadixBins];   // start of each digit in the block's order
+    __shared__ uint32_t s_goff[kRadixBins];    // global position of the block's digit run
+    __shared__ uint32_t s_warp[33];
+    __shared__ uint32_t s_k[kRadixTile], s_v[kRadixTile];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    s_base[t] = offsets[(int64_t)t * nblocks + blockIdx.x];
-#pragma unroll
-    for (int k = 0; k < NW; k++) s_cnt[k][t] = 0u;
-    __syncthreads();
     const int64_t n = count_of(n_dev, n_cap);
     const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-    if (base >= n) return;
-    const uint32_t lt_mask = (1u << lane) - 1u;
+    if (base >= n) return;  // uniform across the block
+    const int cnt = (int)((n - base) < kRadixTile ? (n - base) : kRadixTile);
+    uint32_t kr[kRadixRounds], vr[kRadixRounds];
+    s_run[t] = 0u;
+#pragma unroll
+    for (int q = 0; q < NW; q++) s_cnt[q][t] = 0u;
+    __syncthreads();
+#pragma unroll
     for (int r = 0; r < kRadixRounds; r++) {
-        const int64_t i = base + (int64_t)r * kRadixThreads + t;
-        if (base + (int64_t)r * kRadixThreads >= n) break;  // uniform across the block
-        const bool valid = i < n;
-        const uint32_t k = valid ? keys_in[i] : 0xffffffffu;
-        const uint32_t d = valid ? ((k >> shift) & mask) : mask;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const int j = r * kRadixThreads + t;
+        const bool valid = j < cnt;
+        kr[r] = valid ? keys_in[base + j] : 0xffffffffu;
+        vr[r] = valid ? vals_in[base + j] : 0u;
+        if (valid) atomicAdd(&s_run[(kr[r] >> shift) & mask], 1u);
+    }
+    __syncthreads();
+    uint32_t tot;
+    const uint32_t start = block_excl_scan(s_run[t], s_warp, &tot);
+    s_start[t] = start;
+    s_goff[t] = offsets[(int64_t)t * nblocks + blockIdx.x];
+    s_run[t] = 0u;
+    __syncthreads();
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < kRadixRounds; r++) {
+        if (r * kRadixThreads >= cnt) continue;  // uniform: the block's tail rounds are empty
+        const bool valid = r * kRadixThreads + t < cnt;
+        const uint32_t d = valid ? ((kr[r] >> shift) & mask) : mask;
+        // lanes holding the same digit: one ballot per digit bit (warp multisplit)
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 8; b++) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bal : ~bal;
+        }
         const uint32_t wr = __popc(peers & lt_mask);
         if (wr == 0u) s_cnt[w][d] = __popc(peers);
         __syncthreads();
         {
-            // exclusive prefix over warps for digit t, and advance the block base
-            uint32_t acc = s_base[t];
+            uint32_t acc = s_run[t];
 #pragma unroll
             for (int q = 0; q < NW; q++) {
-                uint32_t c = s_cnt[q][t];
+                const uint32_t c = s_cnt[q][t];
                 s_cnt[q][t] = acc;
                 acc += c;
             }
-            s_base[t] = acc;
+            s_run[t] = acc;
         }
         __syncthreads();
         if (valid) {
-            const uint32_t p = s_cnt[w][d] + wr;
-            keys_out[p] = k;
-            vals_out[p] = vals_in[i];
+            const uint32_t lp = s_start[d] + s_cnt[w][d] + wr;
+            s_k[lp] = kr[r];
+            s_v[lp] = vr[r];
         }
         __syncthreads();
 #pragma unroll
         for (int q = 0; q < NW; q++) s_cnt[q][t] = 0u;
         __syncthreads();
     }
+    for (int i = t; i < cnt; i += kRadixThreads) {
+        const uint32_t k = s_k[i];
+        const uint32_t d = (k >> shift) & mask;
+        const uint32_t gp = s_goff[d] + ((uint32_t)i - s_start[d]);
+        keys_out[gp] = k;
+        vals_out[gp] = s_v[i];
+    }
 }
 
 // ---- keys, ranges -------------------------------------------------------------------------
 
-__global__ void k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ offsets,
-                       const uint32_t *n_dev, int64_t n_cap, const float4 *__restrict__ splats,
-                       uint32_t n_gauss, const __grid_constant__ CamBatch cb,
-                       uint32_t *__restrict__ tile_keys, uint32_t *__restrict__ tile_vals,
-                       const uint32_t *K_dev, int64_t key_cap, uint32_t *status) {
+// Key emission. A warp takes 32 consecutive records of the depth order; their keys form one
+// contiguous segment of the key array, which the warp assembles in shared memory and writes
+// out with coalesced stores (segments longer than the buffer are written directly).
+constexpr int kEmitThreads = 256;
+constexpr int kEmitBuf = 512;  // keys staged per warp
+
+__global__ void __launch_bounds__(kEmitThreads)
+k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ offsets,
+       const uint32_t *n_dev, int64_t n_cap, const float4 *__restrict__ splats, uint32_t n_gauss,
+       const __grid_constant__ CamBatch cb, const uint2 *__restrict__ kmask,
+       uint32_t *__restrict__ tile_keys, uint32_t *__restrict__ tile_vals, const uint32_t *K_dev,
+       int64_t key_cap, uint32_t *status) {
+    __shared__ uint32_t s_k[kEmitThreads / 32][kEmitBuf], s_v[kEmitThreads / 32][kEmitBuf];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0 && (int64_t)*K_dev > key_cap) atomicOr(status, kStatusCapacity);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t K = (int64_t)*K_dev;
+    if (i == 0 && K > key_cap) atomicOr(status, kStatusCapacity);
     const int64_t n = count_of(n_dev, n_cap);
-    if (i >= n) return;
-    const uint32_t rec = sorted_ids[i];
-    const int v = (int)(rec / n_gauss);
-    const DevCam &c = cb.c[v];
-    const float4 *rp = splats + (size_t)kSplatWords / 4 * rec;
-    int64_t k = offsets[i];
-    for_kept_tiles(rp[0], rp[1], rp[2], rp[3], cb.tile, [&](int tx, int ty) {
-        if (k < key_cap) {
+    if (i - lane >= n) return;  // the whole warp is past the end
+    const bool valid = i < n;
+    const uint32_t off = valid ? offsets[i] : 0u;
+    const uint32_t end = valid ? (i + 1 < n ? offsets[i + 1] : (uint32_t)K) : 0u;
+    const uint32_t seg0 = __shfl_sync(0xffffffffu, off, 0);
+    const uint32_t seg_end = __reduce_max_sync(0xffffffffu, end);
+    const uint32_t seg_len = seg_end - seg0;
+    const bool staged = seg_len <= (uint32_t)kEmitBuf;
+    if (valid && end > off) {
+        const uint32_t rec = sorted_ids[i];
+        const int v = (int)(rec / n_gauss);
+        const DevCam &c = cb.c[v];
+        const float4 *rp = splats + (size_t)kSplatWords / 4 * rec;
+        const int B = cb.tile;
+        const uint32_t rx = __float_as_uint(rp[2].y), ry = __float_as_uint(rp[2].z);
+        const int x0 = (int)(rx & 0xFFFFu) / B, x1 = (int)(rx >> 16) / B;
+        const int y0 = (int)(ry & 0xFFFFu) / B, y1 = (int)(ry >> 16) / B;
+        const int nx = x1 - x0 + 1;
+        int64_t k = off;
+        auto put = [&](int tx, int ty) {
             const bool ok = tx < c.gx && ty < c.gy;   // records from outside may carry any rect
-            tile_keys[k] = ok ? (uint32_t)(c.tile_offset + ty * c.gx + tx) : 0xffffffffu;
-            tile_vals[k] = rec;
+            const uint32_t key = ok ? (uint32_t)(c.tile_offset + ty * c.gx + tx) : 0xffffffffu;
+            if (staged) {
+                s_k[w][k - seg0] = key;
+                s_v[w][k - seg0] = rec;
+            } else if (k < key_cap) {
+                tile_keys[k] = key;
+                tile_vals[k] = rec;
+            }
+            k++;
+        };
+        if (nx * (y1 - y0 + 1) <= 64) {
+            const uint2 mm = kmask[rec];
+            uint64_t m = ((uint64_t)mm.y << 32) | mm.x;
+            while (m) {
+                const int b = __ffsll((long long)m) - 1;
+                m &= m - 1;
+                put(x0 + b % nx, y0 + b / nx);
+            }
+        } else {
+            for_kept_tiles(rp[0], rp[1], rp[2], rp[3], B, put);
         }
-        k++;
-    });
+    }
+    __syncwarp();
+    if (staged)
+        for (uint32_t j = lane; j < seg_len; j += 32) {
+            const int64_t gp = (int64_t)seg0 + j;
+            if (gp < key_cap) {
+                tile_keys[gp] = s_k[w][j];
+                tile_vals[gp] = s_v[w][j];
+            }
+        }
 }
 
 __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *K_dev, int64_t cap,
@@ -306,11 +397,11 @@ void scan_flags(const uint32_t *tiles_touched, int64_t n_cap, uint32_t *out, uin
 
 void compact_visible(uint32_t *tiles_touched, const uint32_t *depth_bits, const uint32_t *pos,
                      int64_t n_cap, const float4 *splats, int tile, uint32_t *keys, uint32_t *vals,
-                     cudaStream_t st) {
+                     uint2 *kmask, cudaStream_t st) {
     if (n_cap <= 0) return;
     count_launch();
     k_compact<<<blocks_for(n_cap, 256), 256, 0, st>>>(tiles_touched, depth_bits, pos, n_cap, splats, tile,
-                                                      keys, vals);
+                                                      keys, vals, kmask);
 }
 
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint32_t *vals_alt,
@@ -343,14 +434,14 @@ void gather_tiles_scan(const uint32_t *sorted_ids, const uint32_t *tiles_touched
 }
 
 void emit_keys(const uint32_t *sorted_ids, const uint32_t *offsets, const uint32_t *n_dev, int64_t n_cap,
-               const float4 *splats, int64_t n_gauss, const CamBatch &cb, uint32_t *tile_keys,
-               uint32_t *tile_vals, const uint32_t *K_dev, int64_t key_capacity, uint32_t *status,
-               cudaStream_t st) {
+               const float4 *splats, int64_t n_gauss, const CamBatch &cb, const uint2 *kmask,
+               uint32_t *tile_keys, uint32_t *tile_vals, const uint32_t *K_dev, int64_t key_capacity,
+               uint32_t *status, cudaStream_t st) {
     if (n_cap <= 0) return;
     count_launch();
-    k_emit<<<blocks_for(n_cap, 256), 256, 0, st>>>(sorted_ids, offsets, n_dev, n_cap, splats,
-                                                   (uint32_t)n_gauss, cb, tile_keys, tile_vals, K_dev,
-                                                   key_capacity, status);
+    k_emit<<<blocks_for(n_cap, kEmitThreads), kEmitThreads, 0, st>>>(sorted_ids, offsets, n_dev, n_cap, splats,
+                                                                     (uint32_t)n_gauss, cb, kmask, tile_keys,
+                                                                     tile_vals, K_dev, key_capacity, status);
 }
 
 void find_ranges(const uint32_t *tile_keys, const uint32_t *K_dev, int64_t key_capacity, uint2 *ranges,

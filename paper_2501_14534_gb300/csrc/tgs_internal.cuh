@@ -63,6 +63,8 @@ struct PixPtrs {
     int32_t *n_exam[kMaxViews];
     const float *dL[kMaxViews];
     const float *target[kMaxViews];
+    int32_t *n_contrib[kMaxViews];
+    int32_t *n_eval[kMaxViews];
 };
 
 // Kernel launches issued by the library on this host thread (the batched step counts its own).
@@ -174,9 +176,10 @@ size_t radix_hist_needed(int64_t n_items);
 // out[i] = exclusive prefix of in_fn(i) for i < *n_dev; *total = sum. n_cap bounds the grid.
 void scan_flags(const uint32_t *tiles_touched, int64_t n_cap, uint32_t *out, uint32_t *total,
                 uint32_t *partials, cudaStream_t st);
+// Also stores per visible record the kept-tile mask of rects of at most 64 tiles (kmask [nt]).
 void compact_visible(uint32_t *tiles_touched, const uint32_t *depth_bits, const uint32_t *pos,
                      int64_t n_cap, const float4 *splats, int tile, uint32_t *keys, uint32_t *vals,
-                     cudaStream_t st);
+                     uint2 *kmask, cudaStream_t st);
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       const uint32_t *n_dev, int64_t n_cap, int begin_bit, int end_bit,
                       uint32_t *hist, uint32_t *partials, cudaStream_t st);
@@ -185,7 +188,7 @@ void gather_tiles_scan(const uint32_t *sorted_ids, const uint32_t *tiles_touched
                        uint32_t *partials, uint32_t *tmp, cudaStream_t st);
 void emit_keys(const uint32_t *sorted_ids, const uint32_t *offsets, const uint32_t *n_dev,
                int64_t n_cap, const float4 *splats, int64_t n_gauss, const CamBatch &cb,
-               uint32_t *tile_keys, uint32_t *tile_vals, const uint32_t *K_dev,
+               const uint2 *kmask, uint32_t *tile_keys, uint32_t *tile_vals, const uint32_t *K_dev,
                int64_t key_capacity, uint32_t *status, cudaStream_t st);
 void find_ranges(const uint32_t *tile_keys, const uint32_t *K_dev, int64_t key_capacity,
                  uint2 *ranges, int total_tiles, cudaStream_t st);

@@ -155,7 +155,8 @@ class Rasterizer:
 
     # ---- plain path ----------------------------------------------------------------------
 
-    def _alloc_views(self, cams, n, want_state=True, want_examined=False, want_radii=False):
+    def _alloc_views(self, cams, n, want_state=True, want_examined=False, want_radii=False,
+                     want_counts=False):
         outs = []
         for c in cams:
             H, W = c.height, c.width
@@ -167,6 +168,9 @@ class Rasterizer:
                 d["n_examined"] = torch.empty((H, W), device="cuda", dtype=torch.int32)
             if want_radii:
                 d["radii"] = torch.empty((n,), device="cuda", dtype=torch.int32)
+            if want_counts:
+                d["n_contrib"] = torch.empty((H, W), device="cuda", dtype=torch.int32)
+                d["n_eval"] = torch.empty((H, W), device="cuda", dtype=torch.int32)
             outs.append(d)
         return outs
 
@@ -175,12 +179,14 @@ class Rasterizer:
         arr = (B.tgs_view_out * len(outs))()
         for i, d in enumerate(outs):
             arr[i] = B.tgs_view_out(_p(d.get("image")), _p(d.get("T_final")), _p(d.get("last")),
-                                    _p(d.get("n_examined")), _p(d.get("radii")))
+                                    _p(d.get("n_examined")), _p(d.get("radii")),
+                                    _p(d.get("n_contrib")), _p(d.get("n_eval")))
         return arr
 
     def forward(self, g: Gaussians, cams, want_state=True, want_examined=False,
-                want_radii=False, outs=None):
-        outs = outs or self._alloc_views(cams, g.n, want_state, want_examined, want_radii)
+                want_radii=False, want_counts=False, outs=None):
+        outs = outs or self._alloc_views(cams, g.n, want_state, want_examined, want_radii,
+                                         want_counts)
         B.check(B.lib.tgs_forward(self._h, C.byref(g.struct()), cameras_array(cams), len(cams),
                                   self._out_structs(outs), 0, _stream()), "tgs_forward")
         return outs
@@ -266,8 +272,8 @@ class Rasterizer:
         k = int(K.value)
         return ids[:k], (keys[:k] if keys is not None else None), ranges, k
 
-    def blend_forward(self, splats, ids, ranges, cams, want_examined=True):
-        outs = self._alloc_views(cams, 0, True, want_examined)
+    def blend_forward(self, splats, ids, ranges, cams, want_examined=True, want_counts=True):
+        outs = self._alloc_views(cams, 0, True, want_examined, want_counts=want_counts)
         B.check(B.lib.tgs_blend_forward(self._h, _p(splats), _p(ids), _p(ranges),
                                         cameras_array(cams), len(cams), self._out_structs(outs),
                                         _stream()), "tgs_blend_forward")

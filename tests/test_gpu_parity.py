@@ -164,6 +164,8 @@ def test_blend_forward_matches_oracle_on_same_records(R, case):
         clear = ref["margin"] >= 1.0
         assert np.array_equal(np_(outs[v]["last"])[clear], ref["last"][clear])
         assert np.array_equal(np_(outs[v]["n_examined"])[clear], ref["n_examined"][clear])
+        assert np.array_equal(np_(outs[v]["n_contrib"])[clear], ref["n_contrib"][clear])
+        assert np.array_equal(np_(outs[v]["n_eval"])[clear], ref["n_eval"][clear])
         np.testing.assert_allclose(np_(outs[v]["T_final"])[clear], ref["T_final"][clear],
                                    rtol=1e-4, atol=1e-7)
 

@@ -626,7 +626,7 @@ def test_tile_masked_blend_equals_full_blend_on_those_tiles(tile):
     mask[np.random.default_rng(0).choice(gx * gy, size=gx * gy // 3, replace=False)] = 1
     part = oracle.blend(sp, 75, 53, tile, st.bg, margins=True, tile_mask=mask)
     pix = np.repeat(np.repeat(mask.reshape(gy, gx), tile, 0), tile, 1)[:53, :75].astype(bool)
-    for k in ("T_final", "last", "n_contrib", "n_examined", "margin"):
+    for k in ("T_final", "last", "n_contrib", "n_examined", "n_eval", "margin"):
         assert np.array_equal(part[k][pix], full[k][pix]), k
     assert np.array_equal(part["image"][:, pix], full["image"][:, pix])
     w = np.random.default_rng(1).normal(size=(3, 53, 75)) * pix[None]
