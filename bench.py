@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--tile", type=int, default=16)
     p.add_argument("--ppt", type=int, default=1)
+    p.add_argument("--step-only", action="store_true",
+                   help="stop after the timed batched steps (for launch lists under a profiler)")
     return p.parse_args()
 
 
@@ -271,6 +273,15 @@ def main():
     ms_step = ms_total / args.steps
     value = V * world / (ms_step / 1000.0)
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
+
+    if args.step_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "views/s", "partial": True,
+                              "ms_per_step": ms_step, "stage_ms": stage_ms,
+                              "kernels_per_step": kernels}), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
 
     # ---- A/B: the same step with separate forward, loss and backward kernels ----
     rast.set_profiling(False)

@@ -34,6 +34,7 @@ struct BlendSmem {
     int4 rect[NT];    // inclusive pixel rect x_lo, x_hi, y_lo, y_hi
     uint32_t id[NT];  // splat record index
     uint32_t hit[NT]; // bit w: the rect meets warp w's pixel block
+    uint32_t vis[NT]; // bit w: in addition some point of (block x rect) may reach alpha >= 1/255
     uint32_t cov[NT]; // bit w: the rect covers warp w's pixel block
     float qmin[NT];   // q below this gives alpha < 1/255: -log2(255 o')
     int maxlast;
@@ -86,6 +87,20 @@ __device__ __forceinline__ void stage_splat(BlendSmem<NT> &sm, int slot,
     block_masks<TILE, PPT>(r.x, r.y, r.z, r.w, tx0, ty0, hit, cov);
     sm.hit[slot] = hit;
     sm.cov[slot] = cov;
+    // warp blocks whose part of the rect stays below alpha = 1/255 everywhere (the cull test of
+    // the keys, on the block): those warps skip the splat, whose fragments they would skip
+    using L = BlendLayout<TILE, PPT>;
+    const float4 s3 = __ldg(rp + 3);
+    uint32_t vis = hit, bits = hit;
+    while (bits) {
+        const int w = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const int bx0 = tx0 + (w % L::WX) * L::BW, by0 = ty0 + (w / L::WX) * L::BH;
+        if (!tile_keep(s0.x, s0.y, s0.z, s0.w, s1.x, s3.x, s3.y, s3.z, max(bx0, r.x),
+                       min(bx0 + L::BW - 1, r.y), max(by0, r.z), min(by0 + L::BH - 1, r.w)))
+            vis &= ~(1u << w);
+    }
+    sm.vis[slot] = vis;
 }
 
 // Exponent of one fragment, with explicit roundings (no contraction choices left to the
@@ -174,7 +189,9 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
         bool warp_done = false;
         for (int c0 = 0; c0 < cnt && !warp_done; c0 += 32) {
           // the splats of this chunk of 32 that meet this warp's pixel block, in list order
-          uint32_t bits = __ballot_sync(full, (c0 + (t & 31) < cnt) && (sm.hit[c0 + (t & 31)] & P.wbit));
+          // with COUNT every fragment in the rect is evaluated (the counters' definition)
+          uint32_t bits = __ballot_sync(full, (c0 + (t & 31) < cnt) &&
+                                                  ((COUNT ? sm.hit : sm.vis)[c0 + (t & 31)] & P.wbit));
           while (bits) {
             const int m = c0 + __ffs(bits) - 1;
             bits &= bits - 1u;
@@ -315,7 +332,7 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
         const int m0 = max(0, top - wmax);    // positions beyond this warp's last contributors
         for (int c0 = (m0 / 32) * 32; c0 < cnt; c0 += 32) {
           const int mi = c0 + lane;
-          uint32_t bits = __ballot_sync(full, mi >= m0 && mi < cnt && (sm.hit[mi] & P.wbit));
+          uint32_t bits = __ballot_sync(full, mi >= m0 && mi < cnt && (sm.vis[mi] & P.wbit));
           while (bits) {
             const int m = c0 + __ffs(bits) - 1;
             bits &= bits - 1u;

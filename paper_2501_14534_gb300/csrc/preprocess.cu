@@ -339,16 +339,38 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_reg(GaussPtrs g,
     int st_cnt = 0, st_max = 0;
     bool any = false;
     if (s.ok) {
+        // the views where the Gaussian is visible, read up front (independent loads), and the
+        // splat gradients of the next visible view prefetched while this one is processed
+        uint64_t vis = 0;
+#pragma unroll 8
+        for (int v = 0; v < cb.V; v++)
+            if (radii[(int64_t)v * n + i] > 0) vis |= 1ull << v;
         load_sh(g, i, s, sh);
-        for (int v = 0; v < cb.V; v++) {
+        int vnext = vis ? __ffsll((long long)vis) - 1 : -1;
+        float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na, nc = na;
+        if (vnext >= 0) {
+            const int64_t r = (int64_t)vnext * n + i;
+            na = sgrads[3 * r];
+            nb = sgrads[3 * r + 1];
+            nc = sgrads[3 * r + 2];
+        }
+        while (vnext >= 0) {
+            const int v = vnext;
+            const float4 ga = na, gb4 = nb, gc4 = nc;
+            vis &= vis - 1ull;
+            vnext = vis ? __ffsll((long long)vis) - 1 : -1;
+            if (vnext >= 0) {
+                const int64_t rn = (int64_t)vnext * n + i;
+                na = sgrads[3 * rn];
+                nb = sgrads[3 * rn + 1];
+                nc = sgrads[3 * rn + 2];
+            }
             const int64_t r = (int64_t)v * n + i;
             const int rad = radii[r];
-            if (rad <= 0) continue;
             const DevCam &c = cb.c[v];
             ViewGeom vg;
             if (!view_geom(s, c, g.near_z, vg)) continue;  // cannot happen when rad > 0
             any = true;
-            float4 ga = sgrads[3 * r], gb4 = sgrads[3 * r + 1], gc4 = sgrads[3 * r + 2];
             float gmx = ga.x, gmy = ga.y, gca = ga.z, gcb = ga.w, gcc = gb4.x;
             g_op += gb4.y;
             float3 g_rgb = make_float3(gb4.z, gb4.w, gc4.x);
