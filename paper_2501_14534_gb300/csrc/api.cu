@@ -189,7 +189,7 @@ tgs_status ensure_records(tgs_ctx *c, int64_t nt, cudaStream_t st) {
     TGS_TRY(ensure(c->cv0, sizeof(uint32_t) * (size_t)nt, st));
     TGS_TRY(ensure(c->ck1, sizeof(uint32_t) * (size_t)nt, st));
     TGS_TRY(ensure(c->cv1, sizeof(uint32_t) * (size_t)nt, st));
-    TGS_TRY(ensure(c->offsets, sizeof(uint32_t) * (size_t)nt, st));
+    TGS_TRY(ensure(c->offsets, sizeof(uint32_t) * scan_partials_needed(nt), st));  // per block of records
     TGS_TRY(ensure(c->kmask, sizeof(uint2) * (size_t)nt, st));
     TGS_TRY(ensure(c->counts, sizeof(uint32_t) * 4, st));
     size_t h = std::max(radix_hist_needed(nt), (size_t)16);
@@ -214,17 +214,22 @@ tgs_status ensure_keys(tgs_ctx *c, int64_t cap, int total_tiles, cudaStream_t st
 
 // Visibility compaction, depth sort and the key-count scan. Leaves the depth-sorted record
 // ids in *sorted and the key count in counts[1].
+// The per-record arrays free once the visible records are compacted hold the key counts of
+// the depth order.
+KeyInfo key_info(tgs_ctx *c) {
+    return KeyInfo{as<uint32_t>(c->pos), as<uint2>(c->kmask), as<uint32_t>(c->dbits), as<uint32_t>(c->tt)};
+}
+
 void bin_front(tgs_ctx *c, int64_t nt, uint32_t **sorted, cudaStream_t st) {
     uint32_t *cnt = as<uint32_t>(c->counts);
     scan_flags(as<uint32_t>(c->tt), nt, as<uint32_t>(c->pos), cnt + 0, as<uint32_t>(c->partials), st);
     compact_visible(as<uint32_t>(c->tt), as<uint32_t>(c->dbits), as<uint32_t>(c->pos), nt,
-                    as<float4>(c->splats), c->cfg.tile, as<uint32_t>(c->ck0), as<uint32_t>(c->cv0),
-                    as<uint2>(c->kmask), st);
+                    as<uint32_t>(c->ck0), as<uint32_t>(c->cv0), st);
     uint32_t *k = as<uint32_t>(c->ck0), *v = as<uint32_t>(c->cv0);
     radix_sort_pairs(k, v, as<uint32_t>(c->ck1), as<uint32_t>(c->cv1), cnt + 0, nt, 0, 32,
                      as<uint32_t>(c->hist), as<uint32_t>(c->partials), st);
-    gather_tiles_scan(v, as<uint32_t>(c->tt), cnt + 0, nt, as<uint32_t>(c->offsets), cnt + 1,
-                      as<uint32_t>(c->partials), nullptr, st);
+    count_keys(v, cnt + 0, nt, as<float4>(c->splats), c->cfg.tile, key_info(c), as<uint32_t>(c->offsets),
+               cnt + 1, st);
     *sorted = v;
 }
 
@@ -232,9 +237,8 @@ void bin_front(tgs_ctx *c, int64_t nt, uint32_t **sorted, cudaStream_t st) {
 uint32_t *bin_back(tgs_ctx *c, int64_t nt, int64_t n, const uint32_t *sorted, const CamBatch &cb,
                    int64_t cap, cudaStream_t st) {
     uint32_t *cnt = as<uint32_t>(c->counts);
-    emit_keys(sorted, as<uint32_t>(c->offsets), cnt + 0, nt, as<float4>(c->splats), n, cb,
-              as<uint2>(c->kmask), as<uint32_t>(c->tk0), as<uint32_t>(c->tv0), cnt + 1, cap,
-              as<uint32_t>(c->status), st);
+    emit_keys(sorted, as<uint32_t>(c->offsets), cnt + 0, nt, key_info(c), as<float4>(c->splats), n, cb,
+              as<uint32_t>(c->tk0), as<uint32_t>(c->tv0), cnt + 1, cap, as<uint32_t>(c->status), st);
     uint32_t *k = as<uint32_t>(c->tk0), *v = as<uint32_t>(c->tv0);
     radix_sort_pairs(k, v, as<uint32_t>(c->tk1), as<uint32_t>(c->tv1), cnt + 1, cap, 0,
                      bits_for(cb.total_tiles), as<uint32_t>(c->hist), as<uint32_t>(c->partials), st);
@@ -710,7 +714,7 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
     } else {
         mark(c, stage++, "item_order", st);
         uint32_t *it = as<uint32_t>(c->items);
-        const size_t T = (size_t)cb.total_tiles;
+        const size_t T = ((size_t)cb.total_tiles + 3) / 4 * 4;  // 16-byte aligned quarters
         uint32_t *order = nullptr;
         build_item_order(as<uint2>(c->ranges), cb.total_tiles, it, it + T, it + 2 * T, it + 3 * T, &order,
                          as<uint32_t>(c->hist), as<uint32_t>(c->partials), st);
@@ -753,7 +757,7 @@ tgs_status tgs_train_step_batched(tgs_ctx *c, const tgs_gaussians *g, const tgs_
     TGS_TRY(ensure(c->images, sizeof(float) * 3 * pix, st));
     TGS_TRY(ensure(c->dimg, sizeof(float) * 3 * pix, st));
     TGS_TRY(ensure(c->pixstate, sizeof(float) * 2 * pix, st));
-    TGS_TRY(ensure(c->items, sizeof(uint32_t) * 4 * (size_t)std::max(cb.total_tiles, 1), st));
+    TGS_TRY(ensure(c->items, sizeof(uint32_t) * 4 * (((size_t)std::max(cb.total_tiles, 1) + 3) / 4 * 4), st));
     c->state_valid = false;
 
     if (!(flags & TGS_USE_GRAPH) || st == nullptr || capturing(st))

@@ -19,16 +19,17 @@ constexpr int64_t kRec = TGS_NOALLOC_MAX_RECORDS;
 constexpr int64_t kKeys = TGS_NOALLOC_MAX_KEYS;
 // same sizes as radix_hist_needed / scan_partials_needed in sort.cu (checked at set-up)
 constexpr int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+constexpr int64_t round4(int64_t a) { return (a + 3) / 4 * 4; }  // 16-byte aligned regions
 constexpr int64_t kItems = kRec > kKeys ? kRec : kKeys;
 constexpr int64_t kHist = 256 * ceil_div(kItems, 2048) + 1;
 constexpr int64_t kPartials = ceil_div(kHist > kItems ? kHist : kItems, 2048) + 1;
+constexpr int64_t kBlockOffs = ceil_div(kRec, 2048) + 1;
 // word offsets inside the scratch array
 constexpr int64_t oTT = 0, oDB = oTT + kRec, oPOS = oDB + kRec, oCK0 = oPOS + kRec,
                   oCV0 = oCK0 + kRec, oCK1 = oCV0 + kRec, oCV1 = oCK1 + kRec,
-                  oOFF = oCV1 + kRec, oTK0 = oOFF + kRec, oTV0 = oTK0 + kKeys,
-                  oTK1 = oTV0 + kKeys, oTV1 = oTK1 + kKeys, oKM = oTV1 + kKeys,
-                  oHIST = oKM + 2 * kRec,
-                  oPART = oHIST + kHist, oCNT = oPART + kPartials, oSTAT = oCNT + 4,
+                  oTK0 = oCV1 + kRec, oTV0 = oTK0 + kKeys, oTK1 = oTV0 + kKeys, oTV1 = oTK1 + kKeys,
+                  oKM = oTV1 + kKeys, oOFF = oKM + 2 * kRec, oHIST = round4(oOFF + kBlockOffs),
+                  oPART = round4(oHIST + kHist), oCNT = round4(oPART + kPartials), oSTAT = oCNT + 4,
                   kWords = oSTAT + 4;
 
 // The scratch of every tgs_bin_noalloc call on a device (about 13.4 MB, held until exit).
@@ -48,7 +49,8 @@ tgs_status scratch_ptr(uint32_t **out) {
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_dev_ptr[dev]) {
         if ((size_t)radix_hist_needed(kItems) > (size_t)kHist ||
-            scan_partials_needed(kHist > kItems ? kHist : kItems) > (size_t)kPartials)
+            scan_partials_needed(kHist > kItems ? kHist : kItems) > (size_t)kPartials ||
+            scan_partials_needed(kRec) > (size_t)kBlockOffs)
             return TGS_ERR_NOT_SUPPORTED;
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -113,11 +115,12 @@ extern "C" tgs_status tgs_bin_noalloc(const float *splats, const int32_t *radii,
 
     derive_touched(reinterpret_cast<const float4 *>(splats), radii, nt, tile, w + oTT, w + oDB, st);
     scan_flags(w + oTT, nt, w + oPOS, cnt + 0, w + oPART, st);
-    compact_visible(w + oTT, w + oDB, w + oPOS, nt, reinterpret_cast<const float4 *>(splats), tile,
-                    w + oCK0, w + oCV0, reinterpret_cast<uint2 *>(w + oKM), st);
+    compact_visible(w + oTT, w + oDB, w + oPOS, nt, w + oCK0, w + oCV0, st);
     uint32_t *k = w + oCK0, *v = w + oCV0;
     radix_sort_pairs(k, v, w + oCK1, w + oCV1, cnt + 0, nt, 0, 32, w + oHIST, w + oPART, st);
-    gather_tiles_scan(v, w + oTT, cnt + 0, nt, w + oOFF, cnt + 1, w + oPART, nullptr, st);
+    // the per-record arrays free after the compaction hold the key counts of the depth order
+    const KeyInfo ki{w + oPOS, reinterpret_cast<uint2 *>(w + oKM), w + oDB, w + oTT};
+    count_keys(v, cnt + 0, nt, reinterpret_cast<const float4 *>(splats), tile, ki, w + oOFF, cnt + 1, st);
 
     uint32_t hK = 0;
     if (cudaMemcpyAsync(&hK, cnt + 1, sizeof hK, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -131,8 +134,8 @@ extern "C" tgs_status tgs_bin_noalloc(const float *splats, const int32_t *radii,
     if (K > capacity) return TGS_ERR_CAPACITY;
 
     const int64_t cap = K > 0 ? K : 1;
-    emit_keys(v, w + oOFF, cnt + 0, nt, reinterpret_cast<const float4 *>(splats), n, cb,
-              reinterpret_cast<const uint2 *>(w + oKM), w + oTK0, w + oTV0, cnt + 1, cap, status, st);
+    emit_keys(v, w + oOFF, cnt + 0, nt, ki, reinterpret_cast<const float4 *>(splats), n, cb, w + oTK0, w + oTV0,
+              cnt + 1, cap, status, st);
     uint32_t *tk = w + oTK0, *tv = w + oTV0;
     radix_sort_pairs(tk, tv, w + oTK1, w + oTV1, cnt + 1, cap, 0, bits_for_tiles(cb.total_tiles),
                      w + oHIST, w + oPART, st);

@@ -37,10 +37,6 @@ struct LoadVisible {
     const uint32_t *tt;
     __device__ __forceinline__ uint32_t operator()(int64_t i) const { return tt[i] > 0u ? 1u : 0u; }
 };
-struct LoadGathered {
-    const uint32_t *ids, *tt;
-    __device__ __forceinline__ uint32_t operator()(int64_t i) const { return tt[ids[i]]; }
-};
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
 #pragma unroll
@@ -140,31 +136,139 @@ void scan_generic(Load ld, const uint32_t *n_dev, int64_t n_cap, uint32_t *out, 
     }
 }
 
-// Compacts the visible records for the depth sort and replaces each visibility flag by the
-// record's number of keys: the tiles of its rect that pass the cull test.
-// For rects of at most 64 tiles it also stores which tiles (row-major within the rect) passed,
-// so that the emission does not repeat the test.
-__global__ void k_compact(uint32_t *__restrict__ tt, const uint32_t *__restrict__ db,
-                          const uint32_t *__restrict__ pos, int64_t n, const float4 *__restrict__ splats,
-                          int B, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
-                          uint2 *__restrict__ kmask) {
+// Compacts the visible records (depth bits as key, record index as value) for the depth sort.
+__global__ void k_compact(const uint32_t *__restrict__ tt, const uint32_t *__restrict__ db,
+                          const uint32_t *__restrict__ pos, int64_t n, uint32_t *__restrict__ keys,
+                          uint32_t *__restrict__ vals) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || tt[i] == 0u) return;
     const uint32_t p = pos[i];
     keys[p] = db[i];
     vals[p] = (uint32_t)i;
-    const float4 *rp = splats + (size_t)kSplatWords / 4 * i;
-    const uint32_t rx = __float_as_uint(rp[2].y);
-    const int x0 = (int)(rx & 0xFFFFu) / B, nx = (int)(rx >> 16) / B - x0 + 1;
-    uint64_t m = 0;
-    tt[i] = (uint32_t)for_kept_tiles(rp[0], rp[1], rp[2], rp[3], B, [&](int tx, int ty) {
-        const int b = (ty - ((int)(__float_as_uint(rp[2].z) & 0xFFFFu) / B)) * nx + (tx - x0);
-        if (b < 64) m |= (uint64_t)1 << b;
-    });
-    if (kmask) kmask[i] = make_uint2((uint32_t)m, (uint32_t)(m >> 32));
+}
+
+// a = q d + r for a < 2^22, d < 2^22, with one float multiply by rcp = 1/d (rounded): the
+// product is then within 1/d of a/d from below, so the truncated quotient is q or q - 1
+__device__ __forceinline__ void divmod_small(uint32_t a, uint32_t d, float rcp, uint32_t &q, uint32_t &r) {
+    if ((a | d) < (1u << 22)) {
+        q = __float2uint_rz(__uint2float_rn(a) * rcp);
+        r = a - q * d;
+        if (r >= d) {
+            q++;
+            r -= d;
+        }
+    } else {
+        q = a / d;
+        r = a - q * d;
+    }
+}
+
+// Key counts of the depth-sorted records. For each record of the depth order: the tiles of its
+// rect that pass the cull test (their number; for rects of at most 64 tiles also which ones,
+// row-major within the rect) and the packed pixel rect, all stored in depth order for the
+// emission; and per block of kScanTile records the number of keys (the scan's partials).
+//
+// Work balance: warp w of a block takes 256 records, 32 at a time, and spreads the (record,
+// rect tile) pairs of the 32 over its lanes, so that one large rect does not keep the other 31
+// lanes idle. A lane finds the record of pair p by binary search over the exclusive prefix
+// sums of the rect sizes (held one per lane and read with shuffles).
+__global__ void __launch_bounds__(kScanThreads)
+k_count_keys(const uint32_t *__restrict__ sorted_ids, const uint32_t *n_dev, int64_t n_cap,
+             const float4 *__restrict__ splats, int B, KeyInfo ki, uint32_t *__restrict__ partials) {
+    constexpr int NW = kScanThreads / 32;
+    __shared__ float4 s_g[NW][32];     // mean2d x, y; conic a, b
+    __shared__ float4 s_h[NW][32];     // conic c; tau; b / c; b / a
+    __shared__ int4 s_r[NW][32];       // pixel rect x0, x1, y0, y1 (inclusive)
+    __shared__ uint32_t s_m[NW][32][2];  // kept-tile bits of rects of at most 64 tiles
+    __shared__ uint32_t s_c[NW][32];     // kept-tile counts
+    __shared__ uint32_t s_warp[33];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t n = count_of(n_dev, n_cap);
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    if (base >= n) {  // uniform across the block
+        if (threadIdx.x == 0) partials[blockIdx.x] = 0u;
+        return;
+    }
+    uint32_t wsum = 0u;
+#pragma unroll 1
+    for (int q = 0; q < kScanItems; q++) {
+        const int64_t j = base + (int64_t)(w * kScanItems + q) * 32 + lane;
+        const bool valid = j < n;
+        uint32_t ntiles = 0u, rx = 0u, ry = 0u;
+        int tx0 = 0, ty0 = 0, nx = 1;
+        if (valid) {
+            const float4 *rp = splats + (size_t)kSplatWords / 4 * sorted_ids[j];
+            const float4 s0 = rp[0], s1 = rp[1], s2 = rp[2], s3 = rp[3];
+            rx = __float_as_uint(s2.y);
+            ry = __float_as_uint(s2.z);
+            const int ix0 = (int)(rx & 0xFFFFu), ix1 = (int)(rx >> 16);
+            const int iy0 = (int)(ry & 0xFFFFu), iy1 = (int)(ry >> 16);
+            tx0 = ix0 / B;
+            ty0 = iy0 / B;
+            nx = ix1 / B - tx0 + 1;
+            const int ny = iy1 / B - ty0 + 1;
+            ntiles = (nx > 0 && ny > 0) ? (uint32_t)nx * (uint32_t)ny : 0u;
+            s_g[w][lane] = s0;
+            s_h[w][lane] = make_float4(s1.x, s3.x, s3.y, s3.z);
+            s_r[w][lane] = make_int4(ix0, ix1, iy0, iy1);
+        }
+        if (nx < 1) nx = 1;
+        const float rcp = __frcp_rn((float)nx);
+        s_m[w][lane][0] = 0u;
+        s_m[w][lane][1] = 0u;
+        s_c[w][lane] = 0u;
+        const uint32_t inc = warp_incl_scan(ntiles, lane);
+        const uint32_t excl = inc - ntiles;
+        const uint32_t total = __shfl_sync(full, inc, 31);
+        __syncwarp();
+        for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+            const uint32_t p = p0 + (uint32_t)lane;
+            // owner: the last lane whose exclusive prefix is <= p (it has ntiles > 0)
+            int r = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1)
+                if (__shfl_sync(full, excl, r + step) <= p) r += step;
+            const uint32_t er = __shfl_sync(full, excl, r);
+            const uint32_t nxr = (uint32_t)__shfl_sync(full, nx, r);
+            const float rcpr = __shfl_sync(full, rcp, r);
+            const int txr = __shfl_sync(full, tx0, r), tyr = __shfl_sync(full, ty0, r);
+            const uint32_t ntr = __shfl_sync(full, ntiles, r);
+            if (p < total) {
+                const uint32_t local = p - er;
+                uint32_t row, col;
+                divmod_small(local, nxr, rcpr, row, col);
+                const int tx = txr + (int)col, ty = tyr + (int)row;
+                const float4 g = s_g[w][r], h = s_h[w][r];
+                const int4 rc = s_r[w][r];
+                if (tile_keep(g.x, g.y, g.z, g.w, h.x, h.y, h.z, h.w, max(tx * B, rc.x),
+                              min(tx * B + B - 1, rc.y), max(ty * B, rc.z), min(ty * B + B - 1, rc.w))) {
+                    atomicAdd(&s_c[w][r], 1u);
+                    if (ntr <= 64u) atomicOr(&s_m[w][r][local >> 5], 1u << (local & 31u));
+                }
+            }
+        }
+        __syncwarp();
+        if (valid) {
+            const uint32_t c = s_c[w][lane];
+            ki.cnt[j] = c;
+            ki.km[j] = make_uint2(s_m[w][lane][0], s_m[w][lane][1]);
+            ki.rx[j] = rx;
+            ki.ry[j] = ry;
+            wsum += c;
+        }
+        __syncwarp();
+    }
+    uint32_t tot;
+    block_excl_scan(wsum, s_warp, &tot);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
 // ---- radix sort -------------------------------------------------------------------------
+//
+// LSD passes of 8 bits over blocks of kRadixTile items: a histogram pass (per block and
+// digit), an exclusive scan of the histograms in digit-major order (the global start of each
+// block's run of each digit), and a stable scatter.
 
 __global__ void __launch_bounds__(kRadixThreads)
 k_radix_hist(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int64_t n_cap, int shift,
@@ -174,93 +278,104 @@ k_radix_hist(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int64_t n
     __syncthreads();
     const int64_t n = count_of(n_dev, n_cap);
     const int64_t base = (int64_t)blockIdx.x * kRadixTile;
-#pragma unroll 4
-    for (int r = 0; r < kRadixRounds; r++) {
-        const int64_t i = base + (int64_t)r * kRadixThreads + threadIdx.x;
-        if (i < n) atomicAdd(&s_h[(keys[i] >> shift) & mask], 1u);
+    if (base + kRadixTile <= n && (reinterpret_cast<uintptr_t>(keys) & 15u) == 0u) {
+        // full block of a 16-byte aligned array: 16-byte loads (kRadixTile % 4 == 0)
+        const uint4 *k4 = reinterpret_cast<const uint4 *>(keys + base);
+#pragma unroll
+        for (int r = 0; r < kRadixRounds / 4; r++) {
+            const uint4 q = k4[r * kRadixThreads + threadIdx.x];
+            atomicAdd(&s_h[(q.x >> shift) & mask], 1u);
+            atomicAdd(&s_h[(q.y >> shift) & mask], 1u);
+            atomicAdd(&s_h[(q.z >> shift) & mask], 1u);
+            atomicAdd(&s_h[(q.w >> shift) & mask], 1u);
+        }
+    } else {
+        for (int r = 0; r < kRadixRounds; r++) {
+            const int64_t i = base + (int64_t)r * kRadixThreads + threadIdx.x;
+            if (i < n) atomicAdd(&s_h[(keys[i] >> shift) & mask], 1u);
+        }
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_h[threadIdx.x];
 }
 
-// Stable scatter of one block of 2048 items. The block's items are first ranked into shared
-// memory in (digit, index) order -- rank = start of the digit in the block + equal digits in
-// earlier rounds + earlier warps of this round + earlier lanes -- and then written out in
-// that order, so that each digit's run of this block goes to consecutive global addresses.
+// Stable scatter of one block of kRadixTile items. Warp w owns the items
+// [w * 32 * R, (w + 1) * 32 * R) of the block and ranks them on its own, R rounds of 32 lanes,
+// with per-warp digit counters (a warp multisplit: one ballot per digit bit finds the lanes
+// holding the same digit). Then one pass over the digits turns the per-warp counts into each
+// warp's start within each digit, the items are placed in shared memory in (digit, index)
+// order, and written out so that each digit's run of the block goes to consecutive addresses.
 __global__ void __launch_bounds__(kRadixThreads)
 k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 const uint32_t *n_dev, int64_t n_cap, int shift, uint32_t mask,
                 const uint32_t *__restrict__ offsets, int64_t nblocks,
                 uint32_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out) {
-    constexpr int NW = kRadixThreads / 32;
-    __shared__ uint32_t s_cnt[NW][kRadixBins];
-    __shared__ uint32_t s_run[kRadixBins];     // items of each digit placed so far
-    __shared__ uint32_t s_start[kRadixBins];   // start of each digit in the block's order
-    __shared__ uint32_t s_goff[kRadixBins];    // global position of the block's digit run
+    constexpr int NW = kRadixThreads / 32, R = kRadixRounds;
+    __shared__ uint32_t s_cnt[NW][kRadixBins];  // per-warp digit counts, then per-warp starts
+    __shared__ uint32_t s_start[kRadixBins];    // start of each digit in the block's order
+    __shared__ uint32_t s_goff[kRadixBins];     // global position of the block's digit run
     __shared__ uint32_t s_warp[33];
     __shared__ uint32_t s_k[kRadixTile], s_v[kRadixTile];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const unsigned full = 0xffffffffu;
     const int64_t n = count_of(n_dev, n_cap);
     const int64_t base = (int64_t)blockIdx.x * kRadixTile;
     if (base >= n) return;  // uniform across the block
     const int cnt = (int)((n - base) < kRadixTile ? (n - base) : kRadixTile);
-    uint32_t kr[kRadixRounds], vr[kRadixRounds];
-    s_run[t] = 0u;
 #pragma unroll
     for (int q = 0; q < NW; q++) s_cnt[q][t] = 0u;
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < kRadixRounds; r++) {
-        const int j = r * kRadixThreads + t;
-        const bool valid = j < cnt;
-        kr[r] = valid ? keys_in[base + j] : 0xffffffffu;
-        vr[r] = valid ? vals_in[base + j] : 0u;
-        if (valid) atomicAdd(&s_run[(kr[r] >> shift) & mask], 1u);
-    }
-    __syncthreads();
-    uint32_t tot;
-    const uint32_t start = block_excl_scan(s_run[t], s_warp, &tot);
-    s_start[t] = start;
     s_goff[t] = offsets[(int64_t)t * nblocks + blockIdx.x];
-    s_run[t] = 0u;
     __syncthreads();
+    uint32_t kr[R], vr[R], rk[R];
     const uint32_t lt_mask = (1u << lane) - 1u;
+    const int wbase = w * 32 * R;
 #pragma unroll
-    for (int r = 0; r < kRadixRounds; r++) {
-        if (r * kRadixThreads >= cnt) continue;  // uniform: the block's tail rounds are empty
-        const bool valid = r * kRadixThreads + t < cnt;
-        const uint32_t d = valid ? ((kr[r] >> shift) & mask) : mask;
-        // lanes holding the same digit: one ballot per digit bit (warp multisplit)
-        uint32_t peers = 0xffffffffu;
+    for (int r = 0; r < R; r++) {
+        const int j = wbase + r * 32 + lane;
+        const bool valid = j < cnt;
+        kr[r] = valid ? keys_in[base + j] : 0u;
+        vr[r] = valid ? vals_in[base + j] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int j = wbase + r * 32 + lane;
+        const bool valid = j < cnt;
+        const uint32_t d = (kr[r] >> shift) & mask;
+        uint32_t peers = __ballot_sync(full, valid);
 #pragma unroll
         for (int b = 0; b < 8; b++) {
-            const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            const uint32_t bal = __ballot_sync(full, (d >> b) & 1u);
             peers &= ((d >> b) & 1u) ? bal : ~bal;
         }
-        const uint32_t wr = __popc(peers & lt_mask);
-        if (wr == 0u) s_cnt[w][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t acc = s_run[t];
+        const uint32_t before = s_cnt[w][d];
+        rk[r] = before + __popc(peers & lt_mask);
+        __syncwarp();
+        if (valid && (peers & lt_mask) == 0u) s_cnt[w][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread t = digit t: per-warp starts within the digit, and the digit's start in the block
+    uint32_t acc = 0u;
 #pragma unroll
-            for (int q = 0; q < NW; q++) {
-                const uint32_t c = s_cnt[q][t];
-                s_cnt[q][t] = acc;
-                acc += c;
-            }
-            s_run[t] = acc;
-        }
-        __syncthreads();
-        if (valid) {
-            const uint32_t lp = s_start[d] + s_cnt[w][d] + wr;
+    for (int q = 0; q < NW; q++) {
+        const uint32_t c = s_cnt[q][t];
+        s_cnt[q][t] = acc;
+        acc += c;
+    }
+    uint32_t tot;
+    s_start[t] = block_excl_scan(acc, s_warp, &tot);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int j = wbase + r * 32 + lane;
+        if (j < cnt) {
+            const uint32_t d = (kr[r] >> shift) & mask;
+            const uint32_t lp = s_start[d] + s_cnt[w][d] + rk[r];
             s_k[lp] = kr[r];
             s_v[lp] = vr[r];
         }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < NW; q++) s_cnt[q][t] = 0u;
-        __syncthreads();
     }
+    __syncthreads();
     for (int i = t; i < cnt; i += kRadixThreads) {
         const uint32_t k = s_k[i];
         const uint32_t d = (k >> shift) & mask;
@@ -272,87 +387,181 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
 
 // ---- keys, ranges -------------------------------------------------------------------------
 
-// Key emission. A warp takes 32 consecutive records of the depth order; their keys form one
-// contiguous segment of the key array, which the warp assembles in shared memory and writes
-// out with coalesced stores (segments longer than the buffer are written directly).
-constexpr int kEmitThreads = 256;
-constexpr int kEmitBuf = 512;  // keys staged per warp
-
-__global__ void __launch_bounds__(kEmitThreads)
-k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ offsets,
-       const uint32_t *n_dev, int64_t n_cap, const float4 *__restrict__ splats, uint32_t n_gauss,
-       const __grid_constant__ CamBatch cb, const uint2 *__restrict__ kmask,
-       uint32_t *__restrict__ tile_keys, uint32_t *__restrict__ tile_vals, const uint32_t *K_dev,
-       int64_t key_cap, uint32_t *status) {
-    __shared__ uint32_t s_k[kEmitThreads / 32][kEmitBuf], s_v[kEmitThreads / 32][kEmitBuf];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int64_t K = (int64_t)*K_dev;
-    if (i == 0 && K > key_cap) atomicOr(status, kStatusCapacity);
-    const int64_t n = count_of(n_dev, n_cap);
-    if (i - lane >= n) return;  // the whole warp is past the end
-    const bool valid = i < n;
-    const uint32_t off = valid ? offsets[i] : 0u;
-    const uint32_t end = valid ? (i + 1 < n ? offsets[i + 1] : (uint32_t)K) : 0u;
-    const uint32_t seg0 = __shfl_sync(0xffffffffu, off, 0);
-    const uint32_t seg_end = __reduce_max_sync(0xffffffffu, end);
-    const uint32_t seg_len = seg_end - seg0;
-    const bool staged = seg_len <= (uint32_t)kEmitBuf;
-    if (valid && end > off) {
-        const uint32_t rec = sorted_ids[i];
-        const int v = (int)(rec / n_gauss);
-        const DevCam &c = cb.c[v];
-        const float4 *rp = splats + (size_t)kSplatWords / 4 * rec;
-        const int B = cb.tile;
-        const uint32_t rx = __float_as_uint(rp[2].y), ry = __float_as_uint(rp[2].z);
-        const int x0 = (int)(rx & 0xFFFFu) / B, x1 = (int)(rx >> 16) / B;
-        const int y0 = (int)(ry & 0xFFFFu) / B, y1 = (int)(ry >> 16) / B;
-        const int nx = x1 - x0 + 1;
-        int64_t k = off;
-        auto put = [&](int tx, int ty) {
-            const bool ok = tx < c.gx && ty < c.gy;   // records from outside may carry any rect
-            const uint32_t key = ok ? (uint32_t)(c.tile_offset + ty * c.gx + tx) : 0xffffffffu;
-            if (staged) {
-                s_k[w][k - seg0] = key;
-                s_v[w][k - seg0] = rec;
-            } else if (k < key_cap) {
-                tile_keys[k] = key;
-                tile_vals[k] = rec;
-            }
-            k++;
-        };
-        if (nx * (y1 - y0 + 1) <= 64) {
-            const uint2 mm = kmask[rec];
-            uint64_t m = ((uint64_t)mm.y << 32) | mm.x;
-            while (m) {
-                const int b = __ffsll((long long)m) - 1;
-                m &= m - 1;
-                put(x0 + b % nx, y0 + b / nx);
-            }
-        } else {
-            for_kept_tiles(rp[0], rp[1], rp[2], rp[3], B, put);
-        }
+// Position of the k-th set bit (k from 0) of the 64-bit mask hi:lo; k < popc(mask).
+__device__ __forceinline__ int select_bit(uint32_t lo, uint32_t hi, uint32_t k) {
+    const uint32_t pl = __popc(lo);
+    uint32_t x = lo;
+    int b = 0;
+    if (k >= pl) {
+        x = hi;
+        k -= pl;
+        b = 32;
     }
-    __syncwarp();
-    if (staged)
-        for (uint32_t j = lane; j < seg_len; j += 32) {
-            const int64_t gp = (int64_t)seg0 + j;
-            if (gp < key_cap) {
-                tile_keys[gp] = s_k[w][j];
-                tile_vals[gp] = s_v[w][j];
-            }
-        }
+    uint32_t c = __popc(x & 0xFFFFu);
+    if (k >= c) { k -= c; x >>= 16; b += 16; }
+    c = __popc(x & 0xFFu);
+    if (k >= c) { k -= c; x >>= 8; b += 8; }
+    c = __popc(x & 0xFu);
+    if (k >= c) { k -= c; x >>= 4; b += 4; }
+    c = __popc(x & 0x3u);
+    if (k >= c) { k -= c; x >>= 2; b += 2; }
+    if (k >= (x & 1u)) b += 1;
+    return b;
 }
 
+// Key emission. Block b takes the same kScanTile depth-sorted records as block b of the key
+// count, whose keys start at block_off[b]; warp w takes 256 of them, 32 at a time. The keys of
+// 32 records form one contiguous segment, which the warp's lanes fill position by position
+// (coalesced stores, balanced work): the lane of position p finds its record by binary search
+// over the prefix sums, and its tile as the k-th set bit of the record's kept-tile mask.
+// Records of more than 64 rect tiles (no mask) are done by the whole warp, 32 tiles at a time.
+__global__ void __launch_bounds__(kScanThreads)
+k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ block_off,
+       const uint32_t *n_dev, int64_t n_cap, const KeyInfo ki, const float4 *__restrict__ splats,
+       uint32_t n_gauss, const __grid_constant__ CamBatch cb, uint32_t *__restrict__ tile_keys,
+       uint32_t *__restrict__ tile_vals, const uint32_t *K_dev, int64_t key_cap, uint32_t *status) {
+    constexpr int NW = kScanThreads / 32;
+    __shared__ uint32_t s_wtot[NW];
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (int64_t)*K_dev > key_cap) atomicOr(status, kStatusCapacity);
+    const int64_t n = count_of(n_dev, n_cap);
+    const int64_t base = (int64_t)blockIdx.x * kScanTile;
+    if (base >= n) return;  // uniform across the block
+    const int64_t wbase = base + (int64_t)w * 32 * kScanItems;
+    uint32_t wsum = 0u;
+#pragma unroll
+    for (int q = 0; q < kScanItems; q++) {
+        const int64_t j = wbase + q * 32 + lane;
+        wsum += j < n ? ki.cnt[j] : 0u;
+    }
+    wsum = __reduce_add_sync(full, wsum);
+    if (lane == 0) s_wtot[w] = wsum;
+    __syncthreads();
+    int64_t off = (int64_t)block_off[blockIdx.x];
+    for (int q = 0; q < w; q++) off += s_wtot[q];
+    const int B = cb.tile;
+#pragma unroll 1
+    for (int q = 0; q < kScanItems; q++) {
+        const int64_t j = wbase + q * 32 + lane;
+        const bool valid = j < n;
+        const uint32_t cnt = valid ? ki.cnt[j] : 0u;
+        const uint32_t inc = warp_incl_scan(cnt, lane);
+        const uint32_t excl = inc - cnt;
+        const uint32_t total = __shfl_sync(full, inc, 31);
+        if (total == 0u) continue;  // uniform
+        // the lane's record: view, tile rect and mask
+        uint32_t rec = 0u;
+        int tx0 = 0, ty0 = 0, nx = 1, gx = 0, gy = 0, toff = 0;
+        uint2 m = make_uint2(0u, 0u);
+        bool big = false;
+        if (cnt > 0u) {
+            rec = sorted_ids[j];
+            const DevCam &c = cb.c[rec / n_gauss];
+            gx = c.gx;
+            gy = c.gy;
+            toff = c.tile_offset;
+            const uint32_t rx = ki.rx[j], ry = ki.ry[j];
+            tx0 = (int)(rx & 0xFFFFu) / B;
+            ty0 = (int)(ry & 0xFFFFu) / B;
+            nx = (int)(rx >> 16) / B - tx0 + 1;
+            const int ny = (int)(ry >> 16) / B - ty0 + 1;
+            big = (int64_t)nx * ny > 64;
+            if (!big) m = ki.km[j];
+        }
+        const float rcp = __frcp_rn((float)nx);
+        // records of more than 64 rect tiles: the cull test again, on 32 rect tiles at a time
+        uint32_t bigs = __ballot_sync(full, big);
+        while (bigs) {
+            const int o = __ffs(bigs) - 1;
+            bigs &= bigs - 1u;
+            const uint32_t r = __shfl_sync(full, rec, o);
+            const int txo = __shfl_sync(full, tx0, o), tyo = __shfl_sync(full, ty0, o), nxo = __shfl_sync(full, nx, o);
+            const int gxo = __shfl_sync(full, gx, o), gyo = __shfl_sync(full, gy, o), toffo = __shfl_sync(full, toff, o);
+            const int64_t k0 = off + __shfl_sync(full, excl, o);
+            const float4 *rp = splats + (size_t)kSplatWords / 4 * r;
+            const float4 s0 = rp[0], s1 = rp[1], s2 = rp[2], s3 = rp[3];
+            const uint32_t rx = __float_as_uint(s2.y), ry = __float_as_uint(s2.z);
+            const int ix0 = (int)(rx & 0xFFFFu), ix1 = (int)(rx >> 16);
+            const int iy0 = (int)(ry & 0xFFFFu), iy1 = (int)(ry >> 16);
+            const int64_t nt = (int64_t)nxo * (iy1 / B - tyo + 1);
+            int64_t kept = 0;
+            for (int64_t t0 = 0; t0 < nt; t0 += 32) {
+                const int64_t tl = t0 + lane;
+                bool keep = false;
+                int tx = 0, ty = 0;
+                if (tl < nt) {
+                    tx = txo + (int)(tl % nxo);
+                    ty = tyo + (int)(tl / nxo);
+                    keep = tile_keep(s0.x, s0.y, s0.z, s0.w, s1.x, s3.x, s3.y, s3.z, max(tx * B, ix0),
+                                     min(tx * B + B - 1, ix1), max(ty * B, iy0), min(ty * B + B - 1, iy1));
+                }
+                const uint32_t kb = __ballot_sync(full, keep);
+                const int64_t k = k0 + kept + __popc(kb & ((1u << lane) - 1u));
+                if (keep && k < key_cap) {
+                    const bool ok = tx < gxo && ty < gyo;   // records from outside may carry any rect
+                    tile_keys[k] = ok ? (uint32_t)(toffo + ty * gxo + tx) : 0xffffffffu;
+                    tile_vals[k] = r;
+                }
+                kept += __popc(kb);
+            }
+        }
+        for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+            const uint32_t p = p0 + (uint32_t)lane;
+            int o = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1)
+                if (__shfl_sync(full, excl, o + step) <= p) o += step;
+            const uint32_t eo = __shfl_sync(full, excl, o);
+            const uint32_t mlo = __shfl_sync(full, m.x, o), mhi = __shfl_sync(full, m.y, o);
+            const uint32_t nxo = (uint32_t)__shfl_sync(full, nx, o);
+            const float rcpo = __shfl_sync(full, rcp, o);
+            const int txo = __shfl_sync(full, tx0, o), tyo = __shfl_sync(full, ty0, o);
+            const int gxo = __shfl_sync(full, gx, o), gyo = __shfl_sync(full, gy, o);
+            const int toffo = __shfl_sync(full, toff, o);
+            const uint32_t reco = __shfl_sync(full, rec, o);
+            const bool bigo = __shfl_sync(full, big ? 1 : 0, o) != 0;
+            const int64_t gp = off + p;
+            if (p < total && !bigo && gp < key_cap) {
+                uint32_t row, col;
+                divmod_small((uint32_t)select_bit(mlo, mhi, p - eo), nxo, rcpo, row, col);
+                const int tx = txo + (int)col, ty = tyo + (int)row;
+                const bool ok = tx < gxo && ty < gyo;
+                tile_keys[gp] = ok ? (uint32_t)(toffo + ty * gxo + tx) : 0xffffffffu;
+                tile_vals[gp] = reco;
+            }
+        }
+        off += total;
+    }
+}
+// Ranges of the sorted tile keys: ranges[t] = [first, last + 1) of tile t (untouched tiles
+// keep the zeros set before). Each thread looks at 4 consecutive keys and their neighbours.
 __global__ void k_ranges(const uint32_t *__restrict__ keys, const uint32_t *K_dev, int64_t cap,
                          uint2 *__restrict__ ranges, uint32_t total_tiles) {
     const int64_t K = count_of(K_dev, cap);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= K) return;
-    const uint32_t t = keys[i];
-    if (t >= total_tiles) return;
-    if (i == 0 || keys[i - 1] != t) ranges[t].x = (uint32_t)i;
-    if (i == K - 1 || keys[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    if (i0 >= K) return;
+    uint32_t k[6];
+    k[0] = i0 > 0 ? keys[i0 - 1] : 0xffffffffu;
+    if (i0 + 4 <= K && (reinterpret_cast<uintptr_t>(keys) & 15u) == 0u) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(keys + i0);  // aligned: i0 % 4 == 0
+        k[1] = q.x;
+        k[2] = q.y;
+        k[3] = q.z;
+        k[4] = q.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++) k[1 + j] = i0 + j < K ? keys[i0 + j] : 0xffffffffu;
+    }
+    k[5] = i0 + 4 < K ? keys[i0 + 4] : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int64_t i = i0 + j;
+        const uint32_t t = k[1 + j];
+        if (i >= K || t >= total_tiles) continue;
+        if (i == 0 || k[j] != t) ranges[t].x = (uint32_t)i;
+        if (i == K - 1 || k[2 + j] != t) ranges[t].y = (uint32_t)(i + 1);
+    }
 }
 
 __global__ void k_full_keys(const uint32_t *__restrict__ tk, const uint32_t *__restrict__ tv,
@@ -395,13 +604,11 @@ void scan_flags(const uint32_t *tiles_touched, int64_t n_cap, uint32_t *out, uin
     scan_generic(LoadVisible{tiles_touched}, nullptr, n_cap, out, total, partials, st);
 }
 
-void compact_visible(uint32_t *tiles_touched, const uint32_t *depth_bits, const uint32_t *pos,
-                     int64_t n_cap, const float4 *splats, int tile, uint32_t *keys, uint32_t *vals,
-                     uint2 *kmask, cudaStream_t st) {
+void compact_visible(const uint32_t *tiles_touched, const uint32_t *depth_bits, const uint32_t *pos,
+                     int64_t n_cap, uint32_t *keys, uint32_t *vals, cudaStream_t st) {
     if (n_cap <= 0) return;
     count_launch();
-    k_compact<<<blocks_for(n_cap, 256), 256, 0, st>>>(tiles_touched, depth_bits, pos, n_cap, splats, tile,
-                                                      keys, vals, kmask);
+    k_compact<<<blocks_for(n_cap, 256), 256, 0, st>>>(tiles_touched, depth_bits, pos, n_cap, keys, vals);
 }
 
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint32_t *vals_alt,
@@ -426,22 +633,28 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint
     }
 }
 
-void gather_tiles_scan(const uint32_t *sorted_ids, const uint32_t *tiles_touched, const uint32_t *n_dev,
-                       int64_t n_cap, uint32_t *offsets, uint32_t *total, uint32_t *partials,
-                       uint32_t *tmp, cudaStream_t st) {
-    (void)tmp;
-    scan_generic(LoadGathered{sorted_ids, tiles_touched}, n_dev, n_cap, offsets, total, partials, st);
+void count_keys(const uint32_t *sorted_ids, const uint32_t *n_dev, int64_t n_cap, const float4 *splats,
+                int tile, const KeyInfo &ki, uint32_t *block_offsets, uint32_t *total, cudaStream_t st) {
+    const int64_t nb = (n_cap + kScanTile - 1) / kScanTile;
+    if (nb == 0) {
+        if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
+        return;
+    }
+    count_launch();
+    k_count_keys<<<(unsigned)nb, kScanThreads, 0, st>>>(sorted_ids, n_dev, n_cap, splats, tile, ki, block_offsets);
+    count_launch();
+    k_scan_partials<<<1, 1024, 0, st>>>(block_offsets, nb, total);
 }
 
-void emit_keys(const uint32_t *sorted_ids, const uint32_t *offsets, const uint32_t *n_dev, int64_t n_cap,
-               const float4 *splats, int64_t n_gauss, const CamBatch &cb, const uint2 *kmask,
+void emit_keys(const uint32_t *sorted_ids, const uint32_t *block_offsets, const uint32_t *n_dev, int64_t n_cap,
+               const KeyInfo &ki, const float4 *splats, int64_t n_gauss, const CamBatch &cb,
                uint32_t *tile_keys, uint32_t *tile_vals, const uint32_t *K_dev, int64_t key_capacity,
                uint32_t *status, cudaStream_t st) {
     if (n_cap <= 0) return;
     count_launch();
-    k_emit<<<blocks_for(n_cap, kEmitThreads), kEmitThreads, 0, st>>>(sorted_ids, offsets, n_dev, n_cap, splats,
-                                                                     (uint32_t)n_gauss, cb, kmask, tile_keys,
-                                                                     tile_vals, K_dev, key_capacity, status);
+    k_emit<<<blocks_for(n_cap, kScanTile), kScanThreads, 0, st>>>(sorted_ids, block_offsets, n_dev, n_cap, ki,
+                                                                  splats, (uint32_t)n_gauss, cb, tile_keys,
+                                                                  tile_vals, K_dev, key_capacity, status);
 }
 
 void find_ranges(const uint32_t *tile_keys, const uint32_t *K_dev, int64_t key_capacity, uint2 *ranges,
@@ -449,7 +662,7 @@ void find_ranges(const uint32_t *tile_keys, const uint32_t *K_dev, int64_t key_c
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)total_tiles, st);
     if (key_capacity <= 0) return;
     count_launch();
-    k_ranges<<<blocks_for(key_capacity, 256), 256, 0, st>>>(tile_keys, K_dev, key_capacity, ranges,
+    k_ranges<<<blocks_for((key_capacity + 3) / 4, 256), 256, 0, st>>>(tile_keys, K_dev, key_capacity, ranges,
                                                              (uint32_t)total_tiles);
 }
 

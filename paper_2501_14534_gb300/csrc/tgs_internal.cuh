@@ -176,20 +176,28 @@ size_t radix_hist_needed(int64_t n_items);
 // out[i] = exclusive prefix of in_fn(i) for i < *n_dev; *total = sum. n_cap bounds the grid.
 void scan_flags(const uint32_t *tiles_touched, int64_t n_cap, uint32_t *out, uint32_t *total,
                 uint32_t *partials, cudaStream_t st);
-// Also stores per visible record the kept-tile mask of rects of at most 64 tiles (kmask [nt]).
-void compact_visible(uint32_t *tiles_touched, const uint32_t *depth_bits, const uint32_t *pos,
-                     int64_t n_cap, const float4 *splats, int tile, uint32_t *keys, uint32_t *vals,
-                     uint2 *kmask, cudaStream_t st);
+// Visible records -> (depth bits, record index) pairs at pos[i], for the depth sort.
+void compact_visible(const uint32_t *tiles_touched, const uint32_t *depth_bits, const uint32_t *pos,
+                     int64_t n_cap, uint32_t *keys, uint32_t *vals, cudaStream_t st);
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       const uint32_t *n_dev, int64_t n_cap, int begin_bit, int end_bit,
                       uint32_t *hist, uint32_t *partials, cudaStream_t st);
-void gather_tiles_scan(const uint32_t *sorted_ids, const uint32_t *tiles_touched,
-                       const uint32_t *n_dev, int64_t n_cap, uint32_t *offsets, uint32_t *total,
-                       uint32_t *partials, uint32_t *tmp, cudaStream_t st);
-void emit_keys(const uint32_t *sorted_ids, const uint32_t *offsets, const uint32_t *n_dev,
-               int64_t n_cap, const float4 *splats, int64_t n_gauss, const CamBatch &cb,
-               const uint2 *kmask, uint32_t *tile_keys, uint32_t *tile_vals, const uint32_t *K_dev,
-               int64_t key_capacity, uint32_t *status, cudaStream_t st);
+// Per depth-sorted record (arrays of n_cap, in depth order): number of kept tiles, kept-tile
+// mask (rects of at most 64 tiles), packed pixel rect x and y.
+struct KeyInfo {
+    uint32_t *cnt;
+    uint2 *km;
+    uint32_t *rx, *ry;
+};
+// Culls the rect tiles of each depth-sorted record and counts its keys (KeyInfo); per block of
+// 2048 records the exclusive start of its keys (block_offsets, scan_partials_needed(n_cap)
+// words) and the total in *total.
+void count_keys(const uint32_t *sorted_ids, const uint32_t *n_dev, int64_t n_cap, const float4 *splats,
+                int tile, const KeyInfo &ki, uint32_t *block_offsets, uint32_t *total, cudaStream_t st);
+void emit_keys(const uint32_t *sorted_ids, const uint32_t *block_offsets, const uint32_t *n_dev,
+               int64_t n_cap, const KeyInfo &ki, const float4 *splats, int64_t n_gauss, const CamBatch &cb,
+               uint32_t *tile_keys, uint32_t *tile_vals, const uint32_t *K_dev, int64_t key_capacity,
+               uint32_t *status, cudaStream_t st);
 void find_ranges(const uint32_t *tile_keys, const uint32_t *K_dev, int64_t key_capacity,
                  uint2 *ranges, int total_tiles, cudaStream_t st);
 void derive_touched(const float4 *splats, const int32_t *radii, int64_t n_rec, int tile,
