@@ -543,7 +543,7 @@ tgs_status tgs_preprocess_backward(tgs_ctx *c, const tgs_gaussians *g, const tgs
     TGS_TRY(make_gauss(c->cfg, g, gp));
     GradPtrs o = grad_ptrs(grads, stats, (flags & TGS_ACCUMULATE) ? 1 : 0);
     launch_preprocess_backward(gp, cb, reinterpret_cast<const float4 *>(splat_grads), radii, o,
-                               (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, (cudaStream_t)stream);
+                               (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, 0, (cudaStream_t)stream);
     return last_error();
 }
 
@@ -620,7 +620,7 @@ tgs_status tgs_backward(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *ca
         const int acc = ((flags & TGS_ACCUMULATE) || v > 0) ? 1 : 0;
         GradPtrs o = grad_ptrs(grads, stats, acc);
         launch_preprocess_backward(gp, cb, as<float4>(c->sgrads), as<int32_t>(c->radii), o,
-                                   (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, st);
+                                   (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, 0, st);
         TGS_TRY(last_error());
     }
     return TGS_OK;
@@ -726,8 +726,9 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
     }
     mark(c, stage++, "preprocess_backward", st);
     GradPtrs o = grad_ptrs(grads, stats, (flags & TGS_ACCUMULATE) ? 1 : 0);
+    // the fused blend leaves pixel sums (moments) in the gradient records
     launch_preprocess_backward(gp, cb, as<float4>(c->sgrads), as<int32_t>(c->radii), o,
-                               (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, st);
+                               (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, (flags & TGS_UNFUSED) ? 0 : 1, st);
     mark(c, stage, "end", st);
     c->kernels_per_step = g_launches - launches0;
     return last_error();

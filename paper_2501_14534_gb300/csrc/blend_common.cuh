@@ -289,11 +289,16 @@ struct BwdInput {
 };
 
 // Reverse walk of one tile's list from each pixel's last contributor. The transmittance in
-// front of fragment i is recovered as T_i = T_{i+1} / (1 - a_i) from T_final; the colour behind
-// fragment i is accumulated from the back. Per fragment the gradients of the pixels of a warp
-// are summed (transposed reduction) and added with one atomic per value per warp into the
-// splat gradient record: dL/d mean2d (2), dL/d conic a, b, c, dL/d opacity, dL/d rgb (3).
-template <int TILE, int PPT>
+// front of fragment i is recovered as T_i = T_{i+1} / (1 - a_i) from T_final; of the colour
+// behind fragment i only its dot product with dL/dC is needed, and it is accumulated from the
+// back. Per fragment the gradients of the pixels of a warp are summed (transposed reduction)
+// and added with atomics into the splat gradient record: dL/d mean2d (2), dL/d conic a, b, c,
+// dL/d opacity, dL/d rgb (3). With MOMENTS the record receives instead the pixel sums that
+// these are linear in -- sum u dx, sum u dy, sum u dx^2, sum u dx dy, sum u dy^2 (u = dL/dG'
+// for the unclamped fragments, dx, dy = mean2d - pixel) -- then dL/d opacity = sum u and
+// dL/d rgb, and the consumer applies the splat's conic and opacity (see splat_grads in
+// preprocess.cu): that takes the per-fragment conversion out of the loop.
+template <int TILE, int PPT, bool MOMENTS = false>
 __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
                                               const float4 *__restrict__ splats,
                                               const uint32_t *__restrict__ ids, uint2 rg,
@@ -303,13 +308,13 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
     constexpr int NT = TILE * TILE / PPT;
     const unsigned full = 0xffffffffu;
     const int t = threadIdx.x, lane = t & 31;
-    // acc = colour of the fragments behind the current one, blended among themselves
-    float T[PPT], acR[PPT], acG[PPT], acB[PPT], tbg[PPT];
+    // acd = (colour of the fragments behind the current one, blended among themselves) . dL/dC
+    float T[PPT], acd[PPT], tbg[PPT];
     int mymax = 0;
 #pragma unroll
     for (int k = 0; k < PPT; k++) {
         T[k] = in.Tfin[k];
-        acR[k] = acG[k] = acB[k] = 0.f;
+        acd[k] = 0.f;
         tbg[k] = in.Tfin[k] * (bg0 * in.dR[k] + bg1 * in.dG[k] + bg2 * in.dB[k]);
         mymax = max(mymax, in.last[k]);
     }
@@ -367,11 +372,10 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
                 g[7] = fmaf(w, in.dG[k], g[7]);
                 g[8] = fmaf(w, in.dB[k], g[8]);
                 // dC/da = T (c - acc) - T_final / (1 - a) bg, acc = colour behind this fragment
-                float dLda = (b.z - acR[k]) * in.dR[k] + (b.w - acG[k]) * in.dG[k] + (cbl - acB[k]) * in.dB[k];
-                dLda = fmaf(dLda, T[k], -tbg[k] * inv);
-                acR[k] = fmaf(alpha, b.z - acR[k], acR[k]);   // now includes this fragment
-                acG[k] = fmaf(alpha, b.w - acG[k], acG[k]);
-                acB[k] = fmaf(alpha, cbl - acB[k], acB[k]);
+                const float cd = fmaf(cbl, in.dB[k], fmaf(b.w, in.dG[k], b.z * in.dR[k]));
+                const float diff = cd - acd[k];
+                const float dLda = fmaf(diff, T[k], -tbg[k] * inv);
+                acd[k] = fmaf(alpha, diff, acd[k]);   // now includes this fragment
                 if (x <= kAlphaMax) {
                     const float u = dLda * G;
                     const float ux = u * dx, uy = u * dy;
@@ -387,6 +391,12 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
             float *dst = sgrads + 12 * (size_t)sm.id[m];
             warp_transpose_reduce8(g, lane);
             const float gb = warp_sum(g[8]);
+            if (MOMENTS) {
+                // lane 4j holds the total of value j: one reduction of 8 lanes, one of 1
+                if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), g[0]);
+                if (lane == 0) atomicAdd(dst + 8, gb);
+                continue;
+            }
             // lane 4j holds the total of value j. dL/dpower = o' u; with the scaled conic
             // -a dx - b dy = ln2 (2A dx + B dy), -c dy - b dx = ln2 (2C dy + B dx)
             const int j = lane >> 2;

@@ -91,7 +91,7 @@ k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
         }
         lsum = warp_sum(lsum);
         if (lane == 0) s_loss[w] = lsum;
-        tile_backward<TILE, PPT>(sm, splats, ids, rg, P, in, bg0, bg1, bg2, sgrads);
+        tile_backward<TILE, PPT, true>(sm, splats, ids, rg, P, in, bg0, bg1, bg2, sgrads);
         // s_loss was written before the barriers inside tile_backward
         if (t == 0 && loss) {
             float x = 0.f;

@@ -315,6 +315,29 @@ __device__ __forceinline__ void out_write(float *p, int64_t idx, float v, int ac
 
 constexpr int kBwdThreads = 128;
 
+// Splat gradients of one (view, Gaussian) from its gradient record: either the gradients
+// themselves, or (moments != 0) the pixel sums of the blend backward that they are linear in,
+// to which the splat's conic (a, b, c) and opacity o' are applied here:
+// dL/d mean2d = -o' (Q m), Q = [[a, b], [b, c]], m = (sum u dx, sum u dy);
+// dL/d conic a, b, c = -o' (1/2 sum u dx^2, sum u dx dy, 1/2 sum u dy^2).
+__device__ __forceinline__ void splat_grads(const float4 &ga, const float4 &gb, int moments, float o,
+                                            float ca, float cb, float cc, float &gmx, float &gmy,
+                                            float &gca, float &gcb, float &gcc) {
+    if (moments) {
+        gmx = -o * (ca * ga.x + cb * ga.y);
+        gmy = -o * (cb * ga.x + cc * ga.y);
+        gca = -0.5f * o * ga.z;
+        gcb = -o * ga.w;
+        gcc = -0.5f * o * gb.x;
+    } else {
+        gmx = ga.x;
+        gmy = ga.y;
+        gca = ga.z;
+        gcb = ga.w;
+        gcc = gb.x;
+    }
+}
+
 // Two forms of the same backward, chosen by the number of views of the launch: with many
 // views the 45 dL/d sh_rest accumulators and the coefficients stay in registers (fewer
 // instructions per view); with one or two views they live in shared memory and cache (fewer
@@ -322,7 +345,7 @@ constexpr int kBwdThreads = 128;
 __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_reg(GaussPtrs g, const __grid_constant__ CamBatch cb,
                                                         const float4 *__restrict__ sgrads,
                                                         const int32_t *__restrict__ radii,
-                                                        GradPtrs out, int no_sh_rest) {
+                                                        GradPtrs out, int no_sh_rest, int moments) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const int64_t n = g.n;
@@ -371,7 +394,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_reg(GaussPtrs g,
             ViewGeom vg;
             if (!view_geom(s, c, g.near_z, vg)) continue;  // cannot happen when rad > 0
             any = true;
-            float gmx = ga.x, gmy = ga.y, gca = ga.z, gcb = ga.w, gcc = gb4.x;
+            float gmx, gmy, gca, gcb, gcc;
+            splat_grads(ga, gb4, moments, s.op, vg.ca, vg.cb, vg.cc, gmx, gmy, gca, gcb, gcc);
             g_op += gb4.y;
             float3 g_rgb = make_float3(gb4.z, gb4.w, gc4.x);
             st_acc += sqrtf(gmx * gmx + gmy * gmy);
@@ -549,7 +573,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_reg(GaussPtrs g,
 __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_smem(GaussPtrs g, const __grid_constant__ CamBatch cb,
                                                         const float4 *__restrict__ sgrads,
                                                         const int32_t *__restrict__ radii,
-                                                        GradPtrs out, int no_sh_rest) {
+                                                        GradPtrs out, int no_sh_rest, int moments) {
     // dL/d sh_rest accumulates in shared memory ([coefficient][thread]: no bank conflicts)
     // and the SH coefficients are re-read per view from cache, to keep registers for the rest
     __shared__ float s_gf[45][kBwdThreads];
@@ -580,7 +604,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_smem(GaussPtrs g
             if (!view_geom(s, c, g.near_z, vg)) continue;  // cannot happen when rad > 0
             any = true;
             float4 ga = sgrads[3 * r], gb4 = sgrads[3 * r + 1], gc4 = sgrads[3 * r + 2];
-            float gmx = ga.x, gmy = ga.y, gca = ga.z, gcb = ga.w, gcc = gb4.x;
+            float gmx, gmy, gca, gcb, gcc;
+            splat_grads(ga, gb4, moments, s.op, vg.ca, vg.cb, vg.cc, gmx, gmy, gca, gcb, gcc);
             g_op += gb4.y;
             float3 g_rgb = make_float3(gb4.z, gb4.w, gc4.x);
             st_acc += sqrtf(gmx * gmx + gmy * gmy);
@@ -774,15 +799,15 @@ void launch_preprocess(const GaussPtrs &g, const CamBatch &cb, float4 *splats, i
 
 void launch_preprocess_backward(const GaussPtrs &g, const CamBatch &cb, const float4 *sgrads,
                                 const int32_t *radii, const GradPtrs &out, int no_sh_rest,
-                                cudaStream_t st) {
+                                int moments, cudaStream_t st) {
     if (g.n <= 0) return;
     const int bs = kBwdThreads;
     const int64_t grid = (g.n + bs - 1) / bs;
     count_launch();
     if (cb.V <= 2)
-        k_preprocess_bwd_smem<<<(unsigned)grid, bs, 0, st>>>(g, cb, sgrads, radii, out, no_sh_rest);
+        k_preprocess_bwd_smem<<<(unsigned)grid, bs, 0, st>>>(g, cb, sgrads, radii, out, no_sh_rest, moments);
     else
-        k_preprocess_bwd_reg<<<(unsigned)grid, bs, 0, st>>>(g, cb, sgrads, radii, out, no_sh_rest);
+        k_preprocess_bwd_reg<<<(unsigned)grid, bs, 0, st>>>(g, cb, sgrads, radii, out, no_sh_rest, moments);
 }
 
 }  // namespace tgs

@@ -161,9 +161,10 @@ __device__ __forceinline__ int for_kept_tiles(const float4 &s0, const float4 &s1
 void launch_preprocess(const GaussPtrs &g, const CamBatch &cb, float4 *splats, int32_t *radii,
                        uint32_t *tiles_touched, uint32_t *depth_bits, float *zero_grads,
                        cudaStream_t st);
+// moments != 0: the gradient records hold the pixel sums of the fused blend backward
 void launch_preprocess_backward(const GaussPtrs &g, const CamBatch &cb, const float4 *sgrads,
                                 const int32_t *radii, const GradPtrs &out, int no_sh_rest,
-                                cudaStream_t st);
+                                int moments, cudaStream_t st);
 
 // sort.cu
 struct SortScratch {
