@@ -1,15 +1,3 @@
-// Front-to-back alpha blending (Eq. 2 of the paper) and its backward.
-//
-// One CTA per (view, tile); TILE*TILE/PPT threads, each owning PPT pixels of the tile.
-// The tile's depth-sorted list is streamed through shared memory in batches of one splat
-// per thread. The forward stops a pixel before the fragment that would bring its
-// transmittance below 1e-4 and leaves the CTA's loop once every pixel has stopped. The
-// backward walks the list in reverse from each pixel's last contributor, recovering the
-// transmittance in front of each fragment from T_final by division, and scatters the
-// per-splat gradients with one warp-level transposed reduction and one atomic per value
-// per warp.
-#include "tgs_internal.cuh"
-
 // Front-to-back alpha blending (Eq. 2 of the paper) and its backward, one CTA per (view,
 // tile). The per-tile work lives in blend_common.cuh (shared with the fused kernel): the
 // tile's depth-sorted list is streamed through shared memory in batches of one splat per
