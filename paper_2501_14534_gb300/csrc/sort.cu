@@ -305,7 +305,9 @@ k_radix_hist(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int64_t n
 // holding the same digit). Then one pass over the digits turns the per-warp counts into each
 // warp's start within each digit, the items are placed in shared memory in (digit, index)
 // order, and written out so that each digit's run of the block goes to consecutive addresses.
-__global__ void __launch_bounds__(kRadixThreads)
+// The values wait in shared memory in input order meanwhile (registers only for keys and
+// ranks: 5 CTAs per SM).
+__global__ void __launch_bounds__(kRadixThreads, 5)
 k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 const uint32_t *n_dev, int64_t n_cap, int shift, uint32_t mask,
                 const uint32_t *__restrict__ offsets, int64_t nblocks,
@@ -315,7 +317,7 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     __shared__ uint32_t s_start[kRadixBins];    // start of each digit in the block's order
     __shared__ uint32_t s_goff[kRadixBins];     // global position of the block's digit run
     __shared__ uint32_t s_warp[33];
-    __shared__ uint32_t s_k[kRadixTile], s_v[kRadixTile];
+    __shared__ uint32_t s_k[kRadixTile], s_v[kRadixTile], s_vin[kRadixTile];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const unsigned full = 0xffffffffu;
     const int64_t n = count_of(n_dev, n_cap);
@@ -326,7 +328,7 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     for (int q = 0; q < NW; q++) s_cnt[q][t] = 0u;
     s_goff[t] = offsets[(int64_t)t * nblocks + blockIdx.x];
     __syncthreads();
-    uint32_t kr[R], vr[R], rk[R];
+    uint32_t kr[R], rk[R];
     const uint32_t lt_mask = (1u << lane) - 1u;
     const int wbase = w * 32 * R;
 #pragma unroll
@@ -334,7 +336,11 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
         const int j = wbase + r * 32 + lane;
         const bool valid = j < cnt;
         kr[r] = valid ? keys_in[base + j] : 0u;
-        vr[r] = valid ? vals_in[base + j] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int j = wbase + r * 32 + lane;
+        if (j < cnt) s_vin[j] = vals_in[base + j];
     }
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -372,7 +378,7 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
             const uint32_t d = (kr[r] >> shift) & mask;
             const uint32_t lp = s_start[d] + s_cnt[w][d] + rk[r];
             s_k[lp] = kr[r];
-            s_v[lp] = vr[r];
+            s_v[lp] = s_vin[j];
         }
     }
     __syncthreads();
