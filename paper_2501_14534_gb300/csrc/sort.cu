@@ -351,7 +351,7 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
 #pragma unroll
         for (int b = 0; b < 8; b++) {
             const uint32_t bal = __ballot_sync(full, (d >> b) & 1u);
-            peers &= ((d >> b) & 1u) ? bal : ~bal;
+            peers &= bal ^ (((d >> b) & 1u) - 1u);   // bal where the bit is set, ~bal where not
         }
         const uint32_t before = s_cnt[w][d];
         rk[r] = before + __popc(peers & lt_mask);
