@@ -363,33 +363,34 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_reg(GaussPtrs g,
     bool any = false;
     if (s.ok) {
         // the views where the Gaussian is visible, read up front (independent loads), and the
-        // splat gradients of the next visible view prefetched while this one is processed
+        // splat gradients of the next view prefetched while this one is processed. The loop
+        // runs over all views in step across the warp, so that the camera read is the same
+        // for every lane (one broadcast, not one constant-cache access per distinct view).
         uint64_t vis = 0;
 #pragma unroll 8
-        for (int v = 0; v < cb.V; v++)
-            if (radii[(int64_t)v * n + i] > 0) vis |= 1ull << v;
-        load_sh(g, i, s, sh);
-        int vnext = vis ? __ffsll((long long)vis) - 1 : -1;
-        float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na, nc = na;
-        if (vnext >= 0) {
-            const int64_t r = (int64_t)vnext * n + i;
-            na = sgrads[3 * r];
-            nb = sgrads[3 * r + 1];
-            nc = sgrads[3 * r + 2];
+        for (int v = 0; v < cb.V; v++) {
+            const int rad = radii[(int64_t)v * n + i];
+            if (rad > 0) {
+                vis |= 1ull << v;
+                st_max = max(st_max, rad);
+            }
         }
-        while (vnext >= 0) {
-            const int v = vnext;
+        load_sh(g, i, s, sh);
+        float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na, nc = na;
+        if (vis & 1ull) {
+            na = sgrads[3 * i];
+            nb = sgrads[3 * i + 1];
+            nc = sgrads[3 * i + 2];
+        }
+        for (int v = 0; v < cb.V; v++) {
             const float4 ga = na, gb4 = nb, gc4 = nc;
-            vis &= vis - 1ull;
-            vnext = vis ? __ffsll((long long)vis) - 1 : -1;
-            if (vnext >= 0) {
-                const int64_t rn = (int64_t)vnext * n + i;
+            if (v + 1 < cb.V && ((vis >> (v + 1)) & 1ull)) {
+                const int64_t rn = (int64_t)(v + 1) * n + i;
                 na = sgrads[3 * rn];
                 nb = sgrads[3 * rn + 1];
                 nc = sgrads[3 * rn + 2];
             }
-            const int64_t r = (int64_t)v * n + i;
-            const int rad = radii[r];
+            if (!((vis >> v) & 1ull)) continue;
             const DevCam &c = cb.c[v];
             ViewGeom vg;
             if (!view_geom(s, c, g.near_z, vg)) continue;  // cannot happen when rad > 0
@@ -400,7 +401,6 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_reg(GaussPtrs g,
             float3 g_rgb = make_float3(gb4.z, gb4.w, gc4.x);
             st_acc += sqrtf(gmx * gmx + gmy * gmy);
             st_cnt += 1;
-            st_max = max(st_max, rad);
 
             // ---- colour ----
             float dx = s.mu.x - c.campos[0], dy = s.mu.y - c.campos[1], dz = s.mu.z - c.campos[2];
