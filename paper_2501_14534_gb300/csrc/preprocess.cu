@@ -313,6 +313,120 @@ __device__ __forceinline__ void out_write(float *p, int64_t idx, float v, int ac
     if (acc) p[idx] += v; else p[idx] = v;
 }
 
+// EWA backward of one view: dL/dSigma (full-matrix entries xx, xy, xz, yy, yz, zz) and dL/dmu
+// from the view's dL/d mean2d and dL/d conic.
+__device__ __forceinline__ void view_geom_backward(const GaussState &s, const DevCam &c, const ViewGeom &vg,
+                                                   float gmx, float gmy, float gca, float gcb, float gcc,
+                                                   float g_S[6], float3 &g_mu) {
+    // ---- conic -> Sigma': G = -Q dL/dQ Q, dL/dQ = [[ga, gb/2], [gb/2, gc]] ----
+    float a = vg.ca, b = vg.cb, cc = vg.cc;
+    float G00 = -(a * a * gca + a * b * gcb + b * b * gcc);
+    float G01 = -(a * b * gca + 0.5f * (b * b + a * cc) * gcb + b * cc * gcc);
+    float G11 = -(b * b * gca + b * cc * gcb + cc * cc * gcc);
+    // ---- Sigma' = T Sigma T^T: dL/dSigma = T^T G T ----
+    const float *T0 = vg.T0, *T1 = vg.T1;
+    // full-matrix entries (a,b) for a <= b: xx, xy, xz, yy, yz, zz
+    const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+    for (int e = 0; e < 6; e++) {
+        int p = ia[e], q = ib[e];
+        g_S[e] += T0[p] * T0[q] * G00 + (T0[p] * T1[q] + T1[p] * T0[q]) * G01 + T1[p] * T1[q] * G11;
+    }
+    // dL/dT = 2 G T Sigma
+    const float *S = s.S;
+    float sT0[3] = {S[0] * T0[0] + S[1] * T0[1] + S[2] * T0[2],
+                    S[1] * T0[0] + S[3] * T0[1] + S[4] * T0[2],
+                    S[2] * T0[0] + S[4] * T0[1] + S[5] * T0[2]};
+    float sT1[3] = {S[0] * T1[0] + S[1] * T1[1] + S[2] * T1[2],
+                    S[1] * T1[0] + S[3] * T1[1] + S[4] * T1[2],
+                    S[2] * T1[0] + S[4] * T1[1] + S[5] * T1[2]};
+    float GT0[3], GT1[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        GT0[k] = 2.f * (G00 * sT0[k] + G01 * sT1[k]);
+        GT1[k] = 2.f * (G01 * sT0[k] + G11 * sT1[k]);
+    }
+    // dL/dJ = dL/dT W^T (entries 00, 02, 11, 12)
+    const float *W = c.R;
+    float GJ00 = GT0[0] * W[0] + GT0[1] * W[1] + GT0[2] * W[2];
+    float GJ02 = GT0[0] * W[6] + GT0[1] * W[7] + GT0[2] * W[8];
+    float GJ11 = GT1[0] * W[3] + GT1[1] * W[4] + GT1[2] * W[5];
+    float GJ12 = GT1[0] * W[6] + GT1[1] * W[7] + GT1[2] * W[8];
+    float itz = vg.inv_tz, itz2 = itz * itz;
+    float g_tx = 0.f, g_ty = 0.f, g_tz = 0.f;
+    g_tz += -c.fx * itz2 * GJ00 - c.fy * itz2 * GJ11;
+    // J02 = -fx u / tz, u = clamp(tx / tz)
+    float du_dtx = vg.cx_on ? 0.f : itz, du_dtz = vg.cx_on ? 0.f : -vg.tx * itz2;
+    float dw_dty = vg.cy_on ? 0.f : itz, dw_dtz = vg.cy_on ? 0.f : -vg.ty * itz2;
+    g_tx += GJ02 * (-c.fx * itz) * du_dtx;
+    g_tz += GJ02 * (c.fx * vg.u * itz2 - c.fx * itz * du_dtz);
+    g_ty += GJ12 * (-c.fy * itz) * dw_dty;
+    g_tz += GJ12 * (c.fy * vg.w * itz2 - c.fy * itz * dw_dtz);
+    // mean2d = f t / tz + c - 1/2
+    g_tx += gmx * c.fx * itz;
+    g_ty += gmy * c.fy * itz;
+    g_tz += -(gmx * c.fx * vg.tx + gmy * c.fy * vg.ty) * itz2;
+    // t = W mu + tau
+    g_mu.x += W[0] * g_tx + W[3] * g_ty + W[6] * g_tz;
+    g_mu.y += W[1] * g_tx + W[4] * g_ty + W[7] * g_tz;
+    g_mu.z += W[2] * g_tx + W[5] * g_ty + W[8] * g_tz;
+}
+
+// Parameter gradients of one Gaussian from its summed dL/dSigma, dL/d opacity and per-band
+// colour gradients (the latter for the SH band masks).
+__device__ __forceinline__ void gauss_backward(const GaussPtrs &g, int64_t i, const GaussState &s,
+                                               const float g_S[6], float g_op, const float g_band[4],
+                                               float g_q[4], float g_ls[3], float &g_o, float &g_m,
+                                               float g_shm[3]) {
+    // ---- Sigma = (R S)(R S)^T: dL/d(RS) = (G + G^T)(RS), G symmetric here ----
+    const float *R = s.R;
+    float Gf[9] = {g_S[0], g_S[1], g_S[2], g_S[1], g_S[3], g_S[4], g_S[2], g_S[4], g_S[5]};
+    // Gf holds the full-matrix gradient with both off-diagonal entries equal to the
+    // gradient of one entry, so (G + G^T) = 2 Gf.
+    float g_s[3] = {0.f, 0.f, 0.f}, GR[9];
+#pragma unroll
+    for (int rr = 0; rr < 3; rr++)
+#pragma unroll
+        for (int cc = 0; cc < 3; cc++) {
+            float acc2 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; k++) acc2 += 2.f * Gf[3 * rr + k] * R[3 * k + cc] * s.scale[cc];
+            g_s[cc] += acc2 * R[3 * rr + cc];
+            GR[3 * rr + cc] = acc2 * s.scale[cc];
+        }
+    // dR/dq for q = (w, x, y, z)
+    float w = s.qn[0], x = s.qn[1], y = s.qn[2], z = s.qn[3];
+    float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
+    float gx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] + w * GR[7] - 2.f * x * GR[8]);
+    float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6] + z * GR[7] - 2.f * y * GR[8]);
+    float gz = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] + y * GR[5] + x * GR[6] + y * GR[7]);
+    float qd = gw * w + gx * x + gy * y + gz * z;
+    float iq = 1.f / s.qnorm;
+    g_q[0] = (gw - w * qd) * iq;
+    g_q[1] = (gx - x * qd) * iq;
+    g_q[2] = (gy - y * qd) * iq;
+    g_q[3] = (gz - z * qd) * iq;
+    float gM = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        g_ls[k] = g_s[k] * s.scale[k];
+        gM += g_s[k] * s.scale[k];  // exp(l_k) = scale_k since M = 1 here
+    }
+    g_o = g_op * s.M * s.sig_o * (1.f - s.sig_o);
+    gM += g_op * s.sig_o;
+    if (g.mask) {
+        float sm = sigmoidf_(g.mask[i]);
+        g_m = gM * sm * (1.f - sm);
+    }
+    if (g.shmask)
+#pragma unroll
+        for (int l = 1; l <= 3; l++) {
+            if (l > s.deg) continue;
+            float sm = sigmoidf_(g.shmask[3 * i + l - 1]);
+            g_shm[l - 1] = g_band[l] * sm * (1.f - sm);
+        }
+}
+
 constexpr int kBwdThreads = 128;
 
 // Splat gradients of one (view, Gaussian) from its gradient record: either the gradients
@@ -433,58 +547,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_reg(GaussPtrs g,
             g_mu.y += (g_dir.y - y * dd) * inv;
             g_mu.z += (g_dir.z - z * dd) * inv;
 
-            // ---- conic -> Sigma': G = -Q dL/dQ Q, dL/dQ = [[ga, gb/2], [gb/2, gc]] ----
-            float a = vg.ca, b = vg.cb, cc = vg.cc;
-            float G00 = -(a * a * gca + a * b * gcb + b * b * gcc);
-            float G01 = -(a * b * gca + 0.5f * (b * b + a * cc) * gcb + b * cc * gcc);
-            float G11 = -(b * b * gca + b * cc * gcb + cc * cc * gcc);
-            // ---- Sigma' = T Sigma T^T: dL/dSigma = T^T G T ----
-            const float *T0 = vg.T0, *T1 = vg.T1;
-            // full-matrix entries (a,b) for a <= b: xx, xy, xz, yy, yz, zz
-            const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-            for (int e = 0; e < 6; e++) {
-                int p = ia[e], q = ib[e];
-                g_S[e] += T0[p] * T0[q] * G00 + (T0[p] * T1[q] + T1[p] * T0[q]) * G01 + T1[p] * T1[q] * G11;
-            }
-            // dL/dT = 2 G T Sigma
-            const float *S = s.S;
-            float sT0[3] = {S[0] * T0[0] + S[1] * T0[1] + S[2] * T0[2],
-                            S[1] * T0[0] + S[3] * T0[1] + S[4] * T0[2],
-                            S[2] * T0[0] + S[4] * T0[1] + S[5] * T0[2]};
-            float sT1[3] = {S[0] * T1[0] + S[1] * T1[1] + S[2] * T1[2],
-                            S[1] * T1[0] + S[3] * T1[1] + S[4] * T1[2],
-                            S[2] * T1[0] + S[4] * T1[1] + S[5] * T1[2]};
-            float GT0[3], GT1[3];
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                GT0[k] = 2.f * (G00 * sT0[k] + G01 * sT1[k]);
-                GT1[k] = 2.f * (G01 * sT0[k] + G11 * sT1[k]);
-            }
-            // dL/dJ = dL/dT W^T (entries 00, 02, 11, 12)
-            const float *W = c.R;
-            float GJ00 = GT0[0] * W[0] + GT0[1] * W[1] + GT0[2] * W[2];
-            float GJ02 = GT0[0] * W[6] + GT0[1] * W[7] + GT0[2] * W[8];
-            float GJ11 = GT1[0] * W[3] + GT1[1] * W[4] + GT1[2] * W[5];
-            float GJ12 = GT1[0] * W[6] + GT1[1] * W[7] + GT1[2] * W[8];
-            float itz = vg.inv_tz, itz2 = itz * itz;
-            float g_tx = 0.f, g_ty = 0.f, g_tz = 0.f;
-            g_tz += -c.fx * itz2 * GJ00 - c.fy * itz2 * GJ11;
-            // J02 = -fx u / tz, u = clamp(tx / tz)
-            float du_dtx = vg.cx_on ? 0.f : itz, du_dtz = vg.cx_on ? 0.f : -vg.tx * itz2;
-            float dw_dty = vg.cy_on ? 0.f : itz, dw_dtz = vg.cy_on ? 0.f : -vg.ty * itz2;
-            g_tx += GJ02 * (-c.fx * itz) * du_dtx;
-            g_tz += GJ02 * (c.fx * vg.u * itz2 - c.fx * itz * du_dtz);
-            g_ty += GJ12 * (-c.fy * itz) * dw_dty;
-            g_tz += GJ12 * (c.fy * vg.w * itz2 - c.fy * itz * dw_dtz);
-            // mean2d = f t / tz + c - 1/2
-            g_tx += gmx * c.fx * itz;
-            g_ty += gmy * c.fy * itz;
-            g_tz += -(gmx * c.fx * vg.tx + gmy * c.fy * vg.ty) * itz2;
-            // t = W mu + tau
-            g_mu.x += W[0] * g_tx + W[3] * g_ty + W[6] * g_tz;
-            g_mu.y += W[1] * g_tx + W[4] * g_ty + W[7] * g_tz;
-            g_mu.z += W[2] * g_tx + W[5] * g_ty + W[8] * g_tz;
+            view_geom_backward(s, c, vg, gmx, gmy, gca, gcb, gcc, g_S, g_mu);
         }
     }
     const int acc = out.accumulate;
@@ -496,55 +559,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_reg(GaussPtrs g,
     }
     float g_q[4] = {0.f, 0.f, 0.f, 0.f}, g_ls[3] = {0.f, 0.f, 0.f}, g_o = 0.f, g_m = 0.f;
     float g_shm[3] = {0.f, 0.f, 0.f};
-    if (any) {
-        // ---- Sigma = (R S)(R S)^T: dL/d(RS) = (G + G^T)(RS), G symmetric here ----
-        const float *R = s.R;
-        float Gf[9] = {g_S[0], g_S[1], g_S[2], g_S[1], g_S[3], g_S[4], g_S[2], g_S[4], g_S[5]};
-        // Gf holds the full-matrix gradient with both off-diagonal entries equal to the
-        // gradient of one entry, so (G + G^T) = 2 Gf.
-        float g_s[3] = {0.f, 0.f, 0.f}, GR[9];
-#pragma unroll
-        for (int rr = 0; rr < 3; rr++)
-#pragma unroll
-            for (int cc = 0; cc < 3; cc++) {
-                float acc2 = 0.f;
-#pragma unroll
-                for (int k = 0; k < 3; k++) acc2 += 2.f * Gf[3 * rr + k] * R[3 * k + cc] * s.scale[cc];
-                g_s[cc] += acc2 * R[3 * rr + cc];
-                GR[3 * rr + cc] = acc2 * s.scale[cc];
-            }
-        // dR/dq for q = (w, x, y, z)
-        float w = s.qn[0], x = s.qn[1], y = s.qn[2], z = s.qn[3];
-        float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
-        float gx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] + w * GR[7] - 2.f * x * GR[8]);
-        float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6] + z * GR[7] - 2.f * y * GR[8]);
-        float gz = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] + y * GR[5] + x * GR[6] + y * GR[7]);
-        float qd = gw * w + gx * x + gy * y + gz * z;
-        float iq = 1.f / s.qnorm;
-        g_q[0] = (gw - w * qd) * iq;
-        g_q[1] = (gx - x * qd) * iq;
-        g_q[2] = (gy - y * qd) * iq;
-        g_q[3] = (gz - z * qd) * iq;
-        float gM = 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            g_ls[k] = g_s[k] * s.scale[k];
-            gM += g_s[k] * s.scale[k];  // exp(l_k) = scale_k since M = 1 here
-        }
-        g_o = g_op * s.M * s.sig_o * (1.f - s.sig_o);
-        gM += g_op * s.sig_o;
-        if (g.mask) {
-            float sm = sigmoidf_(g.mask[i]);
-            g_m = gM * sm * (1.f - sm);
-        }
-        if (g.shmask)
-#pragma unroll
-            for (int l = 1; l <= 3; l++) {
-                if (l > s.deg) continue;
-                float sm = sigmoidf_(g.shmask[3 * i + l - 1]);
-                g_shm[l - 1] = g_band[l] * sm * (1.f - sm);
-            }
-    }
+    if (any) gauss_backward(g, i, s, g_S, g_op, g_band, g_q, g_ls, g_o, g_m, g_shm);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         out_write(out.means, 3 * i + k, k == 0 ? g_mu.x : (k == 1 ? g_mu.y : g_mu.z), acc);
@@ -652,58 +667,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_smem(GaussPtrs g
             g_mu.y += (g_dir.y - y * dd) * inv;
             g_mu.z += (g_dir.z - z * dd) * inv;
 
-            // ---- conic -> Sigma': G = -Q dL/dQ Q, dL/dQ = [[ga, gb/2], [gb/2, gc]] ----
-            float a = vg.ca, b = vg.cb, cc = vg.cc;
-            float G00 = -(a * a * gca + a * b * gcb + b * b * gcc);
-            float G01 = -(a * b * gca + 0.5f * (b * b + a * cc) * gcb + b * cc * gcc);
-            float G11 = -(b * b * gca + b * cc * gcb + cc * cc * gcc);
-            // ---- Sigma' = T Sigma T^T: dL/dSigma = T^T G T ----
-            const float *T0 = vg.T0, *T1 = vg.T1;
-            // full-matrix entries (a,b) for a <= b: xx, xy, xz, yy, yz, zz
-            const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-            for (int e = 0; e < 6; e++) {
-                int p = ia[e], q = ib[e];
-                g_S[e] += T0[p] * T0[q] * G00 + (T0[p] * T1[q] + T1[p] * T0[q]) * G01 + T1[p] * T1[q] * G11;
-            }
-            // dL/dT = 2 G T Sigma
-            const float *S = s.S;
-            float sT0[3] = {S[0] * T0[0] + S[1] * T0[1] + S[2] * T0[2],
-                            S[1] * T0[0] + S[3] * T0[1] + S[4] * T0[2],
-                            S[2] * T0[0] + S[4] * T0[1] + S[5] * T0[2]};
-            float sT1[3] = {S[0] * T1[0] + S[1] * T1[1] + S[2] * T1[2],
-                            S[1] * T1[0] + S[3] * T1[1] + S[4] * T1[2],
-                            S[2] * T1[0] + S[4] * T1[1] + S[5] * T1[2]};
-            float GT0[3], GT1[3];
-#pragma unroll
-            for (int k = 0; k < 3; k++) {
-                GT0[k] = 2.f * (G00 * sT0[k] + G01 * sT1[k]);
-                GT1[k] = 2.f * (G01 * sT0[k] + G11 * sT1[k]);
-            }
-            // dL/dJ = dL/dT W^T (entries 00, 02, 11, 12)
-            const float *W = c.R;
-            float GJ00 = GT0[0] * W[0] + GT0[1] * W[1] + GT0[2] * W[2];
-            float GJ02 = GT0[0] * W[6] + GT0[1] * W[7] + GT0[2] * W[8];
-            float GJ11 = GT1[0] * W[3] + GT1[1] * W[4] + GT1[2] * W[5];
-            float GJ12 = GT1[0] * W[6] + GT1[1] * W[7] + GT1[2] * W[8];
-            float itz = vg.inv_tz, itz2 = itz * itz;
-            float g_tx = 0.f, g_ty = 0.f, g_tz = 0.f;
-            g_tz += -c.fx * itz2 * GJ00 - c.fy * itz2 * GJ11;
-            // J02 = -fx u / tz, u = clamp(tx / tz)
-            float du_dtx = vg.cx_on ? 0.f : itz, du_dtz = vg.cx_on ? 0.f : -vg.tx * itz2;
-            float dw_dty = vg.cy_on ? 0.f : itz, dw_dtz = vg.cy_on ? 0.f : -vg.ty * itz2;
-            g_tx += GJ02 * (-c.fx * itz) * du_dtx;
-            g_tz += GJ02 * (c.fx * vg.u * itz2 - c.fx * itz * du_dtz);
-            g_ty += GJ12 * (-c.fy * itz) * dw_dty;
-            g_tz += GJ12 * (c.fy * vg.w * itz2 - c.fy * itz * dw_dtz);
-            // mean2d = f t / tz + c - 1/2
-            g_tx += gmx * c.fx * itz;
-            g_ty += gmy * c.fy * itz;
-            g_tz += -(gmx * c.fx * vg.tx + gmy * c.fy * vg.ty) * itz2;
-            // t = W mu + tau
-            g_mu.x += W[0] * g_tx + W[3] * g_ty + W[6] * g_tz;
-            g_mu.y += W[1] * g_tx + W[4] * g_ty + W[7] * g_tz;
-            g_mu.z += W[2] * g_tx + W[5] * g_ty + W[8] * g_tz;
+            view_geom_backward(s, c, vg, gmx, gmy, gca, gcb, gcc, g_S, g_mu);
         }
     }
     const int acc = out.accumulate;
@@ -715,55 +679,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_smem(GaussPtrs g
     }
     float g_q[4] = {0.f, 0.f, 0.f, 0.f}, g_ls[3] = {0.f, 0.f, 0.f}, g_o = 0.f, g_m = 0.f;
     float g_shm[3] = {0.f, 0.f, 0.f};
-    if (any) {
-        // ---- Sigma = (R S)(R S)^T: dL/d(RS) = (G + G^T)(RS), G symmetric here ----
-        const float *R = s.R;
-        float Gf[9] = {g_S[0], g_S[1], g_S[2], g_S[1], g_S[3], g_S[4], g_S[2], g_S[4], g_S[5]};
-        // Gf holds the full-matrix gradient with both off-diagonal entries equal to the
-        // gradient of one entry, so (G + G^T) = 2 Gf.
-        float g_s[3] = {0.f, 0.f, 0.f}, GR[9];
-#pragma unroll
-        for (int rr = 0; rr < 3; rr++)
-#pragma unroll
-            for (int cc = 0; cc < 3; cc++) {
-                float acc2 = 0.f;
-#pragma unroll
-                for (int k = 0; k < 3; k++) acc2 += 2.f * Gf[3 * rr + k] * R[3 * k + cc] * s.scale[cc];
-                g_s[cc] += acc2 * R[3 * rr + cc];
-                GR[3 * rr + cc] = acc2 * s.scale[cc];
-            }
-        // dR/dq for q = (w, x, y, z)
-        float w = s.qn[0], x = s.qn[1], y = s.qn[2], z = s.qn[3];
-        float gw = 2.f * (-z * GR[1] + y * GR[2] + z * GR[3] - x * GR[5] - y * GR[6] + x * GR[7]);
-        float gx = 2.f * (y * GR[1] + z * GR[2] + y * GR[3] - 2.f * x * GR[4] - w * GR[5] + z * GR[6] + w * GR[7] - 2.f * x * GR[8]);
-        float gy = 2.f * (-2.f * y * GR[0] + x * GR[1] + w * GR[2] + x * GR[3] + z * GR[5] - w * GR[6] + z * GR[7] - 2.f * y * GR[8]);
-        float gz = 2.f * (-2.f * z * GR[0] - w * GR[1] + x * GR[2] + w * GR[3] - 2.f * z * GR[4] + y * GR[5] + x * GR[6] + y * GR[7]);
-        float qd = gw * w + gx * x + gy * y + gz * z;
-        float iq = 1.f / s.qnorm;
-        g_q[0] = (gw - w * qd) * iq;
-        g_q[1] = (gx - x * qd) * iq;
-        g_q[2] = (gy - y * qd) * iq;
-        g_q[3] = (gz - z * qd) * iq;
-        float gM = 0.f;
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            g_ls[k] = g_s[k] * s.scale[k];
-            gM += g_s[k] * s.scale[k];  // exp(l_k) = scale_k since M = 1 here
-        }
-        g_o = g_op * s.M * s.sig_o * (1.f - s.sig_o);
-        gM += g_op * s.sig_o;
-        if (g.mask) {
-            float sm = sigmoidf_(g.mask[i]);
-            g_m = gM * sm * (1.f - sm);
-        }
-        if (g.shmask)
-#pragma unroll
-            for (int l = 1; l <= 3; l++) {
-                if (l > s.deg) continue;
-                float sm = sigmoidf_(g.shmask[3 * i + l - 1]);
-                g_shm[l - 1] = g_band[l] * sm * (1.f - sm);
-            }
-    }
+    if (any) gauss_backward(g, i, s, g_S, g_op, g_band, g_q, g_ls, g_o, g_m, g_shm);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         out_write(out.means, 3 * i + k, k == 0 ? g_mu.x : (k == 1 ? g_mu.y : g_mu.z), acc);

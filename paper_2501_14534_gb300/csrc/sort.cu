@@ -182,6 +182,7 @@ k_count_keys(const uint32_t *__restrict__ sorted_ids, const uint32_t *n_dev, int
     __shared__ uint32_t s_m[NW][32][2];  // kept-tile bits of rects of at most 64 tiles
     __shared__ uint32_t s_c[NW][32];     // kept-tile counts
     __shared__ uint32_t s_warp[33];
+    const int lb = __ffs(B) - 1;  // B is 8, 16 or 32
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t n = count_of(n_dev, n_cap);
@@ -204,10 +205,10 @@ k_count_keys(const uint32_t *__restrict__ sorted_ids, const uint32_t *n_dev, int
             ry = __float_as_uint(s2.z);
             const int ix0 = (int)(rx & 0xFFFFu), ix1 = (int)(rx >> 16);
             const int iy0 = (int)(ry & 0xFFFFu), iy1 = (int)(ry >> 16);
-            tx0 = ix0 / B;
-            ty0 = iy0 / B;
-            nx = ix1 / B - tx0 + 1;
-            const int ny = iy1 / B - ty0 + 1;
+            tx0 = ix0 >> lb;
+            ty0 = iy0 >> lb;
+            nx = (ix1 >> lb) - tx0 + 1;
+            const int ny = (iy1 >> lb) - ty0 + 1;
             ntiles = (nx > 0 && ny > 0) ? (uint32_t)nx * (uint32_t)ny : 0u;
             s_g[w][lane] = s0;
             s_h[w][lane] = make_float4(s1.x, s3.x, s3.y, s3.z);
@@ -424,7 +425,7 @@ __device__ __forceinline__ int select_bit(uint32_t lo, uint32_t hi, uint32_t k) 
 __global__ void __launch_bounds__(kScanThreads)
 k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ block_off,
        const uint32_t *n_dev, int64_t n_cap, const KeyInfo ki, const float4 *__restrict__ splats,
-       uint32_t n_gauss, const __grid_constant__ CamBatch cb, uint32_t *__restrict__ tile_keys,
+       uint32_t n_gauss, uint32_t n_magic, const __grid_constant__ CamBatch cb, uint32_t *__restrict__ tile_keys,
        uint32_t *__restrict__ tile_vals, const uint32_t *K_dev, int64_t key_cap, uint32_t *status) {
     constexpr int NW = kScanThreads / 32;
     __shared__ uint32_t s_wtot[NW];
@@ -446,7 +447,7 @@ k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ blo
     __syncthreads();
     int64_t off = (int64_t)block_off[blockIdx.x];
     for (int q = 0; q < w; q++) off += s_wtot[q];
-    const int B = cb.tile;
+    const int B = cb.tile, lb = __ffs(cb.tile) - 1;
 #pragma unroll 1
     for (int q = 0; q < kScanItems; q++) {
         const int64_t j = wbase + q * 32 + lane;
@@ -463,15 +464,20 @@ k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ blo
         bool big = false;
         if (cnt > 0u) {
             rec = sorted_ids[j];
-            const DevCam &c = cb.c[rec / n_gauss];
+            uint32_t v = rec;  // view = rec / n_gauss, by multiplying with ceil(2^32 / n_gauss)
+            if (n_magic) {
+                v = __umulhi(rec, n_magic);
+                if ((uint64_t)v * n_gauss > rec) v--;
+            }
+            const DevCam &c = cb.c[v];
             gx = c.gx;
             gy = c.gy;
             toff = c.tile_offset;
             const uint32_t rx = ki.rx[j], ry = ki.ry[j];
-            tx0 = (int)(rx & 0xFFFFu) / B;
-            ty0 = (int)(ry & 0xFFFFu) / B;
-            nx = (int)(rx >> 16) / B - tx0 + 1;
-            const int ny = (int)(ry >> 16) / B - ty0 + 1;
+            tx0 = (int)(rx & 0xFFFFu) >> lb;
+            ty0 = (int)(ry & 0xFFFFu) >> lb;
+            nx = ((int)(rx >> 16) >> lb) - tx0 + 1;
+            const int ny = ((int)(ry >> 16) >> lb) - ty0 + 1;
             big = (int64_t)nx * ny > 64;
             if (!big) m = ki.km[j];
         }
@@ -490,7 +496,7 @@ k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ blo
             const uint32_t rx = __float_as_uint(s2.y), ry = __float_as_uint(s2.z);
             const int ix0 = (int)(rx & 0xFFFFu), ix1 = (int)(rx >> 16);
             const int iy0 = (int)(ry & 0xFFFFu), iy1 = (int)(ry >> 16);
-            const int64_t nt = (int64_t)nxo * (iy1 / B - tyo + 1);
+            const int64_t nt = (int64_t)nxo * ((iy1 >> lb) - tyo + 1);
             int64_t kept = 0;
             for (int64_t t0 = 0; t0 < nt; t0 += 32) {
                 const int64_t tl = t0 + lane;
@@ -658,8 +664,10 @@ void emit_keys(const uint32_t *sorted_ids, const uint32_t *block_offsets, const 
                uint32_t *status, cudaStream_t st) {
     if (n_cap <= 0) return;
     count_launch();
+    // ceil(2^32 / n_gauss), 0 for n_gauss = 1 (the view of record r is r / n_gauss)
+    const uint32_t n_magic = n_gauss > 1 ? (uint32_t)(0xFFFFFFFFull / (uint64_t)n_gauss + 1ull) : 0u;
     k_emit<<<blocks_for(n_cap, kScanTile), kScanThreads, 0, st>>>(sorted_ids, block_offsets, n_dev, n_cap, ki,
-                                                                  splats, (uint32_t)n_gauss, cb, tile_keys,
+                                                                  splats, (uint32_t)n_gauss, n_magic, cb, tile_keys,
                                                                   tile_vals, K_dev, key_capacity, status);
 }
 

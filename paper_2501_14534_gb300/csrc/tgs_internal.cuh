@@ -134,27 +134,6 @@ __device__ __forceinline__ bool tile_keep(float mx, float my, float a, float b, 
     return q <= tau;
 }
 
-// Tiles of a splat record kept by the cull test; calls f(tx, ty) for each, row-major.
-template <class F>
-__device__ __forceinline__ int for_kept_tiles(const float4 &s0, const float4 &s1, const float4 &s2,
-                                              const float4 &s3, int B, F f) {
-    const uint32_t rx = __float_as_uint(s2.y), ry = __float_as_uint(s2.z);
-    const int ix0 = (int)(rx & 0xFFFFu), ix1 = (int)(rx >> 16);
-    const int iy0 = (int)(ry & 0xFFFFu), iy1 = (int)(ry >> 16);
-    int kept = 0;
-    for (int ty = iy0 / B; ty <= iy1 / B; ty++) {
-        const int y0 = max(ty * B, iy0), y1 = min(ty * B + B - 1, iy1);
-        for (int tx = ix0 / B; tx <= ix1 / B; tx++) {
-            const int x0 = max(tx * B, ix0), x1 = min(tx * B + B - 1, ix1);
-            if (tile_keep(s0.x, s0.y, s0.z, s0.w, s1.x, s3.x, s3.y, s3.z, x0, x1, y0, y1)) {
-                f(tx, ty);
-                kept++;
-            }
-        }
-    }
-    return kept;
-}
-
 // ---- launchers implemented in the .cu files --------------------------------------------
 
 // preprocess.cu
