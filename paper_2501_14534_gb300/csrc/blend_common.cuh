@@ -105,8 +105,9 @@ __device__ __forceinline__ void stage_splat(BlendSmem<NT> &sm, int slot,
 
 // Exponent of one fragment, with explicit roundings (no contraction choices left to the
 // compiler) so that every kernel computes the same bits.
-__device__ __forceinline__ float frag_q(float A, float Bq, float Cq, float dx, float dy) {
-    const float u = __fmaf_rn(A, dx, __fmul_rn(Bq, dy));
+// A thread's pixels share their column, so dx and A dx are computed once per splat (Adx).
+__device__ __forceinline__ float frag_q(float Adx, float Bq, float Cq, float dx, float dy) {
+    const float u = __fmaf_rn(Bq, dy, Adx);
     const float w = __fmul_rn(__fmul_rn(Cq, dy), dy);
     return __fmaf_rn(dx, u, w);
 }
@@ -199,14 +200,15 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
             const bool cover = (sm.cov[m] & P.wbit) != 0u;
             const float4 a = sm.a[m], b = sm.b[m];
             const float cbl = sm.c[m], qmin = sm.qmin[m];
+            const float dx = a.x - P.fx[0], Adx = __fmul_rn(a.z, dx);  // same column for all PPT
             bool fin = false;
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
                 if (S.done[k]) continue;
                 if (!cover && !pix_in(r, P.x[k], P.y[k])) continue;
                 if (COUNT) S.eval[k]++;
-                const float dx = a.x - P.fx[k], dy = a.y - P.fy[k];
-                const float q = frag_q(a.z, a.w, b.x, dx, dy);
+                const float dy = a.y - P.fy[k];
+                const float q = frag_q(Adx, a.w, b.x, dx, dy);
                 if (q > 0.f || q < qmin) continue;   // alpha < 1/255: skipped
                 const float alpha = fminf(kAlphaMax, __fmul_rn(b.y, ex2_approx(q)));
                 const float tT = __fmul_rn(S.T[k], __fsub_rn(1.f, alpha));
@@ -346,6 +348,7 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
             const bool cover = (sm.cov[m] & P.wbit) != 0u;
             const float4 a = sm.a[m], b = sm.b[m];
             const float cbl = sm.c[m], qmin = sm.qmin[m];
+            const float dx = a.x - P.fx[0], Adx = __fmul_rn(a.z, dx);  // same column for all PPT
             // per-warp sums over the pixels of u = dL/da G (for the unclamped fragments):
             // g[0] = sum u dx, g[1] = sum u dy, g[2] = sum u dx^2, g[3] = sum u dx dy,
             // g[4] = sum u dy^2, g[5] = sum u, g[6..8] = dL/d rgb; turned into the gradients
@@ -358,8 +361,8 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
             for (int k = 0; k < PPT; k++) {
                 if (pos > in.last[k]) continue;
                 if (!cover && !pix_in(r, P.x[k], P.y[k])) continue;
-                const float dx = a.x - P.fx[k], dy = a.y - P.fy[k];
-                const float q = frag_q(a.z, a.w, b.x, dx, dy);
+                const float dy = a.y - P.fy[k];
+                const float q = frag_q(Adx, a.w, b.x, dx, dy);
                 if (q > 0.f || q < qmin) continue;   // skipped in the forward too
                 const float G = ex2_approx(q);
                 const float x = __fmul_rn(b.y, G);
