@@ -30,13 +30,11 @@ template <int NT>
 struct BlendSmem {
     float4 a[NT];     // mean2d x, y; scaled conic A, B
     float4 b[NT];     // scaled conic C; opacity; r, g
-    float c[NT];      // b
     int4 rect[NT];    // inclusive pixel rect x_lo, x_hi, y_lo, y_hi
-    uint32_t id[NT];  // splat record index
     uint32_t hit[NT]; // bit w: the rect meets warp w's pixel block
     uint32_t vis[NT]; // bit w: in addition some point of (block x rect) may reach alpha >= 1/255
-    uint32_t cov[NT]; // bit w: the rect covers warp w's pixel block
-    float qmin[NT];   // q below this gives alpha < 1/255: -log2(255 o')
+    float4 d[NT];     // b; qmin = -log2(255 o') (q below it gives alpha < 1/255); cover bits
+                      // (bit w: the rect covers warp w's pixel block); splat record index
     int maxlast;
 };
 
@@ -76,17 +74,15 @@ __device__ __forceinline__ void stage_splat(BlendSmem<NT> &sm, int slot,
     const float4 s0 = __ldg(rp), s1 = __ldg(rp + 1), s2 = __ldg(rp + 2);
     sm.a[slot] = make_float4(s0.x, s0.y, __fmul_rn(-0.5f * kLog2e, s0.z), __fmul_rn(-kLog2e, s0.w));
     sm.b[slot] = make_float4(__fmul_rn(-0.5f * kLog2e, s1.x), s1.y, s1.z, s1.w);
-    sm.c[slot] = s2.x;
     // o' 2^q < 1/255  <=>  q < -log2(255 o'): the skip test before any exponential
-    sm.qmin[slot] = -log2f(__fmul_rn(255.f, s1.y));
+    const float qmin = -log2f(__fmul_rn(255.f, s1.y));
     const uint32_t rx = __float_as_uint(s2.y), ry = __float_as_uint(s2.z);
     const int4 r = make_int4((int)(rx & 0xFFFFu), (int)(rx >> 16), (int)(ry & 0xFFFFu), (int)(ry >> 16));
     sm.rect[slot] = r;
-    sm.id[slot] = id;
     uint32_t hit, cov;
     block_masks<TILE, PPT>(r.x, r.y, r.z, r.w, tx0, ty0, hit, cov);
     sm.hit[slot] = hit;
-    sm.cov[slot] = cov;
+    sm.d[slot] = make_float4(s2.x, qmin, __uint_as_float(cov), __uint_as_float(id));
     // warp blocks whose part of the rect stays below alpha = 1/255 everywhere (the cull test of
     // the keys, on the block): those warps skip the splat, whose fragments they would skip
     using L = BlendLayout<TILE, PPT>;
@@ -197,9 +193,9 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
             const int m = c0 + __ffs(bits) - 1;
             bits &= bits - 1u;
             const int4 r = sm.rect[m];
-            const bool cover = (sm.cov[m] & P.wbit) != 0u;
-            const float4 a = sm.a[m], b = sm.b[m];
-            const float cbl = sm.c[m], qmin = sm.qmin[m];
+            const float4 a = sm.a[m], b = sm.b[m], dd = sm.d[m];
+            const bool cover = (__float_as_uint(dd.z) & P.wbit) != 0u;
+            const float cbl = dd.x, qmin = dd.y;
             const float dx = a.x - P.fx[0], Adx = __fmul_rn(a.z, dx);  // same column for all PPT
             bool fin = false;
 #pragma unroll
@@ -345,9 +341,9 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
             bits &= bits - 1u;
             const int pos = top - m;
             const int4 r = sm.rect[m];
-            const bool cover = (sm.cov[m] & P.wbit) != 0u;
-            const float4 a = sm.a[m], b = sm.b[m];
-            const float cbl = sm.c[m], qmin = sm.qmin[m];
+            const float4 a = sm.a[m], b = sm.b[m], dd = sm.d[m];
+            const bool cover = (__float_as_uint(dd.z) & P.wbit) != 0u;
+            const float cbl = dd.x, qmin = dd.y;
             const float dx = a.x - P.fx[0], Adx = __fmul_rn(a.z, dx);  // same column for all PPT
             // per-warp sums over the pixels of u = dL/da G (for the unclamped fragments):
             // g[0] = sum u dx, g[1] = sum u dy, g[2] = sum u dx^2, g[3] = sum u dx dy,
@@ -391,7 +387,7 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
                 }
             }
             if (__ballot_sync(full, contrib) == 0u) continue;
-            float *dst = sgrads + 12 * (size_t)sm.id[m];
+            float *dst = sgrads + 12 * (size_t)__float_as_uint(dd.w);
             warp_transpose_reduce8(g, lane);
             const float gb = warp_sum(g[8]);
             if (MOMENTS) {
