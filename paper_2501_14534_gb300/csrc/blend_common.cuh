@@ -197,7 +197,6 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
             const bool cover = (__float_as_uint(dd.z) & P.wbit) != 0u;
             const float cbl = dd.x, qmin = dd.y;
             const float dx = a.x - P.fx[0], Adx = __fmul_rn(a.z, dx);  // same column for all PPT
-            bool fin = false;
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
                 if (S.done[k]) continue;
@@ -211,7 +210,6 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
                 if (tT < kTMin) {
                     S.done[k] = true;
                     S.exam[k] = pos0 + m + 1;
-                    fin = true;
                     continue;
                 }
                 if (COUNT) S.contrib[k]++;
@@ -222,16 +220,12 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
                 S.T[k] = tT;
                 S.last[k] = pos0 + m + 1;
             }
-            if (__any_sync(full, fin)) {
-                bool all = true;
-#pragma unroll
-                for (int k = 0; k < PPT; k++) all = all && S.done[k];
-                if (__all_sync(full, all)) {
-                    warp_done = true;
-                    break;
-                }
-            }
           }
+          // checked once per chunk: a warp whose pixels all stopped leaves the list
+          bool all = true;
+#pragma unroll
+          for (int k = 0; k < PPT; k++) all = all && S.done[k];
+          warp_done = __all_sync(full, all);
         }
     }
     const int len = (int)(rg.y - rg.x);
