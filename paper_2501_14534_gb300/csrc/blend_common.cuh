@@ -370,17 +370,19 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
                 const float dLda = fmaf(diff, T[k], -tbg[k] * inv);
                 acd[k] = fmaf(alpha, diff, acd[k]);   // now includes this fragment
                 if (x <= kAlphaMax) {
+                    // the pixels of a thread share dx: sum u, u dy, u dy^2 here and apply dx
+                    // once below (g[0] = dx sum u, g[2] = dx^2 sum u, g[3] = dx sum u dy)
                     const float u = dLda * G;
-                    const float ux = u * dx, uy = u * dy;
+                    const float uy = u * dy;
                     g[5] += u;
-                    g[0] += ux;
                     g[1] += uy;
-                    g[2] = fmaf(ux, dx, g[2]);
-                    g[3] = fmaf(ux, dy, g[3]);
                     g[4] = fmaf(uy, dy, g[4]);
                 }
             }
             if (__ballot_sync(full, contrib) == 0u) continue;
+            g[0] = g[5] * dx;
+            g[2] = g[0] * dx;
+            g[3] = g[1] * dx;
             float *dst = sgrads + 12 * (size_t)__float_as_uint(dd.w);
             warp_transpose_reduce8(g, lane);
             const float gb = warp_sum(g[8]);
