@@ -108,10 +108,6 @@ __device__ __forceinline__ float frag_q(float Adx, float Bq, float Cq, float dx,
     return __fmaf_rn(dx, u, w);
 }
 
-__device__ __forceinline__ bool pix_in(const int4 &r, int x, int y) {
-    return (unsigned)(x - r.x) <= (unsigned)(r.y - r.x) && (unsigned)(y - r.z) <= (unsigned)(r.w - r.z);
-}
-
 // Pixels of this thread in tile (tx, ty).
 template <int TILE, int PPT>
 struct TilePixels {
@@ -197,10 +193,11 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
             const bool cover = (__float_as_uint(dd.z) & P.wbit) != 0u;
             const float cbl = dd.x, qmin = dd.y;
             const float dx = a.x - P.fx[0], Adx = __fmul_rn(a.z, dx);  // same column for all PPT
+            const bool xin = cover || (unsigned)(P.x[0] - r.x) <= (unsigned)(r.y - r.x);
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
                 if (S.done[k]) continue;
-                if (!cover && !pix_in(r, P.x[k], P.y[k])) continue;
+                if (!cover && !(xin && (unsigned)(P.y[k] - r.z) <= (unsigned)(r.w - r.z))) continue;
                 if (COUNT) S.eval[k]++;
                 const float dy = a.y - P.fy[k];
                 const float q = frag_q(Adx, a.w, b.x, dx, dy);
@@ -339,6 +336,7 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
             const bool cover = (__float_as_uint(dd.z) & P.wbit) != 0u;
             const float cbl = dd.x, qmin = dd.y;
             const float dx = a.x - P.fx[0], Adx = __fmul_rn(a.z, dx);  // same column for all PPT
+            const bool xin = cover || (unsigned)(P.x[0] - r.x) <= (unsigned)(r.y - r.x);
             // per-warp sums over the pixels of u = dL/da G (for the unclamped fragments):
             // g[0] = sum u dx, g[1] = sum u dy, g[2] = sum u dx^2, g[3] = sum u dx dy,
             // g[4] = sum u dy^2, g[5] = sum u, g[6..8] = dL/d rgb; turned into the gradients
@@ -350,7 +348,7 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
                 if (pos > in.last[k]) continue;
-                if (!cover && !pix_in(r, P.x[k], P.y[k])) continue;
+                if (!cover && !(xin && (unsigned)(P.y[k] - r.z) <= (unsigned)(r.w - r.z))) continue;
                 const float dy = a.y - P.fy[k];
                 const float q = frag_q(Adx, a.w, b.x, dx, dy);
                 if (q > 0.f || q < qmin) continue;   // skipped in the forward too
