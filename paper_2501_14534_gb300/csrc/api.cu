@@ -34,7 +34,7 @@ struct tgs_ctx {
     int device = 0;
     // scratch arena
     Buf splats, radii, tt, dbits, pos, ck0, cv0, ck1, cv1, offsets, tk0, tv0, tk1, tv1, ranges,
-        hist, partials, sgrads, counts, status, pixstate, dimg, images, items, kmask;
+        hist, partials, sgrads, counts, status, pixstate, dimg, images, items, kmask, viskeys;
     uint32_t *h_counts = nullptr;   // pinned host copy of (visible, K)
     // binning kept from the last plain forward
     bool state_valid = false;
@@ -205,6 +205,7 @@ tgs_status ensure_keys(tgs_ctx *c, int64_t cap, int total_tiles, cudaStream_t st
     TGS_TRY(ensure(c->tk1, sizeof(uint32_t) * (size_t)cap, st));
     TGS_TRY(ensure(c->tv1, sizeof(uint32_t) * (size_t)cap, st));
     TGS_TRY(ensure(c->ranges, sizeof(uint2) * (size_t)std::max(total_tiles, 1), st));
+    TGS_TRY(ensure(c->viskeys, sizeof(uint16_t) * (size_t)cap, st));  // fused blend's per-key masks
     size_t h = radix_hist_needed(cap);
     TGS_TRY(ensure(c->hist, sizeof(uint32_t) * std::max(h, c->hist.bytes / sizeof(uint32_t)), st));
     size_t p = std::max(scan_partials_needed(cap), scan_partials_needed((int64_t)h));
@@ -392,7 +393,7 @@ void tgs_destroy(tgs_ctx *c) {
     Buf *bufs[] = {&c->splats, &c->radii, &c->tt, &c->dbits, &c->pos, &c->ck0, &c->cv0, &c->ck1,
                    &c->cv1, &c->offsets, &c->tk0, &c->tv0, &c->tk1, &c->tv1, &c->ranges, &c->hist,
                    &c->partials, &c->sgrads, &c->counts, &c->status, &c->pixstate, &c->dimg,
-                   &c->images, &c->items, &c->kmask};
+                   &c->images, &c->items, &c->kmask, &c->viskeys};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_counts) cudaFreeHost(c->h_counts);
@@ -722,7 +723,7 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
         TGS_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), st));
         mark(c, stage++, "fused_blend", st);
         launch_fused_l1(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), order, counter,
-                        cb, px, c->cfg.bg, as<float>(c->sgrads), loss_out, st);
+                        cb, px, c->cfg.bg, as<float>(c->sgrads), loss_out, as<uint16_t>(c->viskeys), st);
     }
     mark(c, stage++, "preprocess_backward", st);
     GradPtrs o = grad_ptrs(grads, stats, (flags & TGS_ACCUMULATE) ? 1 : 0);

@@ -66,7 +66,9 @@ __device__ __forceinline__ void block_masks(int xl, int xh, int yl, int yh, int 
     }
 }
 
-template <int TILE, int PPT, int NT>
+// With VIS the warps that may see alpha >= 1/255 are found by the cull test below; without,
+// the caller stores sm.vis itself.
+template <int TILE, int PPT, int NT, bool VIS = true>
 __device__ __forceinline__ void stage_splat(BlendSmem<NT> &sm, int slot,
                                             const float4 *__restrict__ splats, uint32_t id,
                                             int tx0, int ty0) {
@@ -85,6 +87,7 @@ __device__ __forceinline__ void stage_splat(BlendSmem<NT> &sm, int slot,
     sm.d[slot] = make_float4(s2.x, qmin, __uint_as_float(cov), __uint_as_float(id));
     // warp blocks whose part of the rect stays below alpha = 1/255 everywhere (the cull test of
     // the keys, on the block): those warps skip the splat, whose fragments they would skip
+    if (!VIS) return;
     using L = BlendLayout<TILE, PPT>;
     const float4 s3 = __ldg(rp + 3);
     uint32_t vis = hit, bits = hit;
@@ -151,11 +154,12 @@ struct FwdState {
 // Front-to-back blend of one tile's list [rg.x, rg.y). On return every pixel holds its
 // colour sum, transmittance, last contributor (1-based list position, 0 if none) and the
 // number of list entries it examined.
-template <int TILE, int PPT, bool COUNT = false>
+template <int TILE, int PPT, bool COUNT = false, bool KEEPVIS = false>
 __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
                                              const float4 *__restrict__ splats,
                                              const uint32_t *__restrict__ ids, uint2 rg,
-                                             const TilePixels<TILE, PPT> &P, FwdState<PPT> &S) {
+                                             const TilePixels<TILE, PPT> &P, FwdState<PPT> &S,
+                                             uint16_t *__restrict__ vis_out = nullptr) {
     constexpr int NT = TILE * TILE / PPT;
     const unsigned full = 0xffffffffu;
     const int t = threadIdx.x;
@@ -174,7 +178,10 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
         for (int k = 0; k < PPT; k++) mine = mine && S.done[k];
         if (__syncthreads_count(mine) == NT) break;
         const uint32_t j = base + t;
-        if (j < rg.y) stage_splat<TILE, PPT>(sm, t, splats, __ldg(ids + j), P.tx0, P.ty0);
+        if (j < rg.y) {
+            stage_splat<TILE, PPT>(sm, t, splats, __ldg(ids + j), P.tx0, P.ty0);
+            if (KEEPVIS) vis_out[j] = (uint16_t)sm.vis[t];  // read back by the backward's staging
+        }
         __syncthreads();
         if (__all_sync(full, mine)) continue;  // this warp is finished
         const int cnt = min((uint32_t)NT, rg.y - base);
@@ -287,13 +294,14 @@ struct BwdInput {
 // for the unclamped fragments, dx, dy = mean2d - pixel) -- then dL/d opacity = sum u and
 // dL/d rgb, and the consumer applies the splat's conic and opacity (see splat_grads in
 // preprocess.cu): that takes the per-fragment conversion out of the loop.
-template <int TILE, int PPT, bool MOMENTS = false>
+template <int TILE, int PPT, bool MOMENTS = false, bool KEEPVIS = false>
 __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
                                               const float4 *__restrict__ splats,
                                               const uint32_t *__restrict__ ids, uint2 rg,
                                               const TilePixels<TILE, PPT> &P, const BwdInput<PPT> &in,
                                               float bg0, float bg1, float bg2,
-                                              float *__restrict__ sgrads) {
+                                              float *__restrict__ sgrads,
+                                              const uint16_t *__restrict__ vis_in = nullptr) {
     constexpr int NT = TILE * TILE / PPT;
     const unsigned full = 0xffffffffu;
     const int t = threadIdx.x, lane = t & 31;
@@ -319,8 +327,10 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
         const uint32_t bstart = (bend - rg.x > (uint32_t)NT) ? bend - NT : rg.x;
         const int cnt = (int)(bend - bstart);
         __syncthreads();
-        if (t < cnt)  // slot t holds list position bend-1-t
-            stage_splat<TILE, PPT>(sm, t, splats, __ldg(ids + bend - 1 - t), P.tx0, P.ty0);
+        if (t < cnt) {  // slot t holds list position bend-1-t
+            stage_splat<TILE, PPT, NT, !KEEPVIS>(sm, t, splats, __ldg(ids + bend - 1 - t), P.tx0, P.ty0);
+            if (KEEPVIS) sm.vis[t] = vis_in[bend - 1 - t];  // as the forward's staging found it
+        }
         __syncthreads();
         const int top = (int)(bend - rg.x);   // 1-based position of slot 0
         const int m0 = max(0, top - wmax);    // positions beyond this warp's last contributors

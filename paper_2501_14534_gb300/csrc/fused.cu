@@ -38,9 +38,10 @@ k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
            const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, int n_items,
            int *__restrict__ counter, const __grid_constant__ CamBatch cb,
            const __grid_constant__ PixPtrs px, float bg0, float bg1, float bg2,
-           float *__restrict__ sgrads, float *__restrict__ loss) {
+           float *__restrict__ sgrads, float *__restrict__ loss, uint16_t *__restrict__ vis_keys) {
     constexpr int NT = TILE * TILE / PPT;
     constexpr int NW = NT / 32;
+    static_assert(NW <= 16, "the per-key warp masks are 16 bits");
     __shared__ BlendSmem<NT> sm;
     __shared__ int s_item;
     __shared__ float s_loss[NW];
@@ -59,7 +60,7 @@ k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
         P.init(lt % cam.gx, lt / cam.gx, cam.W, cam.H);
         const uint2 rg = ranges[gt];
         FwdState<PPT> S;
-        tile_forward<TILE, PPT>(sm, splats, ids, rg, P, S);
+        tile_forward<TILE, PPT, false, true>(sm, splats, ids, rg, P, S, vis_keys);
 
         // L1 loss: L = mean over views of mean over 3HW |C - target|; dL/dC = sign / (3HWV)
         const int HW = cam.W * cam.H;
@@ -91,7 +92,7 @@ k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
         }
         lsum = warp_sum(lsum);
         if (lane == 0) s_loss[w] = lsum;
-        tile_backward<TILE, PPT, true>(sm, splats, ids, rg, P, in, bg0, bg1, bg2, sgrads);
+        tile_backward<TILE, PPT, true, true>(sm, splats, ids, rg, P, in, bg0, bg1, bg2, sgrads, vis_keys);
         // s_loss was written before the barriers inside tile_backward
         if (t == 0 && loss) {
             float x = 0.f;
@@ -116,7 +117,7 @@ int fused_blocks_per_sm() {
 template <int TILE, int PPT>
 void fused_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const uint32_t *order,
                   int *counter, const CamBatch &cb, const PixPtrs &px, const float *bg, float *sgrads,
-                  float *loss, cudaStream_t st) {
+                  float *loss, uint16_t *vis_keys, cudaStream_t st) {
     static std::once_flag once;
     static int per_sm = 1, sms = 1;
     std::call_once(once, [] {
@@ -130,7 +131,7 @@ void fused_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges
     if (grid < 1) grid = 1;
     count_launch();
     k_fused_l1<TILE, PPT><<<grid, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, order, cb.total_tiles, counter,
-                                                              cb, px, bg[0], bg[1], bg[2], sgrads, loss);
+                                                              cb, px, bg[0], bg[1], bg[2], sgrads, loss, vis_keys);
 }
 
 }  // namespace
@@ -147,15 +148,15 @@ void build_item_order(const uint2 *ranges, int total_tiles, uint32_t *k0, uint32
 
 void launch_fused_l1(int tile, int ppt, const float4 *splats, const uint32_t *ids, const uint2 *ranges,
                      const uint32_t *order, int *counter, const CamBatch &cb, const PixPtrs &px,
-                     const float *bg, float *sgrads, float *loss, cudaStream_t st) {
+                     const float *bg, float *sgrads, float *loss, uint16_t *vis_keys, cudaStream_t st) {
     if (cb.total_tiles <= 0) return;
-    if (tile == 8 && ppt == 1) fused_launch<8, 1>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
-    else if (tile == 8 && ppt == 2) fused_launch<8, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
-    else if (tile == 16 && ppt == 1) fused_launch<16, 1>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
-    else if (tile == 16 && ppt == 2) fused_launch<16, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
-    else if (tile == 16 && ppt == 4) fused_launch<16, 4>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
-    else if (tile == 32 && ppt == 2) fused_launch<32, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
-    else if (tile == 32 && ppt == 4) fused_launch<32, 4>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, st);
+    if (tile == 8 && ppt == 1) fused_launch<8, 1>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
+    else if (tile == 8 && ppt == 2) fused_launch<8, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
+    else if (tile == 16 && ppt == 1) fused_launch<16, 1>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
+    else if (tile == 16 && ppt == 2) fused_launch<16, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
+    else if (tile == 16 && ppt == 4) fused_launch<16, 4>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
+    else if (tile == 32 && ppt == 2) fused_launch<32, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
+    else if (tile == 32 && ppt == 4) fused_launch<32, 4>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
 }
 
 }  // namespace tgs
