@@ -294,6 +294,13 @@ struct BwdInput {
 // for the unclamped fragments, dx, dy = mean2d - pixel) -- then dL/d opacity = sum u and
 // dL/d rgb, and the consumer applies the splat's conic and opacity (see splat_grads in
 // preprocess.cu): that takes the per-fragment conversion out of the loop.
+// At most this many contributing lanes: each adds its own sums with vector atomics instead of
+// a warp reduction. The atomics are fire-and-forget work for the L2; the reduction costs
+// ~45 issue slots of a kernel bound by issue. Swept on the benchmark step (fused kernel, ms):
+// never 6.70, 8 lanes 6.60, 16 6.48, 24 6.39, 28 6.37, 31 6.36, always 9.39 (same-address
+// contention of full warps).
+constexpr int kDirectLanes = 28;
+
 template <int TILE, int PPT, bool MOMENTS = false, bool KEEPVIS = false>
 __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
                                               const float4 *__restrict__ splats,
@@ -387,11 +394,21 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
                     g[4] = fmaf(uy, dy, g[4]);
                 }
             }
-            if (__ballot_sync(full, contrib) == 0u) continue;
+            const uint32_t cmask = __ballot_sync(full, contrib);
+            if (cmask == 0u) continue;
             g[0] = g[5] * dx;
             g[2] = g[0] * dx;
             g[3] = g[1] * dx;
             float *dst = sgrads + 12 * (size_t)__float_as_uint(dd.w);
+            if (MOMENTS && __popc(cmask) <= kDirectLanes) {
+                // few contributing lanes: each adds its own sums, no warp reduction
+                if (contrib) {
+                    atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(g[0], g[1], g[2], g[3]));
+                    atomicAdd(reinterpret_cast<float4 *>(dst + 4), make_float4(g[4], g[5], g[6], g[7]));
+                    atomicAdd(dst + 8, g[8]);
+                }
+                continue;
+            }
             warp_transpose_reduce8(g, lane);
             const float gb = warp_sum(g[8]);
             if (MOMENTS) {
