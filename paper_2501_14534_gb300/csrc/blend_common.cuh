@@ -400,9 +400,20 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
             g[2] = g[0] * dx;
             g[3] = g[1] * dx;
             float *dst = sgrads + 12 * (size_t)__float_as_uint(dd.w);
-            if (MOMENTS && __popc(cmask) <= kDirectLanes) {
-                // few contributing lanes: each adds its own sums, no warp reduction
+            if (__popc(cmask) <= kDirectLanes) {
+                // not nearly the whole warp: each contributing lane adds its own sums (converted
+                // to the splat gradients first unless MOMENTS), no warp reduction
                 if (contrib) {
+                    if (!MOMENTS) {
+                        const float o = b.y, on = o * kLn2;
+                        const float gmx = on * fmaf(2.f * a.z, g[0], a.w * g[1]);
+                        const float gmy = on * fmaf(2.f * b.x, g[1], a.w * g[0]);
+                        g[0] = gmx;
+                        g[1] = gmy;
+                        g[2] *= -0.5f * o;
+                        g[3] *= -o;
+                        g[4] *= -0.5f * o;
+                    }
                     atomicAdd(reinterpret_cast<float4 *>(dst), make_float4(g[0], g[1], g[2], g[3]));
                     atomicAdd(reinterpret_cast<float4 *>(dst + 4), make_float4(g[4], g[5], g[6], g[7]));
                     atomicAdd(dst + 8, g[8]);
