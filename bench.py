@@ -40,6 +40,25 @@ OPS_BWD = 51         # evaluation again + T recovery, colour-behind update, dL/d
                      # gradient terms: contributing pairs (skipped pairs not counted)
 # float32 lanes: 152 SMs x 128 lanes x 2.07 GHz max SM clock
 ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one fused-blend launch on the default workload at tile 32,
+# 2 px/thread, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; the command
+# is in profiles/k_fused_l1_300k_8x1280x832_tile32_ppt2.md). Reported only while the kernel's
+# sources are the ones measured (their sha256 below), else null.
+FUSED_TRAFFIC = {"bytes": 758516480 + 277465856, "tile": 32, "ppt": 2,
+                 "sources": ("fused.cu", "blend_common.cuh", "tgs_internal.cuh"),
+                 "sha256": "e8f85784e86b5ddd61026c2cb82862e4899e8620c31eda780e2e11de5103c29b"}
+
+
+def fused_traffic(cfg, n, views):
+    import hashlib
+    t = FUSED_TRAFFIC
+    if (cfg.tile, cfg.ppt, n, views) != (t["tile"], t["ppt"], N_GAUSS, N_VIEWS):
+        return None
+    h = hashlib.sha256()
+    for f in t["sources"]:
+        with open(os.path.join(ROOT, "paper_2501_14534_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return t["bytes"] if h.hexdigest() == t["sha256"] else None
 
 
 def parse():
@@ -390,7 +409,8 @@ def main():
     bound, units, peak, unit = work[dom]
     achieved = units / (stage_ms[dom] / 1000.0)
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak,
+                "traffic": fused_traffic(cfg, n, V) if dom == "fused_blend" else None,
                 "peak_source": (f"{peak_kind} hbm_gbs" if bound == "hbm" else
                                 "152 SMs x 128 FP32 lanes x 2.07 GHz")}
 
