@@ -21,7 +21,7 @@ constexpr int64_t kKeys = TGS_NOALLOC_MAX_KEYS;
 constexpr int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 constexpr int64_t round4(int64_t a) { return (a + 3) / 4 * 4; }  // 16-byte aligned regions
 constexpr int64_t kItems = kRec > kKeys ? kRec : kKeys;
-constexpr int64_t kHist = 256 * ceil_div(kItems, 2048) + 1;
+constexpr int64_t kHist = 256 * ceil_div(kItems, 2048) + 256;
 constexpr int64_t kPartials = ceil_div(kHist > kItems ? kHist : kItems, 2048) + 1;
 constexpr int64_t kBlockOffs = ceil_div(kRec, 2048) + 1;
 // word offsets inside the scratch array

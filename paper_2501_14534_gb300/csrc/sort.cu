@@ -300,6 +300,42 @@ k_radix_hist(const uint32_t *__restrict__ keys, const uint32_t *n_dev, int64_t n
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_h[threadIdx.x];
 }
 
+// Exclusive scan, in place, of each digit's row of per-block counts (the histogram is
+// digit-major: hist[d * nblocks + b]); row d's total goes to hist[256 * nblocks + d], which
+// k_digit_starts then turns into the digit's start. One CTA per digit.
+__global__ void __launch_bounds__(1024) k_hist_rows(uint32_t *__restrict__ hist, int64_t nblocks) {
+    __shared__ uint32_t s_warp[33];
+    const int d = blockIdx.x;
+    uint32_t *row = hist + (int64_t)d * nblocks;
+    uint32_t carry = 0u;
+    for (int64_t b0 = 0; b0 < nblocks; b0 += 4 * 1024) {
+        const int64_t i = b0 + 4 * (int64_t)threadIdx.x;
+        uint32_t v[4], sum = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            v[k] = i + k < nblocks ? row[i + k] : 0u;
+            sum += v[k];
+        }
+        uint32_t tot;
+        uint32_t e = block_excl_scan(sum, s_warp, &tot) + carry;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (i + k < nblocks) row[i + k] = e;
+            e += v[k];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) hist[(int64_t)kRadixBins * nblocks + d] = carry;
+}
+
+__global__ void __launch_bounds__(kRadixBins) k_digit_starts(uint32_t *__restrict__ hist, int64_t nblocks) {
+    __shared__ uint32_t s_warp[33];
+    uint32_t *tot = hist + (int64_t)kRadixBins * nblocks;
+    uint32_t all;
+    const uint32_t e = block_excl_scan(tot[threadIdx.x], s_warp, &all);
+    tot[threadIdx.x] = e;
+}
+
 // Stable scatter of one block of kRadixTile items. Warp w owns the items
 // [w * 32 * R, (w + 1) * 32 * R) of the block and ranks them on its own, R rounds of 32 lanes,
 // with per-warp digit counters (a warp multisplit: one ballot per digit bit finds the lanes
@@ -327,7 +363,8 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     const int cnt = (int)((n - base) < kRadixTile ? (n - base) : kRadixTile);
 #pragma unroll
     for (int q = 0; q < NW; q++) s_cnt[q][t] = 0u;
-    s_goff[t] = offsets[(int64_t)t * nblocks + blockIdx.x];
+    // global start of this block's run of digit t: the digit's start + earlier blocks' counts
+    s_goff[t] = offsets[(int64_t)kRadixBins * nblocks + t] + offsets[(int64_t)t * nblocks + blockIdx.x];
     __syncthreads();
     uint32_t kr[R], rk[R];
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -607,8 +644,8 @@ size_t scan_partials_needed(int64_t n_items) {
     return (size_t)((n_items + kScanTile - 1) / kScanTile) + 1;
 }
 
-size_t radix_hist_needed(int64_t n_items) {
-    return (size_t)kRadixBins * (size_t)((n_items + kRadixTile - 1) / kRadixTile) + 1;
+size_t radix_hist_needed(int64_t n_items) {  // per-block counts and the 256 digit totals
+    return (size_t)kRadixBins * (size_t)((n_items + kRadixTile - 1) / kRadixTile) + kRadixBins;
 }
 
 void scan_flags(const uint32_t *tiles_touched, int64_t n_cap, uint32_t *out, uint32_t *total,
@@ -633,7 +670,10 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint
         const uint32_t mask = (1u << bits) - 1u;
         count_launch();
         k_radix_hist<<<(unsigned)nb, kRadixThreads, 0, st>>>(keys, n_dev, n_cap, bit, mask, hist, nb);
-        scan_generic(LoadPlain{hist}, nullptr, (int64_t)kRadixBins * nb, hist, nullptr, partials, st);
+        count_launch();
+        k_hist_rows<<<kRadixBins, 1024, 0, st>>>(hist, nb);
+        count_launch();
+        k_digit_starts<<<1, kRadixBins, 0, st>>>(hist, nb);
         count_launch();
         k_radix_scatter<<<(unsigned)nb, kRadixThreads, 0, st>>>(keys, vals, n_dev, n_cap, bit, mask, hist,
                                                                 nb, keys_alt, vals_alt);
