@@ -232,16 +232,29 @@ __device__ __forceinline__ float3 sh_raw(const GaussState &s, const ShCoeffs &sh
     return c;
 }
 
+// One thread per Gaussian, looping over the views. A warp's 32 Gaussians have consecutive
+// records in every view, so the records (and the zeroed gradient records) go out through
+// shared memory as one contiguous run per warp: full-sector stores instead of four 16-byte
+// pieces per 64-byte record from each thread. Records of Gaussians not visible in a view
+// hold zeros; nothing reads them.
 __global__ void __launch_bounds__(128) k_preprocess(GaussPtrs g, const __grid_constant__ CamBatch cb,
                                                     float4 *__restrict__ splats,
                                                     int32_t *__restrict__ radii,
                                                     uint32_t *__restrict__ tiles_touched,
                                                     uint32_t *__restrict__ depth_bits,
                                                     float4 *__restrict__ zero_grads) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
+    constexpr int RW = kSplatWords / 4;  // float4 per record
+    __shared__ float4 s_rec[4][32 * RW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t n = g.n;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t wfirst = i0 - lane;
+    if (wfirst >= n) return;  // the whole warp is past the end
+    const bool inb = i0 < n;
+    const int64_t i = inb ? i0 : wfirst;
+    const int wn = (int)min((int64_t)32, n - wfirst);  // Gaussians of this warp
     GaussState s = load_state(g, i);
+    if (!inb) s.ok = false;
     ShCoeffs sh;
     if (s.ok) load_sh(g, i, s, sh);
     for (int v = 0; v < cb.V; v++) {
@@ -249,6 +262,9 @@ __global__ void __launch_bounds__(128) k_preprocess(GaussPtrs g, const __grid_co
         const int64_t r = (int64_t)v * n + i;
         int rad = 0;
         uint32_t touched = 0;
+        float4 rec[RW];
+#pragma unroll
+        for (int k = 0; k < RW; k++) rec[k] = make_float4(0.f, 0.f, 0.f, 0.f);
         ViewGeom vg;
         if (s.ok && view_geom(s, c, g.near_z, vg)) {
             float mid = 0.5f * (vg.c00 + vg.c11);
@@ -287,24 +303,36 @@ __global__ void __launch_bounds__(128) k_preprocess(GaussPtrs g, const __grid_co
                     const float tau = 2.f * logf(255.f * s.op / (1.f - kCullMargin));
                     // visible; the binning counts the tiles that pass the cull test
                     touched = 1u;
-                    splats[kSplatWords / 4 * r + 0] = make_float4(vg.mx, vg.my, vg.ca, vg.cb);
-                    splats[kSplatWords / 4 * r + 1] = make_float4(vg.cc, s.op, rgb.x, rgb.y);
-                    splats[kSplatWords / 4 * r + 2] =
-                        make_float4(rgb.z, __uint_as_float(rx), __uint_as_float(ry), vg.tz);
-                    splats[kSplatWords / 4 * r + 3] =
-                        make_float4(tau, __fdiv_rn(vg.cb, vg.cc), __fdiv_rn(vg.cb, vg.ca), 0.f);
+                    rec[0] = make_float4(vg.mx, vg.my, vg.ca, vg.cb);
+                    rec[1] = make_float4(vg.cc, s.op, rgb.x, rgb.y);
+                    rec[2] = make_float4(rgb.z, __uint_as_float(rx), __uint_as_float(ry), vg.tz);
+                    rec[3] = make_float4(tau, __fdiv_rn(vg.cb, vg.cc), __fdiv_rn(vg.cb, vg.ca), 0.f);
                     depth_bits[r] = __float_as_uint(vg.tz);
-                    if (zero_grads) {
-                        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                        zero_grads[3 * r] = z;
-                        zero_grads[3 * r + 1] = z;
-                        zero_grads[3 * r + 2] = z;
-                    }
                 }
             }
         }
-        radii[r] = rad;
-        tiles_touched[r] = touched;
+        if (inb) {
+            radii[r] = rad;
+            tiles_touched[r] = touched;
+        }
+#pragma unroll
+        for (int k = 0; k < RW; k++) s_rec[w][RW * lane + k] = rec[k];
+        __syncwarp();
+        const int64_t r0 = (int64_t)v * n + wfirst;  // the warp's first record in this view
+#pragma unroll
+        for (int k = 0; k < RW; k++) {
+            const int u = lane + 32 * k;
+            if (u < RW * wn) splats[RW * r0 + u] = s_rec[w][u];
+        }
+        if (zero_grads) {
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const int u = lane + 32 * k;
+                if (u < 3 * wn) zero_grads[3 * r0 + u] = z;
+            }
+        }
+        __syncwarp();
     }
 }
 
