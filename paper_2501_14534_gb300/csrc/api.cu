@@ -215,21 +215,20 @@ tgs_status ensure_keys(tgs_ctx *c, int64_t cap, int total_tiles, cudaStream_t st
 
 // Visibility compaction, depth sort and the key-count scan. Leaves the depth-sorted record
 // ids in *sorted and the key count in counts[1].
-// The per-record arrays free once the visible records are compacted hold the key counts of
-// the depth order.
+// The per-record arrays free during the binning hold the key counts of the depth order.
 KeyInfo key_info(tgs_ctx *c) {
-    return KeyInfo{as<uint32_t>(c->pos), as<uint2>(c->kmask), as<uint32_t>(c->dbits), as<uint32_t>(c->tt)};
+    return KeyInfo{as<uint32_t>(c->pos), as<uint2>(c->kmask), as<uint32_t>(c->ck0), as<uint32_t>(c->tt)};
 }
 
+// Depth sort of all records (depth keys from the preprocess; records not visible sort last)
+// and the key counts of the depth order. Leaves the sorted record ids in *sorted and the key
+// count in counts[1].
 void bin_front(tgs_ctx *c, int64_t nt, uint32_t **sorted, cudaStream_t st) {
     uint32_t *cnt = as<uint32_t>(c->counts);
-    scan_flags(as<uint32_t>(c->tt), nt, as<uint32_t>(c->pos), cnt + 0, as<uint32_t>(c->partials), st);
-    compact_visible(as<uint32_t>(c->tt), as<uint32_t>(c->dbits), as<uint32_t>(c->pos), nt,
-                    as<uint32_t>(c->ck0), as<uint32_t>(c->cv0), st);
-    uint32_t *k = as<uint32_t>(c->ck0), *v = as<uint32_t>(c->cv0);
-    radix_sort_pairs(k, v, as<uint32_t>(c->ck1), as<uint32_t>(c->cv1), cnt + 0, nt, 0, 32,
-                     as<uint32_t>(c->hist), as<uint32_t>(c->partials), st);
-    count_keys(v, cnt + 0, nt, as<float4>(c->splats), c->cfg.tile, key_info(c), as<uint32_t>(c->offsets),
+    uint32_t *k = as<uint32_t>(c->dbits), *v = as<uint32_t>(c->cv0);
+    radix_sort_pairs(k, v, as<uint32_t>(c->ck1), as<uint32_t>(c->cv1), nullptr, nt, 0, 32,
+                     as<uint32_t>(c->hist), as<uint32_t>(c->partials), st, true);
+    count_keys(v, k, nullptr, nt, as<float4>(c->splats), c->cfg.tile, key_info(c), as<uint32_t>(c->offsets),
                cnt + 1, st);
     *sorted = v;
 }
@@ -238,7 +237,7 @@ void bin_front(tgs_ctx *c, int64_t nt, uint32_t **sorted, cudaStream_t st) {
 uint32_t *bin_back(tgs_ctx *c, int64_t nt, int64_t n, const uint32_t *sorted, const CamBatch &cb,
                    int64_t cap, cudaStream_t st) {
     uint32_t *cnt = as<uint32_t>(c->counts);
-    emit_keys(sorted, as<uint32_t>(c->offsets), cnt + 0, nt, key_info(c), as<float4>(c->splats), n, cb,
+    emit_keys(sorted, as<uint32_t>(c->offsets), nullptr, nt, key_info(c), as<float4>(c->splats), n, cb,
               as<uint32_t>(c->tk0), as<uint32_t>(c->tv0), cnt + 1, cap, as<uint32_t>(c->status), st);
     uint32_t *k = as<uint32_t>(c->tk0), *v = as<uint32_t>(c->tv0);
     radix_sort_pairs(k, v, as<uint32_t>(c->tk1), as<uint32_t>(c->tv1), cnt + 1, cap, 0,
@@ -248,11 +247,10 @@ uint32_t *bin_back(tgs_ctx *c, int64_t nt, int64_t n, const uint32_t *sorted, co
     return v;
 }
 
-// Synchronous read of (visible, K) after bin_front.
-tgs_status read_counts(tgs_ctx *c, cudaStream_t st, int64_t *vis, int64_t *K) {
+// Synchronous read of the key count K after bin_front.
+tgs_status read_counts(tgs_ctx *c, cudaStream_t st, int64_t *K) {
     TGS_CHECK(cudaMemcpyAsync(c->h_counts, c->counts.p, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, st));
     TGS_CHECK(cudaStreamSynchronize(st));
-    if (vis) *vis = c->h_counts[0];
     if (K) *K = c->h_counts[1];
     return TGS_OK;
 }
@@ -264,7 +262,7 @@ tgs_status bin_plain(tgs_ctx *c, int64_t n, const CamBatch &cb, cudaStream_t st,
     uint32_t *sorted = nullptr;
     bin_front(c, nt, &sorted, st);
     int64_t K = 0;
-    TGS_TRY(read_counts(c, st, nullptr, &K));
+    TGS_TRY(read_counts(c, st, &K));
     if (K_out) *K_out = K;
     if (cap_limit >= 0 && K > cap_limit) return TGS_ERR_CAPACITY;
     TGS_TRY(ensure_keys(c, std::max<int64_t>(K, 1), cb.total_tiles, st));
@@ -644,7 +642,7 @@ tgs_status tgs_plan(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, 
     uint32_t *sorted = nullptr;
     bin_front(c, nt, &sorted, st);
     int64_t K = 0;
-    TGS_TRY(read_counts(c, st, nullptr, &K));
+    TGS_TRY(read_counts(c, st, &K));
     c->state_valid = false;
     int64_t cap = (int64_t)std::ceil(headroom * (double)std::max<int64_t>(K, 1));
     c->cfg.key_capacity = cap;

@@ -114,13 +114,11 @@ extern "C" tgs_status tgs_bin_noalloc(const float *splats, const int32_t *radii,
     if (cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * 8, st) != cudaSuccess) return TGS_ERR_CUDA;
 
     derive_touched(reinterpret_cast<const float4 *>(splats), radii, nt, tile, w + oTT, w + oDB, st);
-    scan_flags(w + oTT, nt, w + oPOS, cnt + 0, w + oPART, st);
-    compact_visible(w + oTT, w + oDB, w + oPOS, nt, w + oCK0, w + oCV0, st);
-    uint32_t *k = w + oCK0, *v = w + oCV0;
-    radix_sort_pairs(k, v, w + oCK1, w + oCV1, cnt + 0, nt, 0, 32, w + oHIST, w + oPART, st);
-    // the per-record arrays free after the compaction hold the key counts of the depth order
-    const KeyInfo ki{w + oPOS, reinterpret_cast<uint2 *>(w + oKM), w + oDB, w + oTT};
-    count_keys(v, cnt + 0, nt, reinterpret_cast<const float4 *>(splats), tile, ki, w + oOFF, cnt + 1, st);
+    uint32_t *k = w + oDB, *v = w + oCV0;
+    radix_sort_pairs(k, v, w + oCK1, w + oCV1, nullptr, nt, 0, 32, w + oHIST, w + oPART, st, true);
+    // the per-record arrays free during the binning hold the key counts of the depth order
+    const KeyInfo ki{w + oPOS, reinterpret_cast<uint2 *>(w + oKM), w + oCK0, w + oTT};
+    count_keys(v, k, nullptr, nt, reinterpret_cast<const float4 *>(splats), tile, ki, w + oOFF, cnt + 1, st);
 
     uint32_t hK = 0;
     if (cudaMemcpyAsync(&hK, cnt + 1, sizeof hK, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -134,7 +132,7 @@ extern "C" tgs_status tgs_bin_noalloc(const float *splats, const int32_t *radii,
     if (K > capacity) return TGS_ERR_CAPACITY;
 
     const int64_t cap = K > 0 ? K : 1;
-    emit_keys(v, w + oOFF, cnt + 0, nt, ki, reinterpret_cast<const float4 *>(splats), n, cb, w + oTK0, w + oTV0,
+    emit_keys(v, w + oOFF, nullptr, nt, ki, reinterpret_cast<const float4 *>(splats), n, cb, w + oTK0, w + oTV0,
               cnt + 1, cap, status, st);
     uint32_t *tk = w + oTK0, *tv = w + oTV0;
     radix_sort_pairs(tk, tv, w + oTK1, w + oTV1, cnt + 1, cap, 0, bits_for_tiles(cb.total_tiles),

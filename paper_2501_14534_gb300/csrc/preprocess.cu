@@ -307,13 +307,14 @@ __global__ void __launch_bounds__(128) k_preprocess(GaussPtrs g, const __grid_co
                     rec[1] = make_float4(vg.cc, s.op, rgb.x, rgb.y);
                     rec[2] = make_float4(rgb.z, __uint_as_float(rx), __uint_as_float(ry), vg.tz);
                     rec[3] = make_float4(tau, __fdiv_rn(vg.cb, vg.cc), __fdiv_rn(vg.cb, vg.ca), 0.f);
-                    depth_bits[r] = __float_as_uint(vg.tz);
                 }
             }
         }
         if (inb) {
             radii[r] = rad;
             tiles_touched[r] = touched;
+            // depth key of every record for the depth sort; the ones not visible sort last
+            depth_bits[r] = touched ? __float_as_uint(rec[2].w) : kNoDepth;
         }
 #pragma unroll
         for (int k = 0; k < RW; k++) s_rec[w][RW * lane + k] = rec[k];

@@ -1,9 +1,10 @@
-// Binning: visibility compaction, depth sort, key emission, tile sort and tile ranges.
+// Binning: depth sort, key count, key emission, tile sort and tile ranges.
 //
 // The keys are (global tile id, float32 bits of depth) with the Gaussian record index as
-// value, stably sorted. Instead of one 64-bit sort over all keys, the visible (view,
-// Gaussian) records are first sorted by depth bits (a 32-bit sort over V*N items), the keys
-// are emitted in that order, and a stable sort on the tile id alone follows. A stable sort
+// value, stably sorted. Instead of one 64-bit sort over all keys, the (view, Gaussian)
+// records are first sorted by depth bits (a 32-bit sort over V*N items; records not visible
+// carry the key 0xffffffff and sort after every visible one), the keys are emitted in that
+// order, and a stable sort on the tile id alone follows. A stable sort
 // by tile of a sequence already ordered by (depth bits, record index) yields exactly the
 // order of a stable sort of the full keys emitted in record order: equal tiles keep depth
 // order, equal depths keep record order.
@@ -32,10 +33,6 @@ __device__ __forceinline__ int64_t count_of(const uint32_t *n_dev, int64_t n_cap
 struct LoadPlain {
     const uint32_t *p;
     __device__ __forceinline__ uint32_t operator()(int64_t i) const { return p[i]; }
-};
-struct LoadVisible {
-    const uint32_t *tt;
-    __device__ __forceinline__ uint32_t operator()(int64_t i) const { return tt[i] > 0u ? 1u : 0u; }
 };
 
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x, int lane) {
@@ -136,17 +133,6 @@ void scan_generic(Load ld, const uint32_t *n_dev, int64_t n_cap, uint32_t *out, 
     }
 }
 
-// Compacts the visible records (depth bits as key, record index as value) for the depth sort.
-__global__ void k_compact(const uint32_t *__restrict__ tt, const uint32_t *__restrict__ db,
-                          const uint32_t *__restrict__ pos, int64_t n, uint32_t *__restrict__ keys,
-                          uint32_t *__restrict__ vals) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || tt[i] == 0u) return;
-    const uint32_t p = pos[i];
-    keys[p] = db[i];
-    vals[p] = (uint32_t)i;
-}
-
 // a = q d + r for a < 2^22, d < 2^22, with one float multiply by rcp = 1/d (rounded): the
 // product is then within 1/d of a/d from below, so the truncated quotient is q or q - 1
 __device__ __forceinline__ void divmod_small(uint32_t a, uint32_t d, float rcp, uint32_t &q, uint32_t &r) {
@@ -173,8 +159,9 @@ __device__ __forceinline__ void divmod_small(uint32_t a, uint32_t d, float rcp, 
 // lanes idle. A lane finds the record of pair p by binary search over the exclusive prefix
 // sums of the rect sizes (held one per lane and read with shuffles).
 __global__ void __launch_bounds__(kScanThreads)
-k_count_keys(const uint32_t *__restrict__ sorted_ids, const uint32_t *n_dev, int64_t n_cap,
-             const float4 *__restrict__ splats, int B, KeyInfo ki, uint32_t *__restrict__ partials) {
+k_count_keys(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ sorted_keys,
+             const uint32_t *n_dev, int64_t n_cap, const float4 *__restrict__ splats, int B, KeyInfo ki,
+             uint32_t *__restrict__ partials) {
     constexpr int NW = kScanThreads / 32;
     __shared__ float4 s_g[NW][32];     // mean2d x, y; conic a, b
     __shared__ float4 s_h[NW][32];     // conic c; tau; b / c; b / a
@@ -195,7 +182,8 @@ k_count_keys(const uint32_t *__restrict__ sorted_ids, const uint32_t *n_dev, int
 #pragma unroll 1
     for (int q = 0; q < kScanItems; q++) {
         const int64_t j = base + (int64_t)(w * kScanItems + q) * 32 + lane;
-        const bool valid = j < n;
+        // records not visible carry the key 0xffffffff and sort last
+        const bool valid = j < n && sorted_keys[j] != kNoDepth;
         uint32_t ntiles = 0u, rx = 0u, ry = 0u;
         int tx0 = 0, ty0 = 0, nx = 1;
         if (valid) {
@@ -378,7 +366,8 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
 #pragma unroll
     for (int r = 0; r < R; r++) {
         const int j = wbase + r * 32 + lane;
-        if (j < cnt) s_vin[j] = vals_in[base + j];
+        // no input values: the items' own positions (the first pass of a sort of indices)
+        if (j < cnt) s_vin[j] = vals_in ? vals_in[base + j] : (uint32_t)(base + j);
     }
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -627,13 +616,10 @@ __global__ void k_derive_touched(const float4 *__restrict__ splats, const int32_
                                  int64_t n, int B, uint32_t *__restrict__ tt, uint32_t *__restrict__ db) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    if (radii[i] <= 0) {
-        tt[i] = 0u;
-        return;
-    }
-    // visibility flag; k_compact replaces it by the number of kept tiles
-    tt[i] = 1u;
-    db[i] = __float_as_uint(splats[(size_t)kSplatWords / 4 * i + 2].w);
+    const bool vis = radii[i] > 0;
+    tt[i] = vis ? 1u : 0u;
+    // depth key of every record; the ones not visible sort last
+    db[i] = vis ? __float_as_uint(splats[(size_t)kSplatWords / 4 * i + 2].w) : kNoDepth;
 }
 
 inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -648,23 +634,13 @@ size_t radix_hist_needed(int64_t n_items) {  // per-block counts and the 256 dig
     return (size_t)kRadixBins * (size_t)((n_items + kRadixTile - 1) / kRadixTile) + kRadixBins;
 }
 
-void scan_flags(const uint32_t *tiles_touched, int64_t n_cap, uint32_t *out, uint32_t *total,
-                uint32_t *partials, cudaStream_t st) {
-    scan_generic(LoadVisible{tiles_touched}, nullptr, n_cap, out, total, partials, st);
-}
-
-void compact_visible(const uint32_t *tiles_touched, const uint32_t *depth_bits, const uint32_t *pos,
-                     int64_t n_cap, uint32_t *keys, uint32_t *vals, cudaStream_t st) {
-    if (n_cap <= 0) return;
-    count_launch();
-    k_compact<<<blocks_for(n_cap, 256), 256, 0, st>>>(tiles_touched, depth_bits, pos, n_cap, keys, vals);
-}
-
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       const uint32_t *n_dev, int64_t n_cap, int begin_bit, int end_bit,
-                      uint32_t *hist, uint32_t *partials, cudaStream_t st) {
+                      uint32_t *hist, uint32_t *partials, cudaStream_t st, bool index_vals) {
+    (void)partials;
     const int64_t nb = (n_cap + kRadixTile - 1) / kRadixTile;
     if (nb == 0) return;
+    bool first = true;
     for (int bit = begin_bit; bit < end_bit; bit += 8) {
         const int bits = (end_bit - bit) < 8 ? (end_bit - bit) : 8;
         const uint32_t mask = (1u << bits) - 1u;
@@ -675,8 +651,10 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint
         count_launch();
         k_digit_starts<<<1, kRadixBins, 0, st>>>(hist, nb);
         count_launch();
-        k_radix_scatter<<<(unsigned)nb, kRadixThreads, 0, st>>>(keys, vals, n_dev, n_cap, bit, mask, hist,
-                                                                nb, keys_alt, vals_alt);
+        k_radix_scatter<<<(unsigned)nb, kRadixThreads, 0, st>>>(keys, (first && index_vals) ? nullptr : vals,
+                                                                n_dev, n_cap, bit, mask, hist, nb, keys_alt,
+                                                                vals_alt);
+        first = false;
         uint32_t *tk = keys, *tv = vals;
         keys = keys_alt;
         vals = vals_alt;
@@ -685,15 +663,17 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint
     }
 }
 
-void count_keys(const uint32_t *sorted_ids, const uint32_t *n_dev, int64_t n_cap, const float4 *splats,
-                int tile, const KeyInfo &ki, uint32_t *block_offsets, uint32_t *total, cudaStream_t st) {
+void count_keys(const uint32_t *sorted_ids, const uint32_t *sorted_keys, const uint32_t *n_dev, int64_t n_cap,
+                const float4 *splats, int tile, const KeyInfo &ki, uint32_t *block_offsets, uint32_t *total,
+                cudaStream_t st) {
     const int64_t nb = (n_cap + kScanTile - 1) / kScanTile;
     if (nb == 0) {
         if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
         return;
     }
     count_launch();
-    k_count_keys<<<(unsigned)nb, kScanThreads, 0, st>>>(sorted_ids, n_dev, n_cap, splats, tile, ki, block_offsets);
+    k_count_keys<<<(unsigned)nb, kScanThreads, 0, st>>>(sorted_ids, sorted_keys, n_dev, n_cap, splats, tile, ki,
+                                                        block_offsets);
     count_launch();
     k_scan_partials<<<1, 1024, 0, st>>>(block_offsets, nb, total);
 }

@@ -72,6 +72,7 @@ extern thread_local int64_t g_launches;
 inline void count_launch(int k = 1) { g_launches += k; }
 
 // Device status word bits.
+constexpr uint32_t kNoDepth = 0xffffffffu;  // depth key of a record that is not visible
 constexpr uint32_t kStatusCapacity = 1u;
 constexpr uint32_t kStatusTimeout = 2u;
 
@@ -153,15 +154,12 @@ struct SortScratch {
 };
 size_t scan_partials_needed(int64_t n_items);
 size_t radix_hist_needed(int64_t n_items);
-// out[i] = exclusive prefix of in_fn(i) for i < *n_dev; *total = sum. n_cap bounds the grid.
-void scan_flags(const uint32_t *tiles_touched, int64_t n_cap, uint32_t *out, uint32_t *total,
-                uint32_t *partials, cudaStream_t st);
-// Visible records -> (depth bits, record index) pairs at pos[i], for the depth sort.
-void compact_visible(const uint32_t *tiles_touched, const uint32_t *depth_bits, const uint32_t *pos,
-                     int64_t n_cap, uint32_t *keys, uint32_t *vals, cudaStream_t st);
+// Stable LSD sort of (keys, vals) on bits [begin_bit, end_bit); on return keys/vals point to
+// the sorted arrays (one of the two buffer pairs). index_vals: the input values are the items'
+// positions (vals is then only written).
 void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint32_t *vals_alt,
                       const uint32_t *n_dev, int64_t n_cap, int begin_bit, int end_bit,
-                      uint32_t *hist, uint32_t *partials, cudaStream_t st);
+                      uint32_t *hist, uint32_t *partials, cudaStream_t st, bool index_vals = false);
 // Per depth-sorted record (arrays of n_cap, in depth order): number of kept tiles, kept-tile
 // mask (rects of at most 64 tiles), packed pixel rect x and y.
 struct KeyInfo {
@@ -172,8 +170,9 @@ struct KeyInfo {
 // Culls the rect tiles of each depth-sorted record and counts its keys (KeyInfo); per block of
 // 2048 records the exclusive start of its keys (block_offsets, scan_partials_needed(n_cap)
 // words) and the total in *total.
-void count_keys(const uint32_t *sorted_ids, const uint32_t *n_dev, int64_t n_cap, const float4 *splats,
-                int tile, const KeyInfo &ki, uint32_t *block_offsets, uint32_t *total, cudaStream_t st);
+void count_keys(const uint32_t *sorted_ids, const uint32_t *sorted_keys, const uint32_t *n_dev, int64_t n_cap,
+                const float4 *splats, int tile, const KeyInfo &ki, uint32_t *block_offsets, uint32_t *total,
+                cudaStream_t st);
 void emit_keys(const uint32_t *sorted_ids, const uint32_t *block_offsets, const uint32_t *n_dev,
                int64_t n_cap, const KeyInfo &ki, const float4 *splats, int64_t n_gauss, const CamBatch &cb,
                uint32_t *tile_keys, uint32_t *tile_vals, const uint32_t *K_dev, int64_t key_capacity,
