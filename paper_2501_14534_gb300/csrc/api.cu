@@ -466,7 +466,7 @@ tgs_status tgs_preprocess(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *
     const int64_t nt = g->n * V;
     TGS_TRY(ensure(c->tt, sizeof(uint32_t) * (size_t)nt, st));
     TGS_TRY(ensure(c->dbits, sizeof(uint32_t) * (size_t)nt, st));
-    launch_preprocess(gp, cb, reinterpret_cast<float4 *>(splats), radii, as<uint32_t>(c->tt),
+    launch_preprocess(gp, cb, reinterpret_cast<float4 *>(splats), radii, nullptr,
                       as<uint32_t>(c->dbits), nullptr, st);
     return last_error();
 }
@@ -483,7 +483,7 @@ tgs_status tgs_bin(tgs_ctx *c, const float *splats, const int32_t *radii, int64_
     // records come from the caller: copy them in and derive tiles touched and depth bits
     TGS_CHECK(cudaMemcpyAsync(c->splats.p, splats, sizeof(float) * kSplatWords * (size_t)nt, cudaMemcpyDeviceToDevice, st));
     TGS_CHECK(cudaMemcpyAsync(c->radii.p, radii, sizeof(int32_t) * (size_t)nt, cudaMemcpyDeviceToDevice, st));
-    derive_touched(as<float4>(c->splats), as<int32_t>(c->radii), nt, c->cfg.tile, as<uint32_t>(c->tt),
+    derive_touched(as<float4>(c->splats), as<int32_t>(c->radii), nt, c->cfg.tile, nullptr,
                    as<uint32_t>(c->dbits), st);
     int64_t K = 0;
     uint32_t *ids = nullptr;
@@ -559,7 +559,7 @@ static tgs_status plain_bin_view(tgs_ctx *c, const tgs_gaussians *g, const Gauss
                                  const tgs_camera *cam, CamBatch &cb, cudaStream_t st, uint32_t **ids) {
     TGS_TRY(make_batch(c->cfg, cam, 1, cb));
     TGS_TRY(ensure_records(c, g->n, st));
-    launch_preprocess(gp, cb, as<float4>(c->splats), as<int32_t>(c->radii), as<uint32_t>(c->tt),
+    launch_preprocess(gp, cb, as<float4>(c->splats), as<int32_t>(c->radii), nullptr,
                       as<uint32_t>(c->dbits), nullptr, st);
     TGS_TRY(bin_plain(c, g->n, cb, st, nullptr, -1, ids));
     c->state_valid = true;
@@ -637,7 +637,7 @@ tgs_status tgs_plan(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, 
     TGS_TRY(make_gauss(c->cfg, g, gp));
     const int64_t nt = g->n * V;
     TGS_TRY(ensure_records(c, nt, st));
-    launch_preprocess(gp, cb, as<float4>(c->splats), as<int32_t>(c->radii), as<uint32_t>(c->tt),
+    launch_preprocess(gp, cb, as<float4>(c->splats), as<int32_t>(c->radii), nullptr,
                       as<uint32_t>(c->dbits), nullptr, st);
     uint32_t *sorted = nullptr;
     bin_front(c, nt, &sorted, st);
@@ -687,7 +687,7 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
     }
     const int64_t launches0 = g_launches;
     mark(c, 0, "preprocess", st);
-    launch_preprocess(gp, cb, as<float4>(c->splats), as<int32_t>(c->radii), as<uint32_t>(c->tt),
+    launch_preprocess(gp, cb, as<float4>(c->splats), as<int32_t>(c->radii), nullptr,
                       as<uint32_t>(c->dbits), as<float>(c->sgrads), st);
     mark(c, 1, "bin", st);
     uint32_t *sorted = nullptr;

@@ -113,7 +113,7 @@ extern "C" tgs_status tgs_bin_noalloc(const float *splats, const int32_t *radii,
     // the array keeps the previous call's contents: clear the words read before written
     if (cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * 8, st) != cudaSuccess) return TGS_ERR_CUDA;
 
-    derive_touched(reinterpret_cast<const float4 *>(splats), radii, nt, tile, w + oTT, w + oDB, st);
+    derive_touched(reinterpret_cast<const float4 *>(splats), radii, nt, tile, nullptr, w + oDB, st);
     uint32_t *k = w + oDB, *v = w + oCV0;
     radix_sort_pairs(k, v, w + oCK1, w + oCV1, nullptr, nt, 0, 32, w + oHIST, w + oPART, st, true);
     // the per-record arrays free during the binning hold the key counts of the depth order

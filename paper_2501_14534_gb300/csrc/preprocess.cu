@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(128) k_preprocess(GaussPtrs g, const __grid_co
         }
         if (inb) {
             radii[r] = rad;
-            tiles_touched[r] = touched;
+            if (tiles_touched) tiles_touched[r] = touched;
             // depth key of every record for the depth sort; the ones not visible sort last
             depth_bits[r] = touched ? __float_as_uint(rec[2].w) : kNoDepth;
         }

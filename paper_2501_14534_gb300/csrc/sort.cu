@@ -617,7 +617,7 @@ __global__ void k_derive_touched(const float4 *__restrict__ splats, const int32_
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const bool vis = radii[i] > 0;
-    tt[i] = vis ? 1u : 0u;
+    if (tt) tt[i] = vis ? 1u : 0u;
     // depth key of every record; the ones not visible sort last
     db[i] = vis ? __float_as_uint(splats[(size_t)kSplatWords / 4 * i + 2].w) : kNoDepth;
 }

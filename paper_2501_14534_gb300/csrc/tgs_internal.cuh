@@ -137,7 +137,8 @@ __device__ __forceinline__ bool tile_keep(float mx, float my, float a, float b, 
 
 // ---- launchers implemented in the .cu files --------------------------------------------
 
-// preprocess.cu
+// preprocess.cu. depth_bits [n*V]: the depth key of every record (kNoDepth where not
+// visible); tiles_touched (may be null): visibility flags.
 void launch_preprocess(const GaussPtrs &g, const CamBatch &cb, float4 *splats, int32_t *radii,
                        uint32_t *tiles_touched, uint32_t *depth_bits, float *zero_grads,
                        cudaStream_t st);
@@ -179,6 +180,8 @@ void emit_keys(const uint32_t *sorted_ids, const uint32_t *block_offsets, const 
                uint32_t *status, cudaStream_t st);
 void find_ranges(const uint32_t *tile_keys, const uint32_t *K_dev, int64_t key_capacity,
                  uint2 *ranges, int total_tiles, cudaStream_t st);
+// Depth keys (and, if tiles_touched is not null, visibility flags) of splat records given
+// from outside, as the preprocess writes them.
 void derive_touched(const float4 *splats, const int32_t *radii, int64_t n_rec, int tile,
                     uint32_t *tiles_touched, uint32_t *depth_bits, cudaStream_t st);
 void make_full_keys(const uint32_t *tile_keys, const uint32_t *tile_vals, const float4 *splats,
