@@ -481,71 +481,42 @@ __device__ __forceinline__ void splat_grads(const float4 &ga, const float4 &gb, 
     }
 }
 
-// Two forms of the same backward, chosen by the number of views of the launch: with many
-// views the 45 dL/d sh_rest accumulators and the coefficients stay in registers (fewer
-// instructions per view); with one or two views they live in shared memory and cache (fewer
-// registers, higher occupancy).
-__global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_reg(GaussPtrs g, const __grid_constant__ CamBatch cb,
+// The backward as two kernels, so that each holds fewer registers and more
+// warps fit on an SM: the colour part (SH coefficient gradients, band-mask gradients and the
+// colour term of dL/dmu through the view direction) and then the geometry part (EWA backward,
+// opacity, scales, rotation, volume mask, statistics), which adds its dL/dmu to the colour
+// kernel's.
+__global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_colour(GaussPtrs g, const __grid_constant__ CamBatch cb,
                                                         const float4 *__restrict__ sgrads,
                                                         const int32_t *__restrict__ radii,
-                                                        GradPtrs out, int no_sh_rest, int moments) {
+                                                        GradPtrs out, int no_sh_rest) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const int64_t n = g.n;
+    const float *rec = reinterpret_cast<const float *>(sgrads);  // 12 floats per (view, Gaussian)
     GaussState s = load_state(g, i);
     ShCoeffs sh;
     float3 g_mu = make_float3(0.f, 0.f, 0.f);
-    float g_S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (full-matrix entries)
-    float g_op = 0.f;
     float3 g_f[16];
 #pragma unroll
     for (int k = 0; k < 16; k++) g_f[k] = make_float3(0.f, 0.f, 0.f);
     float g_band[4] = {0.f, 0.f, 0.f, 0.f};
-    float st_acc = 0.f;
-    int st_cnt = 0, st_max = 0;
-    bool any = false;
+    uint64_t vis = 0;
     if (s.ok) {
-        // the views where the Gaussian is visible, read up front (independent loads), and the
-        // splat gradients of the next view prefetched while this one is processed. The loop
-        // runs over all views in step across the warp, so that the camera read is the same
-        // for every lane (one broadcast, not one constant-cache access per distinct view).
-        uint64_t vis = 0;
 #pragma unroll 8
-        for (int v = 0; v < cb.V; v++) {
-            const int rad = radii[(int64_t)v * n + i];
-            if (rad > 0) {
-                vis |= 1ull << v;
-                st_max = max(st_max, rad);
-            }
-        }
+        for (int v = 0; v < cb.V; v++)
+            if (radii[(int64_t)v * n + i] > 0) vis |= 1ull << v;
         load_sh(g, i, s, sh);
-        float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na, nc = na;
-        if (vis & 1ull) {
-            na = sgrads[3 * i];
-            nb = sgrads[3 * i + 1];
-            nc = sgrads[3 * i + 2];
-        }
+        float3 nrgb = make_float3(0.f, 0.f, 0.f);
+        if (vis & 1ull) nrgb = make_float3(rec[12 * i + 6], rec[12 * i + 7], rec[12 * i + 8]);
         for (int v = 0; v < cb.V; v++) {
-            const float4 ga = na, gb4 = nb, gc4 = nc;
+            const float3 g_rgb = nrgb;
             if (v + 1 < cb.V && ((vis >> (v + 1)) & 1ull)) {
-                const int64_t rn = (int64_t)(v + 1) * n + i;
-                na = sgrads[3 * rn];
-                nb = sgrads[3 * rn + 1];
-                nc = sgrads[3 * rn + 2];
+                const int64_t rn = 12 * ((int64_t)(v + 1) * n + i);
+                nrgb = make_float3(rec[rn + 6], rec[rn + 7], rec[rn + 8]);
             }
             if (!((vis >> v) & 1ull)) continue;
             const DevCam &c = cb.c[v];
-            ViewGeom vg;
-            if (!view_geom(s, c, g.near_z, vg)) continue;  // cannot happen when rad > 0
-            any = true;
-            float gmx, gmy, gca, gcb, gcc;
-            splat_grads(ga, gb4, moments, s.op, vg.ca, vg.cb, vg.cc, gmx, gmy, gca, gcb, gcc);
-            g_op += gb4.y;
-            float3 g_rgb = make_float3(gb4.z, gb4.w, gc4.x);
-            st_acc += sqrtf(gmx * gmx + gmy * gmy);
-            st_cnt += 1;
-
-            // ---- colour ----
             float dx = s.mu.x - c.campos[0], dy = s.mu.y - c.campos[1], dz = s.mu.z - c.campos[2];
             float dn = sqrtf(dx * dx + dy * dy + dz * dz);
             float inv = 1.f / dn;
@@ -575,28 +546,20 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_reg(GaussPtrs g,
             g_mu.x += (g_dir.x - x * dd) * inv;
             g_mu.y += (g_dir.y - y * dd) * inv;
             g_mu.z += (g_dir.z - z * dd) * inv;
-
-            view_geom_backward(s, c, vg, gmx, gmy, gca, gcb, gcc, g_S, g_mu);
         }
     }
     const int acc = out.accumulate;
-    // ---- statistics (always accumulated) ----
-    if (st_cnt > 0) {
-        if (out.stat_accum) out.stat_accum[i] += st_acc;
-        if (out.stat_count) out.stat_count[i] += st_cnt;
-        if (out.stat_maxr) out.stat_maxr[i] = max(out.stat_maxr[i], st_max);
-    }
-    float g_q[4] = {0.f, 0.f, 0.f, 0.f}, g_ls[3] = {0.f, 0.f, 0.f}, g_o = 0.f, g_m = 0.f;
     float g_shm[3] = {0.f, 0.f, 0.f};
-    if (any) gauss_backward(g, i, s, g_S, g_op, g_band, g_q, g_ls, g_o, g_m, g_shm);
+    if (vis && g.shmask)
 #pragma unroll
-    for (int k = 0; k < 3; k++) {
-        out_write(out.means, 3 * i + k, k == 0 ? g_mu.x : (k == 1 ? g_mu.y : g_mu.z), acc);
-        out_write(out.log_scales, 3 * i + k, g_ls[k], acc);
-    }
-#pragma unroll
-    for (int k = 0; k < 4; k++) out_write(out.quats, 4 * i + k, g_q[k], acc);
-    out_write(out.opac, i, g_o, acc);
+        for (int l = 1; l <= 3; l++) {
+            if (l > s.deg) continue;
+            const float sm = sigmoidf_(g.shmask[3 * i + l - 1]);
+            g_shm[l - 1] = g_band[l] * sm * (1.f - sm);
+        }
+    out_write(out.means, 3 * i + 0, g_mu.x, acc);
+    out_write(out.means, 3 * i + 1, g_mu.y, acc);
+    out_write(out.means, 3 * i + 2, g_mu.z, acc);
     out_write(out.sh_dc, 3 * i + 0, g_f[0].x, acc);
     out_write(out.sh_dc, 3 * i + 1, g_f[0].y, acc);
     out_write(out.sh_dc, 3 * i + 2, g_f[0].z, acc);
@@ -608,94 +571,56 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_reg(GaussPtrs g,
             out_write(out.sh_rest, 45 * i + 3 * (k - 1) + 2, g_f[k].z, acc);
         }
     }
-    out_write(out.mask, i, g_m, acc);
 #pragma unroll
     for (int l = 0; l < 3; l++) out_write(out.shmask, 3 * i + l, g_shm[l], acc);
 }
 
-
-__global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_smem(GaussPtrs g, const __grid_constant__ CamBatch cb,
-                                                        const float4 *__restrict__ sgrads,
-                                                        const int32_t *__restrict__ radii,
-                                                        GradPtrs out, int no_sh_rest, int moments) {
-    // dL/d sh_rest accumulates in shared memory ([coefficient][thread]: no bank conflicts)
-    // and the SH coefficients are re-read per view from cache, to keep registers for the rest
-    __shared__ float s_gf[45][kBwdThreads];
+__global__ void __launch_bounds__(kBwdThreads, 5) k_preprocess_bwd_geom(GaussPtrs g, const __grid_constant__ CamBatch cb,
+                                                      const float4 *__restrict__ sgrads,
+                                                      const int32_t *__restrict__ radii,
+                                                      GradPtrs out, int moments) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
-    const int tid = threadIdx.x;
     const int64_t n = g.n;
     GaussState s = load_state(g, i);
     float3 g_mu = make_float3(0.f, 0.f, 0.f);
     float g_S[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // dL/dSigma (full-matrix entries)
     float g_op = 0.f;
-    float3 g_dc = make_float3(0.f, 0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < 45; j++) s_gf[j][tid] = 0.f;
-    const float *fr = g.sh_rest ? g.sh_rest + 45 * i : nullptr;
-    float g_band[4] = {0.f, 0.f, 0.f, 0.f};
     float st_acc = 0.f;
     int st_cnt = 0, st_max = 0;
     bool any = false;
     if (s.ok) {
-        const float3 dc = make_float3(g.sh_dc[3 * i], g.sh_dc[3 * i + 1], g.sh_dc[3 * i + 2]);
+        uint64_t vis = 0;
+#pragma unroll 8
         for (int v = 0; v < cb.V; v++) {
-            const int64_t r = (int64_t)v * n + i;
-            const int rad = radii[r];
-            if (rad <= 0) continue;
+            const int rad = radii[(int64_t)v * n + i];
+            if (rad > 0) {
+                vis |= 1ull << v;
+                st_max = max(st_max, rad);
+            }
+        }
+        float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
+        if (vis & 1ull) {
+            na = sgrads[3 * i];
+            nb = sgrads[3 * i + 1];
+        }
+        for (int v = 0; v < cb.V; v++) {
+            const float4 ga = na, gb4 = nb;
+            if (v + 1 < cb.V && ((vis >> (v + 1)) & 1ull)) {
+                const int64_t rn = (int64_t)(v + 1) * n + i;
+                na = sgrads[3 * rn];
+                nb = sgrads[3 * rn + 1];
+            }
+            if (!((vis >> v) & 1ull)) continue;
             const DevCam &c = cb.c[v];
             ViewGeom vg;
             if (!view_geom(s, c, g.near_z, vg)) continue;  // cannot happen when rad > 0
             any = true;
-            float4 ga = sgrads[3 * r], gb4 = sgrads[3 * r + 1], gc4 = sgrads[3 * r + 2];
             float gmx, gmy, gca, gcb, gcc;
             splat_grads(ga, gb4, moments, s.op, vg.ca, vg.cb, vg.cc, gmx, gmy, gca, gcb, gcc);
             g_op += gb4.y;
-            float3 g_rgb = make_float3(gb4.z, gb4.w, gc4.x);
             st_acc += sqrtf(gmx * gmx + gmy * gmy);
             st_cnt += 1;
-            st_max = max(st_max, rad);
-
-            // ---- colour ----
-            float dx = s.mu.x - c.campos[0], dy = s.mu.y - c.campos[1], dz = s.mu.z - c.campos[2];
-            float dn = sqrtf(dx * dx + dy * dy + dz * dz);
-            float inv = 1.f / dn;
-            float x = dx * inv, y = dy * inv, z = dz * inv;
-            float Y[16];
-            sh_basis(x, y, z, Y);
-            float3 raw = make_float3(0.5f + Y[0] * dc.x, 0.5f + Y[0] * dc.y, 0.5f + Y[0] * dc.z);
-#pragma unroll
-            for (int k = 1; k < 16; k++) {
-                if (!fr || !s.band[band_of(k)]) continue;
-                raw.x += Y[k] * __ldg(fr + 3 * (k - 1));
-                raw.y += Y[k] * __ldg(fr + 3 * (k - 1) + 1);
-                raw.z += Y[k] * __ldg(fr + 3 * (k - 1) + 2);
-            }
-            float3 gr = make_float3(raw.x < 0.f ? 0.f : g_rgb.x, raw.y < 0.f ? 0.f : g_rgb.y,
-                                    raw.z < 0.f ? 0.f : g_rgb.z);
-            g_dc.x += Y[0] * gr.x;
-            g_dc.y += Y[0] * gr.y;
-            g_dc.z += Y[0] * gr.z;
-            float3 g_dir = make_float3(0.f, 0.f, 0.f);
-#pragma unroll
-            for (int k = 1; k < 16; k++) {
-                const int l = band_of(k);
-                if (!fr || l > s.deg) continue;
-                const float f0 = __ldg(fr + 3 * (k - 1)), f1 = __ldg(fr + 3 * (k - 1) + 1),
-                            f2 = __ldg(fr + 3 * (k - 1) + 2);
-                const float sk = f0 * gr.x + f1 * gr.y + f2 * gr.z;
-                g_band[l] += Y[k] * sk;
-                if (!s.band[l]) continue;
-                s_gf[3 * (k - 1)][tid] += Y[k] * gr.x;
-                s_gf[3 * (k - 1) + 1][tid] += Y[k] * gr.y;
-                s_gf[3 * (k - 1) + 2][tid] += Y[k] * gr.z;
-                sh_basis_grad_add(k, x, y, z, sk, g_dir);
-            }
-            float dd = g_dir.x * x + g_dir.y * y + g_dir.z * z;
-            g_mu.x += (g_dir.x - x * dd) * inv;
-            g_mu.y += (g_dir.y - y * dd) * inv;
-            g_mu.z += (g_dir.z - z * dd) * inv;
-
             view_geom_backward(s, c, vg, gmx, gmy, gca, gcb, gcc, g_S, g_mu);
         }
     }
@@ -708,25 +633,17 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_smem(GaussPtrs g
     }
     float g_q[4] = {0.f, 0.f, 0.f, 0.f}, g_ls[3] = {0.f, 0.f, 0.f}, g_o = 0.f, g_m = 0.f;
     float g_shm[3] = {0.f, 0.f, 0.f};
-    if (any) gauss_backward(g, i, s, g_S, g_op, g_band, g_q, g_ls, g_o, g_m, g_shm);
+    const float no_band[4] = {0.f, 0.f, 0.f, 0.f};  // the colour kernel did the band masks
+    if (any) gauss_backward(g, i, s, g_S, g_op, no_band, g_q, g_ls, g_o, g_m, g_shm);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        out_write(out.means, 3 * i + k, k == 0 ? g_mu.x : (k == 1 ? g_mu.y : g_mu.z), acc);
+        if (out.means) out.means[3 * i + k] += (k == 0 ? g_mu.x : (k == 1 ? g_mu.y : g_mu.z));
         out_write(out.log_scales, 3 * i + k, g_ls[k], acc);
     }
 #pragma unroll
     for (int k = 0; k < 4; k++) out_write(out.quats, 4 * i + k, g_q[k], acc);
     out_write(out.opac, i, g_o, acc);
-    out_write(out.sh_dc, 3 * i + 0, g_dc.x, acc);
-    out_write(out.sh_dc, 3 * i + 1, g_dc.y, acc);
-    out_write(out.sh_dc, 3 * i + 2, g_dc.z, acc);
-    if (out.sh_rest && !no_sh_rest) {
-#pragma unroll
-        for (int j = 0; j < 45; j++) out_write(out.sh_rest, 45 * i + j, s_gf[j][tid], acc);
-    }
     out_write(out.mask, i, g_m, acc);
-#pragma unroll
-    for (int l = 0; l < 3; l++) out_write(out.shmask, 3 * i + l, g_shm[l], acc);
 }
 
 }  // namespace
@@ -749,10 +666,9 @@ void launch_preprocess_backward(const GaussPtrs &g, const CamBatch &cb, const fl
     const int bs = kBwdThreads;
     const int64_t grid = (g.n + bs - 1) / bs;
     count_launch();
-    if (cb.V <= 2)
-        k_preprocess_bwd_smem<<<(unsigned)grid, bs, 0, st>>>(g, cb, sgrads, radii, out, no_sh_rest, moments);
-    else
-        k_preprocess_bwd_reg<<<(unsigned)grid, bs, 0, st>>>(g, cb, sgrads, radii, out, no_sh_rest, moments);
+    k_preprocess_bwd_colour<<<(unsigned)grid, bs, 0, st>>>(g, cb, sgrads, radii, out, no_sh_rest);
+    count_launch();
+    k_preprocess_bwd_geom<<<(unsigned)grid, bs, 0, st>>>(g, cb, sgrads, radii, out, moments);
 }
 
 }  // namespace tgs
