@@ -675,7 +675,8 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
     size_t off = 0;
     for (int v = 0; v < V; v++) {
         const size_t hw = (size_t)cams[v].width * cams[v].height;
-        outs[v].image = images && images[v] ? images[v] : imgbuf + 3 * off;
+        // the fused step needs no image of its own: it writes one only where the caller asks
+        outs[v].image = images && images[v] ? images[v] : ((flags & TGS_UNFUSED) ? imgbuf + 3 * off : nullptr);
         outs[v].T_final = Tf + off;
         outs[v].last = last + off;
         outs[v].n_examined = nullptr;
