@@ -6,7 +6,7 @@ no code with the CUDA library.
 
 Functions follow the paper's notation: Eq. 1 (EWA projection to G'), Eq. 2 (front-to-back
 blending), the straight-through volume mask and the straight-through SH-band masks (Eq.
-sh-masks). ``tgs_oracle.c`` states the conventions the paper inherits from 3DGS.
+sh-masks), and the significance score of Eq. significance-score (ray hits, opacity, volume). ``tgs_oracle.c`` states the conventions the paper inherits from 3DGS.
 """
 from __future__ import annotations
 
@@ -92,6 +92,8 @@ def _declare(L):
                                           _dp, _i32p, _i32p]
     L.orc_l1.argtypes = [C.c_int64, _dp, _dp, C.c_double, _dp]
     L.orc_l1.restype = C.c_double
+    L.orc_hits.argtypes = [C.c_int64, C.POINTER(_Splats), C.c_int, C.c_int, C.c_int, C.c_int,
+                           C.c_int, _u8p, _u32p, _u32p, C.POINTER(C.c_int64)]
 
 
 def _ptr(a, t=_dp):
@@ -293,6 +295,59 @@ def render(scene, cam, st: Settings, brute=False, nthreads=1, margins=False):
     out = blend(sp, cam.width, cam.height, st.tile, st.bg, brute=brute, nthreads=nthreads,
                 margins=margins, depth_margin=margins)
     out["splats"] = sp
+    return out
+
+
+def hits(splats, W, H, tile=16, brute=False, nthreads=1, tile_mask=None, lists=None):
+    """Ray hits of one view for Eq. significance-score: per Gaussian, the number of pixels
+    whose blend (Eq. 2) blends it (alpha >= 1/255, before the pixel's stop). int64 [n]."""
+    n = splats["radius"].shape[0]
+    out = np.zeros(max(n, 1), np.int64)
+    tm = _mask(tile_mask)
+    lv, lr, _keep = _lists(lists)
+    lib().orc_hits(n, C.byref(_splats_struct(splats)), W, H, tile, int(brute), nthreads,
+                   _ptr(tm, _u8p), lv, lr, out.ctypes.data_as(C.POINTER(C.c_int64)))
+    return out[:n]
+
+
+def volume_mask(scene, st: Settings):
+    """The hard volume mask M of each Gaussian: float32(mask logit) > float32(logit(eps))."""
+    n = np.shape(scene["means"])[0]
+    m = scene.get("mask_logits")
+    if m is None:
+        return np.ones(n)
+    tau = np.float32(np.log(st.eps_mask / (1.0 - st.eps_mask)))
+    return (np.asarray(m, np.float32) > tau).astype(np.float64)
+
+
+def significance(scene, st: Settings, hit_count, quantile=0.9):
+    """Significance score of Eq. significance-score, GS_j = hits_j * alpha_j * gamma(Sigma_j):
+    hits_j from ``hits`` summed over the views, alpha_j the Gaussian's opacity o'_j = M
+    sigmoid(o_j) and gamma its volume s_x s_y s_z (masked scales M exp(l)) divided by the
+    volume at rank floor(quantile (n - 1)) of all n volumes sorted ascending, capped at 1 (1
+    where that volume is 0). Float64."""
+    n = np.shape(scene["means"])[0]
+    M = volume_mask(scene, st)
+    o = np.asarray(scene["opacity_logits"], np.float64).reshape(n)
+    opac = M / (1.0 + np.exp(-o))
+    ls = np.asarray(scene["log_scales"], np.float64).reshape(n, 3)
+    vol = M * np.exp(ls[:, 0]) * np.exp(ls[:, 1]) * np.exp(ls[:, 2])
+    if n == 0:
+        return np.zeros(0)
+    vq = np.sort(vol)[int(np.floor(quantile * (n - 1)))]
+    gamma = np.minimum(vol / vq, 1.0) if vq > 0 else np.ones(n)
+    return np.asarray(hit_count, np.float64) * opac * gamma
+
+
+def prune_select(scores, fraction):
+    """The Gaussians a pruning round removes: the floor(fraction n) lowest scores, equal
+    scores by lower index first. bool [n]."""
+    scores = np.asarray(scores)
+    n = scores.shape[0]
+    k = int(np.floor(fraction * n))
+    order = np.lexsort((np.arange(n), scores))
+    out = np.zeros(n, bool)
+    out[order[:k]] = True
     return out
 
 

@@ -613,6 +613,7 @@ typedef struct {
     /* backward */
     const double *dL_dimg;
     double *acc; /* [nthreads][n][9] */
+    int64_t *hits; /* [nthreads][n]: fragments blended per Gaussian (significance score) */
     int nthreads;
 } blend_job;
 
@@ -744,8 +745,9 @@ static void *blend_worker(void *p) {
             if (l > maxlen) maxlen = l;
         }
     frag_t *frags = NULL;
-    if (J->dL_dimg) frags = (frag_t *)malloc(sizeof(frag_t) * (size_t)(maxlen > 0 ? maxlen : 1));
+    if (J->dL_dimg || J->hits) frags = (frag_t *)malloc(sizeof(frag_t) * (size_t)(maxlen > 0 ? maxlen : 1));
     double *acc = J->acc ? J->acc + (int64_t)a->tid * J->n * 9 : NULL;
+    int64_t *hits = J->hits ? J->hits + (int64_t)a->tid * J->n : NULL;
     for (int t = a->tid; t < ntiles; t += J->nthreads) {
         if (J->tile_mask && !J->tile_mask[t]) continue;
         int tx = t % J->gx, ty = t / J->gx;
@@ -774,6 +776,8 @@ static void *blend_worker(void *p) {
                 if (J->n_examined) J->n_examined[pix] = ex;
                 if (J->n_eval) J->n_eval[pix] = ev;
                 if (J->margin) J->margin[pix] = mg;
+                if (hits)
+                    for (int f = 0; f < ncf; f++) hits[frags[f].id]++;
                 if (J->dL_dimg) {
                     double d[3];
                     for (int ch = 0; ch < 3; ch++)
@@ -951,6 +955,33 @@ int orc_blend_backward(int64_t n, const orc_splats *S, int W, int H, int tile, c
     for (int t = 0; t < J.nthreads; t++)
         for (int64_t i = 0; i < 9 * n; i++) g9[i] += J.acc[(int64_t)t * 9 * n + i];
     free(J.acc);
+    return 0;
+}
+
+/* Ray hits of Eq. significance-score for one view: per Gaussian, the number of pixels whose
+   forward blend (Eq. 2) blends it, i.e. the indicator 1(G(X_j), r_i) summed over the
+   view's rays, read as "fragment j contributes to pixel i" (alpha >= 1/255, before the
+   pixel's stop). Adds into hits [n]. */
+int orc_hits(int64_t n, const orc_splats *S, int W, int H, int tile, int brute, int nthreads,
+             const uint8_t *tile_mask, const uint32_t *list_vals, const uint32_t *list_ranges,
+             int64_t *hits) {
+    blend_job J;
+    memset(&J, 0, sizeof J);
+    J.tile_mask = tile_mask;
+    J.vals = list_vals;
+    J.ranges = list_ranges;
+    J.S = S;
+    J.n = n;
+    J.W = W;
+    J.H = H;
+    J.tile = tile;
+    J.brute = brute;
+    J.nthreads = nthreads < 1 ? 1 : nthreads;
+    J.hits = (int64_t *)calloc((size_t)J.nthreads * (size_t)(n > 0 ? n : 1), sizeof(int64_t));
+    run_blend(&J);
+    for (int t = 0; t < J.nthreads; t++)
+        for (int64_t i = 0; i < n; i++) hits[i] += J.hits[(int64_t)t * n + i];
+    free(J.hits);
     return 0;
 }
 

@@ -693,3 +693,103 @@ def test_tile_cull_drops_only_tiles_without_a_visible_pixel(tile):
     cul = oracle.blend(sp, 90, 70, tile, lists=(v_cul, r_cul))
     for k in ("image", "T_final", "n_contrib"):
         assert np.array_equal(full[k], cul[k]), k
+
+
+# ---------------------------------------------------------------------------------------
+# significance score (Eq. significance-score)
+# ---------------------------------------------------------------------------------------
+
+def python_hits(sp, W, H):
+    """Ray hits by a plain per-pixel loop over all Gaussians in (depth bits, index) order,
+    written here from Eq. 2 without the oracle's tile lists: a pixel blends a Gaussian when it
+    is inside its box, the exponent is <= 0, alpha = min(0.99, o G) >= 1/255 and the
+    transmittance stays >= 1e-4."""
+    n = sp["radius"].shape[0]
+    vis = [i for i in range(n) if sp["radius"][i] > 0]
+    db = np.asarray(sp["depth"], np.float32).view(np.uint32)
+    order = sorted(vis, key=lambda i: (int(db[i]), i))
+    hits = np.zeros(n, np.int64)
+    for py in range(H):
+        for px in range(W):
+            T = 1.0
+            for g in order:
+                x0, x1, y0, y1 = sp["rect"][g]
+                if not (x0 <= px <= x1 and y0 <= py <= y1):
+                    continue
+                dx, dy = sp["mean2d"][g][0] - px, sp["mean2d"][g][1] - py
+                a, b, c = sp["conic"][g]
+                power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+                if power > 0.0:
+                    continue
+                alpha = min(0.99, sp["opacity"][g] * math.exp(power))
+                if alpha < 1.0 / 255.0:
+                    continue
+                if T * (1.0 - alpha) < 1e-4:
+                    break
+                hits[g] += 1
+                T *= 1.0 - alpha
+    return hits
+
+
+def test_hits_equal_a_plain_per_pixel_loop():
+    scene = tiny_scene(60, 9)
+    cam = tiny_cam(24, 20)
+    st = oracle.Settings(tile=8, eps_mask=0.5, eps_sh=0.5)
+    sp = oracle.preprocess(scene, cam, st)
+    ref = python_hits(sp, cam.width, cam.height)
+    for tile in (8, 16):
+        np.testing.assert_array_equal(oracle.hits(sp, cam.width, cam.height, tile=tile), ref)
+    np.testing.assert_array_equal(oracle.hits(sp, cam.width, cam.height, brute=True, nthreads=3), ref)
+    assert ref.sum() > 0 and (ref > 0).sum() > 3
+
+
+def test_hits_of_one_gaussian_closed_form():
+    # one isotropic Gaussian: alpha <= 0.99 never stops a pixel, so its hits are the pixels
+    # of its box where alpha >= 1/255 (the closed-form alpha image above)
+    W, H, f, z, sigma, o_logit = 64, 48, 100.0, 4.0, 0.05, 0.3
+    scene = one_gaussian((0.0, 0.0, 0.0), [math.log(sigma)] * 3, o_logit, (0.3, 0.2, 0.1))
+    cam = direct_camera(z, W, H, f)
+    st = oracle.Settings(tile=16)
+    sp = oracle.preprocess(scene, cam, st)
+    *_, a, _dx, _dy, _o, _c = single_closed_form(W, H, f, z, sigma, o_logit, (0.3, 0.2, 0.1))
+    assert oracle.hits(sp, W, H)[0] == int((a > 0.0).sum()) > 0
+    # masked out: no hits and no score
+    masked = one_gaussian((0.0, 0.0, 0.0), [math.log(sigma)] * 3, o_logit, (0.3, 0.2, 0.1), mask=-3.0)
+    st_m = oracle.Settings(tile=16, eps_mask=0.5)
+    spm = oracle.preprocess(masked, cam, st_m)
+    hm = oracle.hits(spm, W, H)
+    assert hm[0] == 0 and oracle.significance(masked, st_m, hm)[0] == 0.0
+
+
+def test_significance_closed_form():
+    # four Gaussians with volumes 1, 2, 4, 8 (log-scales summing to log v), opacity logits
+    # 0 (o = 1/2) except the last (logit log 3: o = 3/4); the 0.9 quantile of 4 volumes is the
+    # one at rank floor(0.9 * 3) = 2, i.e. 4: gamma = 1/4, 1/2, 1, 1
+    vols = [1.0, 2.0, 4.0, 8.0]
+    scene = dict(means=np.zeros((4, 3)),
+                 log_scales=np.array([[math.log(v), 0.0, 0.0] for v in vols]),
+                 quats=np.tile([1.0, 0.0, 0.0, 0.0], (4, 1)),
+                 opacity_logits=np.array([0.0, 0.0, 0.0, math.log(3.0)]),
+                 sh_dc=np.zeros((4, 3)), sh_rest=None, mask_logits=None, sh_mask_logits=None,
+                 sh_degree=None, deg_max=0)
+    hits = np.array([10, 0, 3, 7])
+    got = oracle.significance(scene, oracle.Settings(), hits)
+    np.testing.assert_allclose(got, [10 * 0.5 * 0.25, 0.0, 3 * 0.5 * 1.0, 7 * 0.75 * 1.0], rtol=1e-14)
+    # a masked Gaussian has opacity and volume 0; the quantile is taken over all n volumes
+    scene["mask_logits"] = np.array([5.0, 5.0, -5.0, 5.0])
+    got = oracle.significance(scene, oracle.Settings(eps_mask=0.5), hits)
+    # volumes 1, 2, 0, 8 -> sorted 0, 1, 2, 8 -> rank 2: 2 -> gamma 1/2, 1, 0, 1
+    np.testing.assert_allclose(got, [10 * 0.5 * 0.5, 0.0, 0.0, 7 * 0.75], rtol=1e-14)
+
+
+def test_prune_selection_rule():
+    s = np.array([3.0, 1.0, 1.0, 2.0, 0.5])
+    np.testing.assert_array_equal(oracle.prune_select(s, 0.5), [False, True, False, False, True])
+    np.testing.assert_array_equal(oracle.prune_select(s, 0.6), [False, True, True, False, True])
+    assert not oracle.prune_select(s, 0.0).any() and oracle.prune_select(s, 1.0).all()
+    rng = np.random.default_rng(3)
+    x = rng.integers(0, 20, 500).astype(float)          # many ties
+    sel = oracle.prune_select(x, 0.37)
+    k = int(math.floor(0.37 * 500))
+    ranked = sorted(range(500), key=lambda i: (x[i], i))  # the rule, by plain sorting
+    assert set(np.flatnonzero(sel)) == set(ranked[:k])
