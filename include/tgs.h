@@ -151,6 +151,9 @@ typedef struct {
     float *grad_norm_accum; /* [n] += |dL/d mean2d|_2 (pixels) per view where visible, or NULL */
     int32_t *vis_count;     /* [n] += 1 per view where visible, or NULL */
     int32_t *max_radius;    /* [n] = max(max_radius, radius), or NULL */
+    uint32_t *hit_count;    /* [n] += pixels whose forward blend blends the Gaussian, or NULL: the
+                               ray hits of the significance score (Eq. significance-score);
+                               counted by the batched step when not NULL */
 } tgs_stats;
 
 /* --- context ------------------------------------------------------------------------ */
@@ -268,6 +271,29 @@ tgs_status tgs_bin_noalloc(const float *splats, const int32_t *radii, int64_t n,
                            const tgs_camera *cams, int32_t V, int32_t tile, uint32_t *sorted_ids,
                            uint64_t *sorted_keys, uint32_t *ranges, int64_t capacity,
                            int64_t *K_out, tgs_stream stream);
+
+/* --- significance pruning (Eq. significance-score) ---------------------------------- */
+
+/* Ray hits of the significance score: renders the V views (forward only, nothing else
+   written) and adds to hit_count [n] (device, uint32) the number of pixels of each view
+   whose blend (Eq. 2) blends the Gaussian -- alpha >= 1/255 and before the pixel's stop.
+   Same decisions as tgs_forward. Errors: TGS_ERR_INVALID_ARG for a null pointer or V <= 0. */
+tgs_status tgs_count_hits(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                          uint32_t *hit_count, tgs_stream stream);
+/* Significance score of each Gaussian, scores [n] (device float):
+   GS_j = hits_j * alpha_j * gamma_j, with hits_j = hit_count[j] summed over the training
+   views, alpha_j = M_j sigmoid(o_j) the opacity the blend uses and gamma_j = min(V_j / V_q, 1)
+   the volume V_j = s_x s_y s_z (masked scales M exp(l)) relative to V_q, the volume at rank
+   floor(quantile * (n - 1)) of all n volumes in ascending order (gamma = 1 where V_q = 0).
+   quantile in [0, 1] (the paper: the 90% largest, 0.9). Uses the context's mask threshold.
+   Asynchronous; TGS_ERR_INVALID_ARG for a null pointer or a quantile outside [0, 1]. */
+tgs_status tgs_significance(tgs_ctx *ctx, const tgs_gaussians *g, const uint32_t *hit_count,
+                            double quantile, float *scores, tgs_stream stream);
+/* The Gaussians a pruning round removes: prune [n] (device bytes) = 1 for the
+   floor(fraction * n) lowest scores (equal scores: lower index first), 0 for the others.
+   scores [n] device float, non-negative. fraction in [0, 1]. Asynchronous. */
+tgs_status tgs_prune_select(tgs_ctx *ctx, const float *scores, int64_t n, double fraction,
+                            uint8_t *prune, tgs_stream stream);
 
 /* --- measurement ------------------------------------------------------------------------ */
 

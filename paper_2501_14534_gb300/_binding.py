@@ -63,7 +63,7 @@ class tgs_grads(C.Structure):
 
 
 class tgs_stats(C.Structure):
-    _fields_ = [("grad_norm_accum", _vp), ("vis_count", _vp), ("max_radius", _vp)]
+    _fields_ = [("grad_norm_accum", _vp), ("vis_count", _vp), ("max_radius", _vp), ("hit_count", _vp)]
 
 
 _ctx_p = C.c_void_p
@@ -102,6 +102,9 @@ SIGNATURES = {
                                             _statp, C.c_uint32, _vp]),
     "tgs_bin_noalloc": (C.c_int32, [_vp, _vp, C.c_int64, _camp, C.c_int32, C.c_int32, _vp, _vp,
                                     _vp, C.c_int64, C.POINTER(C.c_int64), _vp]),
+    "tgs_count_hits": (C.c_int32, [_ctx_p, C.POINTER(tgs_gaussians), _camp, C.c_int32, _vp, _vp]),
+    "tgs_significance": (C.c_int32, [_ctx_p, C.POINTER(tgs_gaussians), _vp, C.c_double, _vp, _vp]),
+    "tgs_prune_select": (C.c_int32, [_ctx_p, _vp, C.c_int64, C.c_double, _vp, _vp]),
     "tgs_set_profiling": (C.c_int32, [_ctx_p, C.c_int32]),
     "tgs_stage_times": (C.c_int32, [_ctx_p, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),
     "tgs_stage_name": (C.c_char_p, [_ctx_p, C.c_int32]),

@@ -625,6 +625,67 @@ tgs_status tgs_backward(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *ca
     return TGS_OK;
 }
 
+// ---- significance pruning (Eq. significance-score) -----------------------------------------
+
+tgs_status tgs_count_hits(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                          uint32_t *hit_count, tgs_stream stream) {
+    if (!c || !g || !cams || V <= 0 || (!hit_count && g->n > 0)) return TGS_ERR_INVALID_ARG;
+    if (g->n == 0) return TGS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    GaussPtrs gp;
+    TGS_TRY(make_gauss(c->cfg, g, gp));
+    for (int v = 0; v < V; v++) {
+        CamBatch cb;
+        uint32_t *ids = nullptr;
+        TGS_TRY(plain_bin_view(c, g, gp, cams + v, cb, st, &ids));
+        PixPtrs px;
+        memset(&px, 0, sizeof px);  // nothing but the hits is written
+        launch_blend_forward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb,
+                             px, c->cfg.bg, st, hit_count, g->n);
+        TGS_TRY(last_error());
+    }
+    c->state_valid = false;  // the binning kept for a backward is not this one's
+    return TGS_OK;
+}
+
+tgs_status tgs_significance(tgs_ctx *c, const tgs_gaussians *g, const uint32_t *hit_count, double quantile,
+                            float *scores, tgs_stream stream) {
+    if (!c || !g || !(quantile >= 0.0 && quantile <= 1.0)) return TGS_ERR_INVALID_ARG;
+    const int64_t n = g->n;
+    if (n == 0) return TGS_OK;
+    if (!hit_count || !scores) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    GaussPtrs gp;
+    TGS_TRY(make_gauss(c->cfg, g, gp));
+    TGS_TRY(ensure_records(c, n, st));
+    float *vol = as<float>(c->pos);
+    uint32_t *k = as<uint32_t>(c->ck0), *v = as<uint32_t>(c->cv0);
+    launch_volumes(gp, vol, k, st);
+    radix_sort_pairs(k, v, as<uint32_t>(c->ck1), as<uint32_t>(c->cv1), nullptr, n, 0, 32, as<uint32_t>(c->hist),
+                     as<uint32_t>(c->partials), st, true);
+    const int64_t q_rank = (int64_t)std::floor(quantile * (double)(n - 1));
+    launch_scores(gp, hit_count, vol, k, q_rank, scores, st);
+    c->state_valid = false;
+    return last_error();
+}
+
+tgs_status tgs_prune_select(tgs_ctx *c, const float *scores, int64_t n, double fraction, uint8_t *prune,
+                            tgs_stream stream) {
+    if (!c || n < 0 || !(fraction >= 0.0 && fraction <= 1.0)) return TGS_ERR_INVALID_ARG;
+    if (n == 0) return TGS_OK;
+    if (!scores || !prune) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    TGS_TRY(ensure_records(c, n, st));
+    uint32_t *k = as<uint32_t>(c->ck0), *v = as<uint32_t>(c->cv0);
+    launch_score_keys(scores, n, k, st);
+    radix_sort_pairs(k, v, as<uint32_t>(c->ck1), as<uint32_t>(c->cv1), nullptr, n, 0, 32, as<uint32_t>(c->hist),
+                     as<uint32_t>(c->partials), st, true);
+    TGS_CHECK(cudaMemsetAsync(prune, 0, (size_t)n, st));
+    launch_mark(v, (int64_t)std::floor(fraction * (double)n), prune, st);
+    c->state_valid = false;
+    return last_error();
+}
+
 // ---- batched path --------------------------------------------------------------------------
 
 tgs_status tgs_plan(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
@@ -701,7 +762,7 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
     if (flags & TGS_UNFUSED) {
         mark(c, stage++, "blend_forward", st);
         launch_blend_forward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
-                             c->cfg.bg, st);
+                             c->cfg.bg, st, stats ? stats->hit_count : nullptr, n);
         mark(c, stage++, "l1_loss", st);
         for (int v = 0; v < V; v++) {
             const int64_t cnt = 3 * (int64_t)cams[v].width * cams[v].height;
@@ -722,7 +783,8 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
         TGS_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), st));
         mark(c, stage++, "fused_blend", st);
         launch_fused_l1(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), order, counter,
-                        cb, px, c->cfg.bg, as<float>(c->sgrads), loss_out, as<uint16_t>(c->viskeys), st);
+                        cb, px, c->cfg.bg, as<float>(c->sgrads), loss_out, as<uint16_t>(c->viskeys), st,
+                        stats ? stats->hit_count : nullptr, n);
     }
     mark(c, stage++, "preprocess_backward", st);
     GradPtrs o = grad_ptrs(grads, stats, (flags & TGS_ACCUMULATE) ? 1 : 0);

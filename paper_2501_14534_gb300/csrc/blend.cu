@@ -9,11 +9,12 @@
 namespace tgs {
 namespace {
 
-template <int TILE, int PPT, bool COUNT>
+template <int TILE, int PPT, bool COUNT, bool HITS>
 __global__ void __launch_bounds__(TILE * TILE / PPT)
 k_blend_fwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
             const uint2 *__restrict__ ranges, const __grid_constant__ CamBatch cb,
-            const __grid_constant__ PixPtrs px, float bg0, float bg1, float bg2) {
+            const __grid_constant__ PixPtrs px, float bg0, float bg1, float bg2,
+            uint32_t *__restrict__ hits, uint32_t n_gauss) {
     __shared__ BlendSmem<TILE * TILE / PPT> sm;
     const int gt = blockIdx.x;
     const int v = view_of_tile(cb, gt);
@@ -22,7 +23,8 @@ k_blend_fwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
     TilePixels<TILE, PPT> P;
     P.init(lt % cam.gx, lt / cam.gx, cam.W, cam.H);
     FwdState<PPT> S;
-    tile_forward<TILE, PPT, COUNT>(sm, splats, ids, ranges[gt], P, S);
+    tile_forward<TILE, PPT, COUNT, false, HITS>(sm, splats, ids, ranges[gt], P, S, nullptr, hits,
+                                                (uint32_t)v * n_gauss);
     const int HW = cam.W * cam.H;
     float *img = px.image[v];
     float *Tf = px.T_final[v];
@@ -32,9 +34,11 @@ k_blend_fwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
     for (int k = 0; k < PPT; k++) {
         if (!P.inside[k]) continue;
         const int pix = P.y[k] * cam.W + P.x[k];
-        img[pix] = S.Cr[k] + S.T[k] * bg0;
-        img[HW + pix] = S.Cg[k] + S.T[k] * bg1;
-        img[2 * HW + pix] = S.Cb[k] + S.T[k] * bg2;
+        if (img) {
+            img[pix] = S.Cr[k] + S.T[k] * bg0;
+            img[HW + pix] = S.Cg[k] + S.T[k] * bg1;
+            img[2 * HW + pix] = S.Cb[k] + S.T[k] * bg2;
+        }
         if (Tf) Tf[pix] = S.T[k];
         if (ls) ls[pix] = S.last[k];
         if (ex) ex[pix] = S.exam[k];
@@ -96,16 +100,19 @@ __global__ void k_l1(const float *__restrict__ img, const float *__restrict__ tg
 
 template <int TILE, int PPT>
 void fwd_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const CamBatch &cb,
-                const PixPtrs &px, const float *bg, cudaStream_t st) {
+                const PixPtrs &px, const float *bg, uint32_t *hits, int64_t n_gauss, cudaStream_t st) {
     bool count = false;
     for (int v = 0; v < cb.V; v++) count = count || px.n_contrib[v] || px.n_eval[v];
+    const uint32_t n = (uint32_t)n_gauss;
     count_launch();
-    if (count)
-        k_blend_fwd<TILE, PPT, true><<<cb.total_tiles, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, cb, px,
-                                                                                   bg[0], bg[1], bg[2]);
-    else
-        k_blend_fwd<TILE, PPT, false><<<cb.total_tiles, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, cb, px,
-                                                                                    bg[0], bg[1], bg[2]);
+#define TGS_FWD(C, HT)                                                                                 \
+    k_blend_fwd<TILE, PPT, C, HT><<<cb.total_tiles, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, cb, px, \
+                                                                               bg[0], bg[1], bg[2], hits, n)
+    if (count && hits) TGS_FWD(true, true);
+    else if (count) TGS_FWD(true, false);
+    else if (hits) TGS_FWD(false, true);
+    else TGS_FWD(false, false);
+#undef TGS_FWD
 }
 
 template <int TILE, int PPT>
@@ -139,9 +146,9 @@ int blend_supported(int tile, int ppt) {
 
 void launch_blend_forward(int tile, int ppt, const float4 *splats, const uint32_t *ids,
                           const uint2 *ranges, const CamBatch &cb, const PixPtrs &px,
-                          const float *bg, cudaStream_t st) {
+                          const float *bg, cudaStream_t st, uint32_t *hits, int64_t n_gauss) {
     if (cb.total_tiles <= 0) return;
-    TGS_DISPATCH(fwd_launch, splats, ids, ranges, cb, px, bg, st);
+    TGS_DISPATCH(fwd_launch, splats, ids, ranges, cb, px, bg, hits, n_gauss, st);
 }
 
 void launch_blend_backward(int tile, int ppt, const float4 *splats, const uint32_t *ids,

@@ -154,12 +154,15 @@ struct FwdState {
 // Front-to-back blend of one tile's list [rg.x, rg.y). On return every pixel holds its
 // colour sum, transmittance, last contributor (1-based list position, 0 if none) and the
 // number of list entries it examined.
-template <int TILE, int PPT, bool COUNT = false, bool KEEPVIS = false>
+// With HITS every blended fragment counts one ray hit of its Gaussian (Eq.
+// significance-score): hits[record - rec_off] += the pixels of the warp that blended it.
+template <int TILE, int PPT, bool COUNT = false, bool KEEPVIS = false, bool HITS = false>
 __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
                                              const float4 *__restrict__ splats,
                                              const uint32_t *__restrict__ ids, uint2 rg,
                                              const TilePixels<TILE, PPT> &P, FwdState<PPT> &S,
-                                             uint16_t *__restrict__ vis_out = nullptr) {
+                                             uint16_t *__restrict__ vis_out = nullptr,
+                                             uint32_t *__restrict__ hits = nullptr, uint32_t rec_off = 0) {
     constexpr int NT = TILE * TILE / PPT;
     const unsigned full = 0xffffffffu;
     const int t = threadIdx.x;
@@ -201,6 +204,7 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
             const float cbl = dd.x, qmin = dd.y;
             const float dx = a.x - P.fx[0], Adx = __fmul_rn(a.z, dx);  // same column for all PPT
             const bool xin = cover || (unsigned)(P.x[0] - r.x) <= (unsigned)(r.y - r.x);
+            uint32_t nb = 0;  // pixels of this thread that blend the splat (HITS)
 #pragma unroll
             for (int k = 0; k < PPT; k++) {
                 if (S.done[k]) continue;
@@ -223,6 +227,11 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
                 S.Cb[k] = __fmaf_rn(cbl, w, S.Cb[k]);
                 S.T[k] = tT;
                 S.last[k] = pos0 + m + 1;
+                if (HITS) nb++;
+            }
+            if (HITS) {
+                const uint32_t tot = __reduce_add_sync(full, nb);
+                if ((t & 31) == 0 && tot) atomicAdd(hits + (__float_as_uint(dd.w) - rec_off), tot);
             }
           }
           // checked once per chunk: a warp whose pixels all stopped leaves the list

@@ -32,13 +32,14 @@ __global__ void k_item_keys(const uint2 *__restrict__ ranges, int n, uint32_t *_
     vals[i] = (uint32_t)i;
 }
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool HITS>
 __global__ void __launch_bounds__(TILE * TILE / PPT)
 k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
            const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, int n_items,
            int *__restrict__ counter, const __grid_constant__ CamBatch cb,
            const __grid_constant__ PixPtrs px, float bg0, float bg1, float bg2,
-           float *__restrict__ sgrads, float *__restrict__ loss, uint16_t *__restrict__ vis_keys) {
+           float *__restrict__ sgrads, float *__restrict__ loss, uint16_t *__restrict__ vis_keys,
+           uint32_t *__restrict__ hits, uint32_t n_gauss) {
     constexpr int NT = TILE * TILE / PPT;
     constexpr int NW = NT / 32;
     static_assert(NW <= 16, "the per-key warp masks are 16 bits");
@@ -60,7 +61,7 @@ k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
         P.init(lt % cam.gx, lt / cam.gx, cam.W, cam.H);
         const uint2 rg = ranges[gt];
         FwdState<PPT> S;
-        tile_forward<TILE, PPT, false, true>(sm, splats, ids, rg, P, S, vis_keys);
+        tile_forward<TILE, PPT, false, true, HITS>(sm, splats, ids, rg, P, S, vis_keys, hits, (uint32_t)v * n_gauss);
 
         // L1 loss: L = mean over views of mean over 3HW |C - target|; dL/dC = sign / (3HWV)
         const int HW = cam.W * cam.H;
@@ -103,10 +104,10 @@ k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
     }
 }
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool HITS>
 int fused_blocks_per_sm() {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_l1<TILE, PPT>, TILE * TILE / PPT, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_l1<TILE, PPT, HITS>, TILE * TILE / PPT, 0) !=
         cudaSuccess) {
         cudaGetLastError();
         b = 1;
@@ -114,24 +115,37 @@ int fused_blocks_per_sm() {
     return b < 1 ? 1 : b;
 }
 
-template <int TILE, int PPT>
-void fused_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const uint32_t *order,
-                  int *counter, const CamBatch &cb, const PixPtrs &px, const float *bg, float *sgrads,
-                  float *loss, uint16_t *vis_keys, cudaStream_t st) {
+template <int TILE, int PPT, bool HITS>
+void fused_launch_t(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const uint32_t *order,
+                    int *counter, const CamBatch &cb, const PixPtrs &px, const float *bg, float *sgrads,
+                    float *loss, uint16_t *vis_keys, uint32_t *hits, uint32_t n_gauss, cudaStream_t st) {
     static std::once_flag once;
     static int per_sm = 1, sms = 1;
     std::call_once(once, [] {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        per_sm = fused_blocks_per_sm<TILE, PPT>();
+        per_sm = fused_blocks_per_sm<TILE, PPT, HITS>();
     });
     int grid = sms * per_sm;
     if (grid > cb.total_tiles) grid = cb.total_tiles;
     if (grid < 1) grid = 1;
     count_launch();
-    k_fused_l1<TILE, PPT><<<grid, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, order, cb.total_tiles, counter,
-                                                              cb, px, bg[0], bg[1], bg[2], sgrads, loss, vis_keys);
+    k_fused_l1<TILE, PPT, HITS><<<grid, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, order, cb.total_tiles,
+                                                                    counter, cb, px, bg[0], bg[1], bg[2], sgrads,
+                                                                    loss, vis_keys, hits, n_gauss);
+}
+
+template <int TILE, int PPT>
+void fused_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const uint32_t *order,
+                  int *counter, const CamBatch &cb, const PixPtrs &px, const float *bg, float *sgrads,
+                  float *loss, uint16_t *vis_keys, uint32_t *hits, uint32_t n_gauss, cudaStream_t st) {
+    if (hits)
+        fused_launch_t<TILE, PPT, true>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys,
+                                        hits, n_gauss, st);
+    else
+        fused_launch_t<TILE, PPT, false>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys,
+                                         hits, n_gauss, st);
 }
 
 }  // namespace
@@ -148,15 +162,17 @@ void build_item_order(const uint2 *ranges, int total_tiles, uint32_t *k0, uint32
 
 void launch_fused_l1(int tile, int ppt, const float4 *splats, const uint32_t *ids, const uint2 *ranges,
                      const uint32_t *order, int *counter, const CamBatch &cb, const PixPtrs &px,
-                     const float *bg, float *sgrads, float *loss, uint16_t *vis_keys, cudaStream_t st) {
+                     const float *bg, float *sgrads, float *loss, uint16_t *vis_keys, cudaStream_t st,
+                     uint32_t *hits, int64_t n_gauss) {
     if (cb.total_tiles <= 0) return;
-    if (tile == 8 && ppt == 1) fused_launch<8, 1>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
-    else if (tile == 8 && ppt == 2) fused_launch<8, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
-    else if (tile == 16 && ppt == 1) fused_launch<16, 1>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
-    else if (tile == 16 && ppt == 2) fused_launch<16, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
-    else if (tile == 16 && ppt == 4) fused_launch<16, 4>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
-    else if (tile == 32 && ppt == 2) fused_launch<32, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
-    else if (tile == 32 && ppt == 4) fused_launch<32, 4>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, st);
+    const uint32_t n = (uint32_t)n_gauss;
+    if (tile == 8 && ppt == 1) fused_launch<8, 1>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    else if (tile == 8 && ppt == 2) fused_launch<8, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    else if (tile == 16 && ppt == 1) fused_launch<16, 1>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    else if (tile == 16 && ppt == 2) fused_launch<16, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    else if (tile == 16 && ppt == 4) fused_launch<16, 4>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    else if (tile == 32 && ppt == 2) fused_launch<32, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    else if (tile == 32 && ppt == 4) fused_launch<32, 4>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
 }
 
 }  // namespace tgs

@@ -189,9 +189,12 @@ void make_full_keys(const uint32_t *tile_keys, const uint32_t *tile_vals, const 
 
 // blend.cu
 int blend_supported(int tile, int ppt);
+// hits (may be null): per-Gaussian ray hits added in (Eq. significance-score); record r of
+// view v is Gaussian r - v n_gauss
 void launch_blend_forward(int tile, int ppt, const float4 *splats, const uint32_t *ids,
                           const uint2 *ranges, const CamBatch &cb, const PixPtrs &px,
-                          const float *bg, cudaStream_t st);
+                          const float *bg, cudaStream_t st, uint32_t *hits = nullptr,
+                          int64_t n_gauss = 0);
 void launch_blend_backward(int tile, int ppt, const float4 *splats, const uint32_t *ids,
                            const uint2 *ranges, const CamBatch &cb, const PixPtrs &px,
                            const float *bg, float *sgrads, cudaStream_t st);
@@ -205,6 +208,14 @@ void build_item_order(const uint2 *ranges, int total_tiles, uint32_t *k0, uint32
 // masks of each list entry, read back by the backward
 void launch_fused_l1(int tile, int ppt, const float4 *splats, const uint32_t *ids, const uint2 *ranges,
                      const uint32_t *order, int *counter, const CamBatch &cb, const PixPtrs &px,
-                     const float *bg, float *sgrads, float *loss, uint16_t *vis_keys, cudaStream_t st);
+                     const float *bg, float *sgrads, float *loss, uint16_t *vis_keys, cudaStream_t st,
+                     uint32_t *hits = nullptr, int64_t n_gauss = 0);
+
+// significance.cu (Eq. significance-score)
+void launch_volumes(const GaussPtrs &g, float *vol, uint32_t *keys, cudaStream_t st);
+void launch_scores(const GaussPtrs &g, const uint32_t *hits, const float *vol, const uint32_t *sorted_vol_bits,
+                   int64_t q_rank, float *scores, cudaStream_t st);
+void launch_score_keys(const float *scores, int64_t n, uint32_t *keys, cudaStream_t st);
+void launch_mark(const uint32_t *sorted_idx, int64_t k, uint8_t *prune, cudaStream_t st);
 
 }  // namespace tgs

@@ -201,10 +201,15 @@ class Rasterizer:
         return d
 
     @staticmethod
-    def alloc_stats(n):
-        return dict(grad_norm_accum=torch.zeros(n, device="cuda"),
-                    vis_count=torch.zeros(n, device="cuda", dtype=torch.int32),
-                    max_radius=torch.zeros(n, device="cuda", dtype=torch.int32))
+    def alloc_stats(n, hits=False):
+        """Densification statistics; with hits also the ray-hit counter of the significance
+        score (Eq. significance-score), which the batched step then fills as well."""
+        st = dict(grad_norm_accum=torch.zeros(n, device="cuda"),
+                  vis_count=torch.zeros(n, device="cuda", dtype=torch.int32),
+                  max_radius=torch.zeros(n, device="cuda", dtype=torch.int32))
+        if hits:
+            st["hit_count"] = torch.zeros(n, device="cuda", dtype=torch.int32)
+        return st
 
     @staticmethod
     def _grad_struct(grads):
@@ -215,7 +220,7 @@ class Rasterizer:
     def _stats_struct(stats):
         stats = stats or {}
         return B.tgs_stats(_p(stats.get("grad_norm_accum")), _p(stats.get("vis_count")),
-                           _p(stats.get("max_radius")))
+                           _p(stats.get("max_radius")), _p(stats.get("hit_count")))
 
     def backward(self, g: Gaussians, cams, outs, dL_dimages, grads=None, stats=None,
                  accumulate=False, no_sh_rest=False):
@@ -320,6 +325,35 @@ class Rasterizer:
             _ptr_array(images) if images is not None else None, C.byref(self._grad_struct(grads)),
             C.byref(self._stats_struct(stats)), _p(loss), flags, _stream()),
             "tgs_train_step_batched")
+
+    # ---- significance pruning (Eq. significance-score) ----
+
+    def count_hits(self, g: Gaussians, cams, hit_count=None):
+        """Adds each Gaussian's ray hits over these views to hit_count (int32 [n], zeros if
+        None) and returns it: the pixels whose blend blends it."""
+        if hit_count is None:
+            hit_count = torch.zeros(g.n, device="cuda", dtype=torch.int32)
+        assert hit_count.dtype == torch.int32 and hit_count.is_cuda and hit_count.numel() == g.n
+        camarr = cameras_array(cams)
+        B.check(B.lib.tgs_count_hits(self._h, C.byref(g.struct()), camarr, len(camarr), _p(hit_count),
+                                     _stream()), "tgs_count_hits")
+        return hit_count
+
+    def significance(self, g: Gaussians, hit_count, quantile=0.9):
+        """Significance score of each Gaussian (float32 [n]) from its ray hits, opacity and
+        volume; quantile picks the reference volume (the paper's 90% largest)."""
+        scores = torch.empty(g.n, device="cuda", dtype=torch.float32)
+        B.check(B.lib.tgs_significance(self._h, C.byref(g.struct()), _p(hit_count), float(quantile),
+                                       _p(scores), _stream()), "tgs_significance")
+        return scores
+
+    def prune_select(self, scores, fraction):
+        """bool [n]: the floor(fraction n) lowest scores (equal scores: lower index first)."""
+        scores = scores.contiguous()
+        out = torch.empty(scores.numel(), device="cuda", dtype=torch.uint8)
+        B.check(B.lib.tgs_prune_select(self._h, _p(scores), scores.numel(), float(fraction), _p(out),
+                                       _stream()), "tgs_prune_select")
+        return out.bool()
 
     def set_profiling(self, on=True):
         B.check(B.lib.tgs_set_profiling(self._h, int(on)), "tgs_set_profiling")
