@@ -775,11 +775,19 @@ def test_significance_closed_form():
     hits = np.array([10, 0, 3, 7])
     got = oracle.significance(scene, oracle.Settings(), hits)
     np.testing.assert_allclose(got, [10 * 0.5 * 0.25, 0.0, 3 * 0.5 * 1.0, 7 * 0.75 * 1.0], rtol=1e-14)
+    # q = 1 normalises by the largest volume (gamma = v / 8), q = 0 by the smallest (gamma = 1)
+    got = oracle.significance(scene, oracle.Settings(), hits, quantile=1.0)
+    np.testing.assert_allclose(got, [10 * 0.5 / 8, 0.0, 3 * 0.5 * 4 / 8, 7 * 0.75], rtol=1e-14)
+    got = oracle.significance(scene, oracle.Settings(), hits, quantile=0.0)
+    np.testing.assert_allclose(got, [10 * 0.5, 0.0, 3 * 0.5, 7 * 0.75], rtol=1e-14)
     # a masked Gaussian has opacity and volume 0; the quantile is taken over all n volumes
     scene["mask_logits"] = np.array([5.0, 5.0, -5.0, 5.0])
     got = oracle.significance(scene, oracle.Settings(eps_mask=0.5), hits)
     # volumes 1, 2, 0, 8 -> sorted 0, 1, 2, 8 -> rank 2: 2 -> gamma 1/2, 1, 0, 1
     np.testing.assert_allclose(got, [10 * 0.5 * 0.5, 0.0, 0.0, 7 * 0.75], rtol=1e-14)
+    # q = 0 now picks the masked Gaussian's volume 0: gamma = 1 for all, the masked one still 0
+    got = oracle.significance(scene, oracle.Settings(eps_mask=0.5), hits, quantile=0.0)
+    np.testing.assert_allclose(got, [10 * 0.5, 0.0, 0.0, 7 * 0.75], rtol=1e-14)
 
 
 def test_prune_selection_rule():
