@@ -334,6 +334,34 @@ def main():
     except Exception as e:  # reported, not fatal
         print(f"[bench] unfused A/B failed: {e}", file=sys.stderr)
 
+    # ---- the step with the L1 + D-SSIM loss of Eq. loss3dgs (separate launches) ----
+    dssim = None
+    try:
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                rast.train_step_batched(g, cams, targets, grads, stats, loss, graph=True, dssim=True)
+            d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            d0.record(stream)
+            for _ in range(3):
+                rast.train_step_batched(g, cams, targets, grads, stats, loss, graph=True, dssim=True)
+            d1.record(stream)
+        stream.synchronize()
+        dssim = {"views_per_s": V * world / (d0.elapsed_time(d1) / 3 / 1000.0)}
+        rast.set_profiling(True)
+        with torch.cuda.stream(stream):
+            for _ in range(2):   # the first captures the profiled graph
+                rast.train_step_batched(g, cams, targets, grads, stats, loss, graph=True, dssim=True)
+            dssim["stage_ms"] = rast.stage_times()
+        rast.set_profiling(False)
+        ms = dssim["stage_ms"].get("l1_dssim_loss")
+        if ms:
+            elems = 3 * sum(c.width * c.height for c in cams)
+            # algorithmic bytes: read image and target, write dL/dimage (4 B each per element)
+            dssim["loss_kernels"] = {"elements": elems, "ms": ms, "algorithmic_GBps": 12 * elems / ms / 1e6}
+    except Exception as e:  # reported, not fatal
+        rast.set_profiling(False)
+        print(f"[bench] D-SSIM step failed: {e}", file=sys.stderr)
+
     # ---- e2e: inputs from pinned host memory each step, loss read back ----
     host = {k: t.detach().cpu().pin_memory() for k, t in g.params().items()}
     host_t = [t.cpu().pin_memory() for t in targets]
@@ -445,7 +473,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms},
             "plain_views_per_s": plain_vps, "render_fps": render_fps,
-            "unfused_views_per_s": unfused,
+            "unfused_views_per_s": unfused, "l1_dssim_step": dssim,
             "speedup_vs_plain": value / world / plain_vps,
             "stage_ms": stage_ms,
             "pairs": {"examined": P_exam, "evaluated": P_eval, "contributing": P_contrib},

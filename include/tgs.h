@@ -91,6 +91,8 @@ typedef int32_t tgs_status;
 #define TGS_NO_SH_REST_GRAD 2u  /* skip dL/d sh_rest (SH rest bands updated every 16 steps) */
 #define TGS_USE_GRAPH 4u        /* batched step: replay a captured CUDA graph when arguments repeat */
 #define TGS_UNFUSED 8u          /* batched step: separate forward, loss and backward kernels (A/B) */
+#define TGS_LOSS_DSSIM 16u      /* batched step: loss (1 - lambda) L1 + lambda D-SSIM (Eq. loss3dgs),
+                                   lambda = tgs_config.ssim_lambda; implies separate kernels */
 
 typedef struct tgs_ctx tgs_ctx;
 typedef void *tgs_stream; /* a cudaStream_t; NULL is the legacy default stream */
@@ -106,6 +108,8 @@ typedef struct {
     float bg[3];           /* background colour (default 0) */
     int64_t key_capacity;  /* (Gaussian, tile) keys the batched path may hold; 0 = sized by tgs_plan */
     int64_t spin_limit;    /* iterations of any bounded device wait (default 1 << 22) */
+    float ssim_lambda;     /* lambda_SSIM of Eq. loss3dgs for TGS_LOSS_DSSIM, in [0, 1] (default 0.2) */
+    int32_t reserved0;
 } tgs_config;
 
 typedef struct {
@@ -189,6 +193,19 @@ tgs_status tgs_backward(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *
    target) (sign(0) = 0). count = 3 H W. loss_accum is a device float. */
 tgs_status tgs_l1_loss(const float *image, const float *target, int64_t count, float scale,
                        float *loss_accum, float *grad, tgs_stream stream);
+/* L1 + D-SSIM loss of Eq. loss3dgs (its mask terms excluded) over V views of any sizes:
+   *loss_accum += mean over views of ((1 - lambda) mean_3HW |x - y| + lambda (1 - SSIM(x, y))),
+   grads[v] = dL/d images[v] (overwritten). images, targets, grads: host arrays of V device
+   pointers to [3,H,W] planar images, the sizes taken from cams[v].width, height (the rest of
+   the camera is not read). SSIM per channel as 3DGS trains it (Wang et al.): local means,
+   variances and covariance under an 11 x 11 Gaussian window of sigma 1.5 normalised to sum 1,
+   the image taken as 0 outside its border, C1 = 0.01^2, C2 = 0.03^2, averaged over the 3HW
+   outputs; the window sums run as two 1D passes (Sec. "Accelerated training"). loss_accum may
+   be NULL. The context provides scratch (3 floats per element; grown outside stream capture,
+   else TGS_ERR_CAPACITY). lambda in [0, 1], else TGS_ERR_INVALID_ARG. Asynchronous. */
+tgs_status tgs_l1_dssim_loss(tgs_ctx *ctx, const tgs_camera *cams, int32_t V, const float *const *images,
+                             const float *const *targets, float lambda, float *loss_accum,
+                             float *const *grads, tgs_stream stream);
 
 /* --- the batched path ---------------------------------------------------------------- */
 
@@ -199,7 +216,9 @@ tgs_status tgs_plan(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams
 /* One training step over V views of any sizes: preprocess of all views, one key sort, a
    persistent fused forward + L1 loss + backward over (view, tile) work items heaviest first
    (TGS_UNFUSED: one forward launch, V loss launches and one backward launch instead), and
-   the preprocess backward. loss_out (device float) = mean over views of mean |C - t|.
+   the preprocess backward. loss_out (device float) = mean over views of mean |C - t|; with
+   TGS_LOSS_DSSIM the loss of tgs_l1_dssim_loss at lambda = tgs_config.ssim_lambda, whose
+   gradient is not pixel-local, so forward, loss and backward run as separate launches.
    images (optional, host array of V device pointers) receives the rendered views.
    Never synchronises; with TGS_USE_GRAPH the whole step is captured once into a CUDA graph
    and replayed while g, cams, targets, images, grads, stats and loss_out are unchanged.

@@ -27,6 +27,7 @@ TGS_ACCUMULATE = 1
 TGS_NO_SH_REST_GRAD = 2
 TGS_USE_GRAPH = 4
 TGS_UNFUSED = 8
+TGS_LOSS_DSSIM = 16
 
 _fp = C.POINTER(C.c_float)
 _vp = C.c_void_p
@@ -36,7 +37,7 @@ class tgs_config(C.Structure):
     _fields_ = [("tile", C.c_int32), ("ppt", C.c_int32), ("support", C.c_int32),
                 ("low_pass", C.c_float), ("eps_mask", C.c_float), ("eps_sh", C.c_float),
                 ("near_plane", C.c_float), ("bg", C.c_float * 3), ("key_capacity", C.c_int64),
-                ("spin_limit", C.c_int64)]
+                ("spin_limit", C.c_int64), ("ssim_lambda", C.c_float), ("reserved0", C.c_int32)]
 
 
 class tgs_gaussians(C.Structure):
@@ -88,6 +89,7 @@ SIGNATURES = {
     "tgs_backward": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _outp, _pp, _gradp, _statp,
                                  C.c_uint32, _vp]),
     "tgs_l1_loss": (C.c_int32, [_vp, _vp, C.c_int64, C.c_float, _vp, _vp, _vp]),
+    "tgs_l1_dssim_loss": (C.c_int32, [_ctx_p, _camp, C.c_int32, _pp, _pp, C.c_float, _vp, _pp, _vp]),
     "tgs_plan": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, C.c_double, C.POINTER(C.c_int64)]),
     "tgs_train_step_batched": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _pp, _pp, _gradp,
                                            _statp, _vp, C.c_uint32, _vp]),

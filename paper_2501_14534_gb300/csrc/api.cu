@@ -34,7 +34,7 @@ struct tgs_ctx {
     int device = 0;
     // scratch arena
     Buf splats, radii, tt, dbits, pos, ck0, cv0, ck1, cv1, offsets, tk0, tv0, tk1, tv1, ranges,
-        hist, partials, sgrads, counts, status, pixstate, dimg, images, items, kmask, viskeys;
+        hist, partials, sgrads, counts, status, pixstate, dimg, images, items, kmask, viskeys, ssim;
     uint32_t *h_counts = nullptr;   // pinned host copy of (visible, K)
     // binning kept from the last plain forward
     bool state_valid = false;
@@ -103,7 +103,7 @@ T *as(Buf &b) { return reinterpret_cast<T *>(b.p); }
 bool valid_cfg(const tgs_config &c) {
     return blend_supported(c.tile, c.ppt) && (c.support == TGS_SUPPORT_BOX3 || c.support == TGS_SUPPORT_ALPHA) &&
            c.low_pass >= 0.f && c.eps_mask > 0.f && c.eps_mask < 1.f && c.eps_sh > 0.f && c.eps_sh < 1.f &&
-           c.near_plane > 0.f && c.key_capacity >= 0;
+           c.near_plane > 0.f && c.key_capacity >= 0 && c.ssim_lambda >= 0.f && c.ssim_lambda <= 1.f;
 }
 
 tgs_status make_batch(const tgs_config &cfg, const tgs_camera *cams, int V, CamBatch &cb) {
@@ -343,6 +343,7 @@ void tgs_default_config(tgs_config *cfg) {
     cfg->near_plane = 0.2f;
     cfg->key_capacity = 0;
     cfg->spin_limit = (int64_t)1 << 22;
+    cfg->ssim_lambda = 0.2f;
 }
 
 const char *tgs_status_string(tgs_status s) {
@@ -391,7 +392,7 @@ void tgs_destroy(tgs_ctx *c) {
     Buf *bufs[] = {&c->splats, &c->radii, &c->tt, &c->dbits, &c->pos, &c->ck0, &c->cv0, &c->ck1,
                    &c->cv1, &c->offsets, &c->tk0, &c->tv0, &c->tk1, &c->tv1, &c->ranges, &c->hist,
                    &c->partials, &c->sgrads, &c->counts, &c->status, &c->pixstate, &c->dimg,
-                   &c->images, &c->items, &c->kmask, &c->viskeys};
+                   &c->images, &c->items, &c->kmask, &c->viskeys, &c->ssim};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_counts) cudaFreeHost(c->h_counts);
@@ -550,6 +551,25 @@ tgs_status tgs_l1_loss(const float *image, const float *target, int64_t count, f
                        float *loss_accum, float *grad, tgs_stream stream) {
     if (!image || !target || count < 0) return TGS_ERR_INVALID_ARG;
     launch_l1(image, target, count, scale, loss_accum, grad, (cudaStream_t)stream);
+    return last_error();
+}
+
+tgs_status tgs_l1_dssim_loss(tgs_ctx *c, const tgs_camera *cams, int32_t V, const float *const *images,
+                             const float *const *targets, float lambda, float *loss_accum, float *const *grads,
+                             tgs_stream stream) {
+    if (!c || !cams || !images || !targets || !grads || V <= 0 || V > kMaxViews || !(lambda >= 0.f) ||
+        !(lambda <= 1.f))
+        return TGS_ERR_INVALID_ARG;
+    int W[kMaxViews], H[kMaxViews];
+    for (int v = 0; v < V; v++) {
+        if (!images[v] || !targets[v] || !grads[v] || cams[v].width < 0 || cams[v].height < 0)
+            return TGS_ERR_INVALID_ARG;
+        W[v] = cams[v].width;
+        H[v] = cams[v].height;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    TGS_TRY(ensure(c->ssim, sizeof(float) * (size_t)ssim_scratch_floats(W, H, V), st));
+    launch_l1_dssim(V, W, H, images, targets, grads, lambda, as<float>(c->ssim), loss_accum, st);
     return last_error();
 }
 
@@ -724,6 +744,8 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
                                float *loss_out, uint32_t flags, cudaStream_t st) {
     const int64_t n = g->n, nt = n * V;
     const int64_t cap = c->cfg.key_capacity;
+    // the D-SSIM gradient is not pixel-local: forward, loss and backward run as separate kernels
+    const bool split = (flags & (TGS_UNFUSED | TGS_LOSS_DSSIM)) != 0;
     // pixel buffers: images (if the caller gives none), T_final, last, dL/dimage
     size_t pix = 0;
     for (int v = 0; v < V; v++) pix += (size_t)cams[v].width * cams[v].height;
@@ -737,7 +759,7 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
     for (int v = 0; v < V; v++) {
         const size_t hw = (size_t)cams[v].width * cams[v].height;
         // the fused step needs no image of its own: it writes one only where the caller asks
-        outs[v].image = images && images[v] ? images[v] : ((flags & TGS_UNFUSED) ? imgbuf + 3 * off : nullptr);
+        outs[v].image = images && images[v] ? images[v] : (split ? imgbuf + 3 * off : nullptr);
         outs[v].T_final = Tf + off;
         outs[v].last = last + off;
         outs[v].n_examined = nullptr;
@@ -759,15 +781,29 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
     for (int v = 0; v < V; v++) px.target[v] = targets[v];
     if (loss_out) TGS_CHECK(cudaMemsetAsync(loss_out, 0, sizeof(float), st));
     int stage = 2;
-    if (flags & TGS_UNFUSED) {
+    if (split) {
         mark(c, stage++, "blend_forward", st);
         launch_blend_forward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
                              c->cfg.bg, st, stats ? stats->hit_count : nullptr, n);
-        mark(c, stage++, "l1_loss", st);
-        for (int v = 0; v < V; v++) {
-            const int64_t cnt = 3 * (int64_t)cams[v].width * cams[v].height;
-            launch_l1(outs[v].image, targets[v], cnt, (float)(1.0 / ((double)cnt * V)), loss_out,
-                      const_cast<float *>(dls[v]), st);
+        if (flags & TGS_LOSS_DSSIM) {
+            mark(c, stage++, "l1_dssim_loss", st);
+            int W[kMaxViews], H[kMaxViews];
+            const float *x[kMaxViews];
+            float *dx[kMaxViews];
+            for (int v = 0; v < V; v++) {
+                W[v] = cams[v].width;
+                H[v] = cams[v].height;
+                x[v] = outs[v].image;
+                dx[v] = const_cast<float *>(dls[v]);
+            }
+            launch_l1_dssim(V, W, H, x, targets, dx, c->cfg.ssim_lambda, as<float>(c->ssim), loss_out, st);
+        } else {
+            mark(c, stage++, "l1_loss", st);
+            for (int v = 0; v < V; v++) {
+                const int64_t cnt = 3 * (int64_t)cams[v].width * cams[v].height;
+                launch_l1(outs[v].image, targets[v], cnt, (float)(1.0 / ((double)cnt * V)), loss_out,
+                          const_cast<float *>(dls[v]), st);
+            }
         }
         mark(c, stage++, "blend_backward", st);
         launch_blend_backward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
@@ -790,7 +826,7 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
     GradPtrs o = grad_ptrs(grads, stats, (flags & TGS_ACCUMULATE) ? 1 : 0);
     // the fused blend leaves pixel sums (moments) in the gradient records
     launch_preprocess_backward(gp, cb, as<float4>(c->sgrads), as<int32_t>(c->radii), o,
-                               (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, (flags & TGS_UNFUSED) ? 0 : 1, st);
+                               (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, split ? 0 : 1, st);
     mark(c, stage, "end", st);
     c->kernels_per_step = g_launches - launches0;
     return last_error();
@@ -820,6 +856,14 @@ tgs_status tgs_train_step_batched(tgs_ctx *c, const tgs_gaussians *g, const tgs_
     TGS_TRY(ensure(c->images, sizeof(float) * 3 * pix, st));
     TGS_TRY(ensure(c->dimg, sizeof(float) * 3 * pix, st));
     TGS_TRY(ensure(c->pixstate, sizeof(float) * 2 * pix, st));
+    if (flags & TGS_LOSS_DSSIM) {
+        int W[kMaxViews], H[kMaxViews];
+        for (int v = 0; v < V; v++) {
+            W[v] = cams[v].width;
+            H[v] = cams[v].height;
+        }
+        TGS_TRY(ensure(c->ssim, sizeof(float) * (size_t)ssim_scratch_floats(W, H, V), st));
+    }
     TGS_TRY(ensure(c->items, sizeof(uint32_t) * 4 * (((size_t)std::max(cb.total_tiles, 1) + 3) / 4 * 4), st));
     c->state_valid = false;
 

@@ -211,6 +211,12 @@ void launch_fused_l1(int tile, int ppt, const float4 *splats, const uint32_t *id
                      const float *bg, float *sgrads, float *loss, uint16_t *vis_keys, cudaStream_t st,
                      uint32_t *hits = nullptr, int64_t n_gauss = 0);
 
+// ssim.cu (Eq. loss3dgs): loss += mean over views of (1 - lam) mean |x - y| + lam (1 - mean
+// SSIM), grad[v] = dL/dx[v]; scratch: ssim_scratch_floats floats
+int64_t ssim_scratch_floats(const int *W, const int *H, int V);
+void launch_l1_dssim(int V, const int *W, const int *H, const float *const *x, const float *const *y,
+                     float *const *grad, float lam, float *scratch, float *loss, cudaStream_t st);
+
 // significance.cu (Eq. significance-score)
 void launch_volumes(const GaussPtrs &g, float *vol, uint32_t *keys, cudaStream_t st);
 void launch_scores(const GaussPtrs &g, const uint32_t *hits, const float *vol, const uint32_t *sorted_vol_bits,

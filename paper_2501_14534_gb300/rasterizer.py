@@ -116,9 +116,10 @@ class Rasterizer:
     """One libtgs context (its settings and its scratch arena) on the current device."""
 
     def __init__(self, tile=16, ppt=1, support=B.TGS_SUPPORT_BOX3, low_pass=0.3, eps_mask=0.05,
-                 eps_sh=0.1, near=0.2, bg=(0.0, 0.0, 0.0), key_capacity=0):
+                 eps_sh=0.1, near=0.2, bg=(0.0, 0.0, 0.0), key_capacity=0, ssim_lambda=0.2):
         cfg = B.tgs_config()
         B.lib.tgs_default_config(C.byref(cfg))
+        cfg.ssim_lambda = ssim_lambda
         cfg.tile, cfg.ppt, cfg.support = tile, ppt, support
         cfg.low_pass, cfg.eps_mask, cfg.eps_sh, cfg.near_plane = low_pass, eps_mask, eps_sh, near
         for i in range(3):
@@ -242,6 +243,25 @@ class Rasterizer:
         B.check(B.lib.tgs_l1_loss(_p(image), _p(target), image.numel(), float(scale),
                                   _p(loss_accum), _p(grad), _stream()), "tgs_l1_loss")
 
+    def l1_dssim_loss(self, images, targets, lam=0.2, loss=None, grads=None):
+        """Eq. loss3dgs without the mask terms over views of any sizes: adds to loss (device
+        float [1], zeros if None) the mean over views of (1 - lam) L1 + lam (1 - SSIM) and
+        returns (loss, grads) with grads[v] = dL/d images[v]."""
+        V = len(images)
+        if loss is None:
+            loss = torch.zeros(1, device="cuda", dtype=torch.float32)
+        if grads is None:
+            grads = [torch.empty_like(x) for x in images]
+        cams = (B.tgs_camera * V)()
+        for v, x in enumerate(images):
+            assert x.dtype == torch.float32 and x.is_contiguous() and x.dim() == 3 and x.shape[0] == 3
+            assert targets[v].shape == x.shape and targets[v].is_contiguous() and grads[v].shape == x.shape
+            cams[v].width, cams[v].height = x.shape[2], x.shape[1]
+        B.check(B.lib.tgs_l1_dssim_loss(self._h, cams, V, _ptr_array(images), _ptr_array(targets),
+                                        float(lam), _p(loss), _ptr_array(grads), _stream()),
+                "tgs_l1_dssim_loss")
+        return loss, grads
+
     # ---- individual steps -----------------------------------------------------------------
 
     def preprocess(self, g: Gaussians, cams):
@@ -316,9 +336,10 @@ class Rasterizer:
 
     def train_step_batched(self, g: Gaussians, cams, targets, grads, stats=None, loss=None,
                            images=None, graph=False, accumulate=False, no_sh_rest=False,
-                           cams_struct=None, fused=True):
+                           cams_struct=None, fused=True, dssim=False):
         flags = ((B.TGS_USE_GRAPH if graph else 0) | (B.TGS_ACCUMULATE if accumulate else 0) |
-                 (B.TGS_NO_SH_REST_GRAD if no_sh_rest else 0) | (0 if fused else B.TGS_UNFUSED))
+                 (B.TGS_NO_SH_REST_GRAD if no_sh_rest else 0) | (0 if fused else B.TGS_UNFUSED) |
+                 (B.TGS_LOSS_DSSIM if dssim else 0))
         camarr = cams_struct if cams_struct is not None else cameras_array(cams)
         B.check(B.lib.tgs_train_step_batched(
             self._h, C.byref(g.struct()), camarr, len(camarr), _ptr_array(targets),
