@@ -353,6 +353,31 @@ def prune_select(scores, fraction):
     return out
 
 
+# ---- compaction (Sec. "Pruning with Volume Masking", Eq. significance-score) ------------------
+
+SCENE_KEYS = ("means", "log_scales", "quats", "opacity_logits", "sh_dc", "sh_rest", "mask_logits",
+              "sh_mask_logits", "sh_degree")
+
+
+def compact(scene, st: Settings, remove=None, masked=True):
+    """The scene without the Gaussians a pruning step removes: those with remove[j] set (e.g.
+    the significance selection) and, when masked, those whose volume mask M_j is 0 (the
+    paper removes masked Gaussians at densification steps). The kept ones stay in order.
+    Returns (scene, kept_index) with kept_index[new] = old index."""
+    n = np.shape(scene["means"])[0]
+    keep = np.ones(n, bool)
+    if remove is not None:
+        keep &= ~np.asarray(remove, bool)
+    if masked and scene.get("mask_logits") is not None:
+        keep &= volume_mask(scene, st) > 0.0
+    idx = np.flatnonzero(keep)
+    out = dict(scene)
+    for k in SCENE_KEYS:
+        if scene.get(k) is not None:
+            out[k] = np.asarray(scene[k])[idx]
+    return out, idx
+
+
 def new_stats(n):
     return dict(accum=np.zeros(n), count=np.zeros(n, np.int32),
                 max_radius=np.zeros(n, np.int32))

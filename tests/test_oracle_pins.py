@@ -801,3 +801,36 @@ def test_prune_selection_rule():
     k = int(math.floor(0.37 * 500))
     ranked = sorted(range(500), key=lambda i: (x[i], i))  # the rule, by plain sorting
     assert set(np.flatnonzero(sel)) == set(ranked[:k])
+
+
+# ---- compaction ----------------------------------------------------------------------------
+
+def test_compact_keeps_order_and_drops_what_is_named():
+    scene = synth.blob_scene(300, 4, 12, log_scale=(-3.0, 0.5), masks=True)
+    st = oracle.Settings(eps_mask=0.5)
+    rng = np.random.default_rng(5)
+    remove = rng.random(300) < 0.3
+    out, idx = oracle.compact(scene, st, remove)
+    # by a plain loop: kept = not removed and mask logit above the float32 threshold
+    tau = np.float32(math.log(0.5 / 0.5))
+    want = [j for j in range(300) if not remove[j] and np.float32(scene["mask_logits"][j]) > tau]
+    assert list(idx) == want
+    for k in oracle.SCENE_KEYS:
+        if scene.get(k) is not None:
+            for new, old in enumerate(want):
+                np.testing.assert_array_equal(out[k][new], scene[k][old])
+    assert oracle.compact(scene, st, None, masked=False)[1].tolist() == list(range(300))
+    assert oracle.compact(scene, st, np.ones(300, bool))[1].size == 0
+
+
+def test_compacting_masked_gaussians_leaves_the_image_unchanged():
+    # a Gaussian with M = 0 has opacity 0 and never blends (the mask equation), so removing it
+    # changes no pixel
+    scene = synth.blob_scene(400, 4, 13, log_scale=(-3.0, 0.5), masks=True)
+    st = oracle.Settings(tile=16, eps_mask=0.5, eps_sh=0.5)
+    cam = synth.ring_cameras(1, [(48, 40)], radius=4.0)[0]
+    out, idx = oracle.compact(scene, st)
+    assert 0 < idx.size < 400
+    a = oracle.render(scene, cam, st)["image"]
+    b = oracle.render(out, cam, st)["image"]
+    np.testing.assert_array_equal(a, b)
