@@ -314,6 +314,26 @@ tgs_status tgs_significance(tgs_ctx *ctx, const tgs_gaussians *g, const uint32_t
 tgs_status tgs_prune_select(tgs_ctx *ctx, const float *scores, int64_t n, double fraction,
                             uint8_t *prune, tgs_stream stream);
 
+/* --- compaction ---------------------------------------------------------------------------- */
+
+#define TGS_COMPACT_MASKED 1u   /* also remove the Gaussians whose volume mask M is 0 */
+
+/* Removes Gaussians from the parameter arrays, keeping the others in their order: those with
+   remove[j] != 0 (remove: device bytes [n], e.g. from tgs_prune_select, or NULL) and, with
+   TGS_COMPACT_MASKED and g->mask_logits given, those whose volume mask is 0 by the same
+   float32 threshold test as the preprocess (Sec. "Pruning with Volume Masking": masked
+   Gaussians are removed at densification steps and every 500 iterations afterwards).
+   out: caller-allocated arrays with room for n Gaussians, in the layouts of tgs_gaussians
+   under the field names of tgs_grads; a NULL field (or a NULL input array) is not copied.
+   sh_degree_out [n] uint8 or NULL. kept_index [n] (device uint32, or NULL) receives, for each
+   new index, the old one -- the gather map for per-Gaussian optimiser state and statistics.
+   The outputs must not overlap the inputs. *n_kept (host) = number kept; the call
+   synchronises the stream once to read it. TGS_ERR_INVALID_ARG for a null ctx, g, out or
+   n_kept or an invalid g. */
+tgs_status tgs_compact(tgs_ctx *ctx, const tgs_gaussians *g, const uint8_t *remove, uint32_t flags,
+                       const tgs_grads *out, uint8_t *sh_degree_out, uint32_t *kept_index,
+                       int64_t *n_kept, tgs_stream stream);
+
 /* --- measurement ------------------------------------------------------------------------ */
 
 /* With profiling on, the batched step records a CUDA event between its stages (also inside

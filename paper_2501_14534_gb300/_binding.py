@@ -28,6 +28,7 @@ TGS_NO_SH_REST_GRAD = 2
 TGS_USE_GRAPH = 4
 TGS_UNFUSED = 8
 TGS_LOSS_DSSIM = 16
+TGS_COMPACT_MASKED = 1
 
 _fp = C.POINTER(C.c_float)
 _vp = C.c_void_p
@@ -90,6 +91,7 @@ SIGNATURES = {
                                  C.c_uint32, _vp]),
     "tgs_l1_loss": (C.c_int32, [_vp, _vp, C.c_int64, C.c_float, _vp, _vp, _vp]),
     "tgs_l1_dssim_loss": (C.c_int32, [_ctx_p, _camp, C.c_int32, _pp, _pp, C.c_float, _vp, _pp, _vp]),
+    "tgs_compact": (C.c_int32, [_ctx_p, _gp, _vp, C.c_uint32, _gradp, _vp, _vp, C.POINTER(C.c_int64), _vp]),
     "tgs_plan": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, C.c_double, C.POINTER(C.c_int64)]),
     "tgs_train_step_batched": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _pp, _pp, _gradp,
                                            _statp, _vp, C.c_uint32, _vp]),

@@ -34,7 +34,7 @@ struct tgs_ctx {
     int device = 0;
     // scratch arena
     Buf splats, radii, tt, dbits, pos, ck0, cv0, ck1, cv1, offsets, tk0, tv0, tk1, tv1, ranges,
-        hist, partials, sgrads, counts, status, pixstate, dimg, images, items, kmask, viskeys, ssim;
+        hist, partials, sgrads, counts, status, pixstate, dimg, images, items, kmask, viskeys, ssim, cbuf;
     uint32_t *h_counts = nullptr;   // pinned host copy of (visible, K)
     // binning kept from the last plain forward
     bool state_valid = false;
@@ -392,7 +392,7 @@ void tgs_destroy(tgs_ctx *c) {
     Buf *bufs[] = {&c->splats, &c->radii, &c->tt, &c->dbits, &c->pos, &c->ck0, &c->cv0, &c->ck1,
                    &c->cv1, &c->offsets, &c->tk0, &c->tv0, &c->tk1, &c->tv1, &c->ranges, &c->hist,
                    &c->partials, &c->sgrads, &c->counts, &c->status, &c->pixstate, &c->dimg,
-                   &c->images, &c->items, &c->kmask, &c->viskeys, &c->ssim};
+                   &c->images, &c->items, &c->kmask, &c->viskeys, &c->ssim, &c->cbuf};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_counts) cudaFreeHost(c->h_counts);
@@ -703,6 +703,26 @@ tgs_status tgs_prune_select(tgs_ctx *c, const float *scores, int64_t n, double f
     TGS_CHECK(cudaMemsetAsync(prune, 0, (size_t)n, st));
     launch_mark(v, (int64_t)std::floor(fraction * (double)n), prune, st);
     c->state_valid = false;
+    return last_error();
+}
+
+tgs_status tgs_compact(tgs_ctx *c, const tgs_gaussians *g, const uint8_t *remove, uint32_t flags,
+                       const tgs_grads *out, uint8_t *sh_degree_out, uint32_t *kept_index, int64_t *n_kept,
+                       tgs_stream stream) {
+    if (!c || !g || !out || !n_kept) return TGS_ERR_INVALID_ARG;
+    GaussPtrs gp;
+    TGS_TRY(make_gauss(c->cfg, g, gp));
+    *n_kept = 0;
+    if (g->n == 0) return TGS_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nb = compact_blocks(g->n);
+    TGS_TRY(ensure(c->cbuf, sizeof(uint32_t) * (size_t)(nb + 1), st));
+    uint32_t *counts = as<uint32_t>(c->cbuf);
+    launch_compact(gp, remove, (flags & TGS_COMPACT_MASKED) != 0, grad_ptrs(out, nullptr, 0), sh_degree_out,
+                   kept_index, counts, counts + nb, st);
+    TGS_CHECK(cudaMemcpyAsync(c->h_counts + 3, counts + nb, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    TGS_CHECK(cudaStreamSynchronize(st));
+    *n_kept = c->h_counts[3];
     return last_error();
 }
 

@@ -217,6 +217,12 @@ int64_t ssim_scratch_floats(const int *W, const int *H, int V);
 void launch_l1_dssim(int V, const int *W, const int *H, const float *const *x, const float *const *y,
                      float *const *grad, float lam, float *scratch, float *loss, cudaStream_t st);
 
+// compact.cu: kept Gaussians (not removed, and M = 1 if masked) copied in order; block_counts:
+// compact_blocks(n) + 1 words of scratch, the last one receiving the number kept
+int64_t compact_blocks(int64_t n);
+void launch_compact(const GaussPtrs &g, const uint8_t *remove, bool masked, const GradPtrs &out, uint8_t *deg_out,
+                    uint32_t *kept_index, uint32_t *block_counts, uint32_t *total, cudaStream_t st);
+
 // significance.cu (Eq. significance-score)
 void launch_volumes(const GaussPtrs &g, float *vol, uint32_t *keys, cudaStream_t st);
 void launch_scores(const GaussPtrs &g, const uint32_t *hits, const float *vol, const uint32_t *sorted_vol_bits,

@@ -347,6 +347,27 @@ class Rasterizer:
             C.byref(self._stats_struct(stats)), _p(loss), flags, _stream()),
             "tgs_train_step_batched")
 
+    # ---- compaction ----
+
+    def compact(self, g: Gaussians, remove=None, masked=True, want_index=True):
+        """The Gaussians that stay after a pruning step, in order: without those marked in
+        remove (uint8 or bool [n] on the device, e.g. prune_select's output) and, if masked,
+        without those whose volume mask is 0. Returns (Gaussians, kept_index or None)."""
+        if remove is not None:
+            assert remove.is_cuda and remove.numel() == g.n and remove.dtype in (torch.uint8, torch.bool)
+            remove = remove.to(torch.uint8).contiguous()
+        out = {k: torch.empty_like(v) for k, v in g.params().items()}
+        deg = torch.empty_like(g.sh_degree) if g.sh_degree is not None else None
+        idx = torch.empty(g.n, device="cuda", dtype=torch.int32) if want_index else None
+        n_kept = C.c_int64(0)
+        B.check(B.lib.tgs_compact(self._h, C.byref(g.struct()), _p(remove),
+                                  B.TGS_COMPACT_MASKED if masked else 0, C.byref(self._grad_struct(out)),
+                                  _p(deg), _p(idx), C.byref(n_kept), _stream()), "tgs_compact")
+        k = int(n_kept.value)
+        kept = Gaussians(**{name: t[:k] for name, t in out.items()},
+                         sh_degree=deg[:k] if deg is not None else None, sh_degree_max=g.sh_degree_max)
+        return kept, (idx[:k] if idx is not None else None)
+
     # ---- significance pruning (Eq. significance-score) ----
 
     def count_hits(self, g: Gaussians, cams, hit_count=None):
