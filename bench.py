@@ -420,6 +420,17 @@ def main():
     p1.record()
     torch.cuda.synchronize()
     render_fps = V / (p0.elapsed_time(p1) / 1000.0)
+    # the same render from FP16 parameter storage (the paper's post-processing)
+    gh = R.Rasterizer.to_half(g)
+    for v in range(min(V, 3)):
+        plain.forward(gh, [cams[v]])
+    p0.record()
+    for v in range(V):
+        plain.forward(gh, [cams[v]])
+    p1.record()
+    torch.cuda.synchronize()
+    render_fps_fp16 = V / (p0.elapsed_time(p1) / 1000.0)
+    del gh
 
     # algorithmic work of the blend stages: pairs examined per pixel (forward) and pairs up to
     # the last contributor (backward), from a forward with per-pixel counters at the tile size
@@ -472,7 +483,7 @@ def main():
                        "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (252 MB params)"},
             "e2e": {"value": e2e_value, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms},
-            "plain_views_per_s": plain_vps, "render_fps": render_fps,
+            "plain_views_per_s": plain_vps, "render_fps": render_fps, "render_fps_fp16_params": render_fps_fp16,
             "unfused_views_per_s": unfused, "l1_dssim_step": dssim,
             "speedup_vs_plain": value / world / plain_vps,
             "stage_ms": stage_ms,

@@ -112,10 +112,16 @@ typedef struct {
     int32_t reserved0;
 } tgs_config;
 
+#define TGS_PARAM_F32 0         /* parameter arrays hold float32 */
+#define TGS_PARAM_F16 1         /* parameter arrays hold IEEE half (FP16 storage; render path only) */
+
 typedef struct {
     int64_t n;                   /* number of Gaussians */
     int32_t sh_degree_max;       /* 0..3; rest bands above it are not read */
-    int32_t reserved;
+    int32_t param_dtype;         /* TGS_PARAM_F32 (0) or TGS_PARAM_F16: every float array below
+                                    then holds halves of the same shape; accepted by
+                                    tgs_preprocess, tgs_forward and tgs_count_hits, the other
+                                    calls return TGS_ERR_NOT_SUPPORTED */
     const float *means;          /* [n,3] */
     const float *log_scales;     /* [n,3] */
     const float *quats;          /* [n,4] */
@@ -313,6 +319,22 @@ tgs_status tgs_significance(tgs_ctx *ctx, const tgs_gaussians *g, const uint32_t
    scores [n] device float, non-negative. fraction in [0, 1]. Asynchronous. */
 tgs_status tgs_prune_select(tgs_ctx *ctx, const float *scores, int64_t n, double fraction,
                             uint8_t *prune, tgs_stream stream);
+
+/* --- FP16 storage -------------------------------------------------------------------------- */
+
+/* Half-precision copies of the parameter arrays (device, same shapes as tgs_gaussians). */
+typedef struct {
+    uint16_t *means, *log_scales, *quats, *opacity_logits, *sh_dc, *sh_rest, *mask_logits,
+        *sh_mask_logits; /* NULL = not wanted */
+} tgs_half_params;
+
+/* The paper's post-processing (Sec. "Experiments", setup): every Gaussian parameter stored
+   with 16-bit precision after training. Writes each float32 array of g (param_dtype
+   TGS_PARAM_F32) rounded to the nearest IEEE half, ties to even, values beyond the half range
+   to +-inf; sh_degree stays uint8. Render from it with param_dtype = TGS_PARAM_F16: the
+   preprocess widens each half to float32 exactly, so the images equal those of the float32
+   path on the rounded values, bit for bit. Asynchronous. */
+tgs_status tgs_params_to_half(const tgs_gaussians *g, const tgs_half_params *out, tgs_stream stream);
 
 /* --- compaction ---------------------------------------------------------------------------- */
 

@@ -378,6 +378,19 @@ def compact(scene, st: Settings, remove=None, masked=True):
     return out, idx
 
 
+# ---- FP16 storage (Sec. "Experiments", setup: parameters kept as 16-bit halves after training) --
+
+def to_half(scene):
+    """Every float parameter rounded to the nearest IEEE binary16 (ties to even, numpy's
+    conversion), widened back exactly; the render of FP16 storage is the render of this."""
+    out = dict(scene)
+    with np.errstate(over="ignore"):   # beyond the half range: +-inf, by definition
+        for k in SCENE_KEYS:
+            if k != "sh_degree" and scene.get(k) is not None:
+                out[k] = np.asarray(scene[k], np.float32).astype(np.float16).astype(np.float32)
+    return out
+
+
 def new_stats(n):
     return dict(accum=np.zeros(n), count=np.zeros(n, np.int32),
                 max_radius=np.zeros(n, np.int32))

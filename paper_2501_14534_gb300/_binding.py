@@ -29,6 +29,8 @@ TGS_USE_GRAPH = 4
 TGS_UNFUSED = 8
 TGS_LOSS_DSSIM = 16
 TGS_COMPACT_MASKED = 1
+TGS_PARAM_F32 = 0
+TGS_PARAM_F16 = 1
 
 _fp = C.POINTER(C.c_float)
 _vp = C.c_void_p
@@ -42,7 +44,7 @@ class tgs_config(C.Structure):
 
 
 class tgs_gaussians(C.Structure):
-    _fields_ = [("n", C.c_int64), ("sh_degree_max", C.c_int32), ("reserved", C.c_int32),
+    _fields_ = [("n", C.c_int64), ("sh_degree_max", C.c_int32), ("param_dtype", C.c_int32),
                 ("means", _vp), ("log_scales", _vp), ("quats", _vp), ("opacity_logits", _vp),
                 ("sh_dc", _vp), ("sh_rest", _vp), ("sh_degree", _vp), ("mask_logits", _vp),
                 ("sh_mask_logits", _vp)]
@@ -70,6 +72,11 @@ class tgs_stats(C.Structure):
 
 _ctx_p = C.c_void_p
 _cfgp = C.POINTER(tgs_config)
+class tgs_half_params(C.Structure):
+    _fields_ = [(k, _vp) for k in ("means", "log_scales", "quats", "opacity_logits", "sh_dc", "sh_rest",
+                                   "mask_logits", "sh_mask_logits")]
+
+
 _gp = C.POINTER(tgs_gaussians)
 _camp = C.POINTER(tgs_camera)
 _outp = C.POINTER(tgs_view_out)
@@ -91,6 +98,7 @@ SIGNATURES = {
                                  C.c_uint32, _vp]),
     "tgs_l1_loss": (C.c_int32, [_vp, _vp, C.c_int64, C.c_float, _vp, _vp, _vp]),
     "tgs_l1_dssim_loss": (C.c_int32, [_ctx_p, _camp, C.c_int32, _pp, _pp, C.c_float, _vp, _pp, _vp]),
+    "tgs_params_to_half": (C.c_int32, [_gp, C.POINTER(tgs_half_params), _vp]),
     "tgs_compact": (C.c_int32, [_ctx_p, _gp, _vp, C.c_uint32, _gradp, _vp, _vp, C.POINTER(C.c_int64), _vp]),
     "tgs_plan": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, C.c_double, C.POINTER(C.c_int64)]),
     "tgs_train_step_batched": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _pp, _pp, _gradp,

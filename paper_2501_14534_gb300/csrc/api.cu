@@ -145,8 +145,10 @@ tgs_status make_batch(const tgs_config &cfg, const tgs_camera *cams, int V, CamB
 
 float logit_threshold(float eps) { return (float)std::log((double)eps / (1.0 - (double)eps)); }
 
-tgs_status make_gauss(const tgs_config &cfg, const tgs_gaussians *g, GaussPtrs &gp) {
+tgs_status make_gauss(const tgs_config &cfg, const tgs_gaussians *g, GaussPtrs &gp, bool allow_half = false) {
     if (!g || g->n < 0) return TGS_ERR_INVALID_ARG;
+    if (g->param_dtype != TGS_PARAM_F32 && g->param_dtype != TGS_PARAM_F16) return TGS_ERR_INVALID_ARG;
+    if (g->param_dtype == TGS_PARAM_F16 && !allow_half) return TGS_ERR_NOT_SUPPORTED;
     // an empty scene may come with null pointers
     if (g->n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh_dc))
         return TGS_ERR_INVALID_ARG;
@@ -168,6 +170,7 @@ tgs_status make_gauss(const tgs_config &cfg, const tgs_gaussians *g, GaussPtrs &
     gp.tau_sh = logit_threshold(cfg.eps_sh);
     gp.support = cfg.support;
     gp.near_z = cfg.near_plane;
+    gp.half = g->param_dtype == TGS_PARAM_F16 ? 1 : 0;
     return TGS_OK;
 }
 
@@ -463,7 +466,7 @@ tgs_status tgs_preprocess(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *
     CamBatch cb;
     GaussPtrs gp;
     TGS_TRY(make_batch(c->cfg, cams, V, cb));
-    TGS_TRY(make_gauss(c->cfg, g, gp));
+    TGS_TRY(make_gauss(c->cfg, g, gp, true));
     const int64_t nt = g->n * V;
     TGS_TRY(ensure(c->tt, sizeof(uint32_t) * (size_t)nt, st));
     TGS_TRY(ensure(c->dbits, sizeof(uint32_t) * (size_t)nt, st));
@@ -596,7 +599,7 @@ tgs_status tgs_forward(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cam
     if (!c || !outs || !cams || V <= 0) return TGS_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     GaussPtrs gp;
-    TGS_TRY(make_gauss(c->cfg, g, gp));
+    TGS_TRY(make_gauss(c->cfg, g, gp, true));
     for (int v = 0; v < V; v++) {
         if (!outs[v].image) return TGS_ERR_INVALID_ARG;
         CamBatch cb;
@@ -653,7 +656,7 @@ tgs_status tgs_count_hits(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *
     if (g->n == 0) return TGS_OK;
     cudaStream_t st = (cudaStream_t)stream;
     GaussPtrs gp;
-    TGS_TRY(make_gauss(c->cfg, g, gp));
+    TGS_TRY(make_gauss(c->cfg, g, gp, true));
     for (int v = 0; v < V; v++) {
         CamBatch cb;
         uint32_t *ids = nullptr;
@@ -703,6 +706,21 @@ tgs_status tgs_prune_select(tgs_ctx *c, const float *scores, int64_t n, double f
     TGS_CHECK(cudaMemsetAsync(prune, 0, (size_t)n, st));
     launch_mark(v, (int64_t)std::floor(fraction * (double)n), prune, st);
     c->state_valid = false;
+    return last_error();
+}
+
+tgs_status tgs_params_to_half(const tgs_gaussians *g, const tgs_half_params *out, tgs_stream stream) {
+    if (!g || !out || g->n < 0 || g->param_dtype != TGS_PARAM_F32) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = g->n;
+    launch_to_half(g->means, out->means, 3 * n, st);
+    launch_to_half(g->log_scales, out->log_scales, 3 * n, st);
+    launch_to_half(g->quats, out->quats, 4 * n, st);
+    launch_to_half(g->opacity_logits, out->opacity_logits, n, st);
+    launch_to_half(g->sh_dc, out->sh_dc, 3 * n, st);
+    launch_to_half(g->sh_rest, out->sh_rest, 45 * n, st);
+    launch_to_half(g->mask_logits, out->mask_logits, n, st);
+    launch_to_half(g->sh_mask_logits, out->sh_mask_logits, 3 * n, st);
     return last_error();
 }
 

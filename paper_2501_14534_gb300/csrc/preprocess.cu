@@ -6,6 +6,10 @@
 // Sigma'^-1, radius, inclusive pixel rect, tiles touched, and the colour from SH with
 // straight-through band masks (Eq. sh-masks). Backward: the chain rule from the splat
 // gradient records to every input, plus the 2D-mean gradient-norm statistics.
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "tgs_internal.cuh"
 
 namespace tgs {
@@ -105,27 +109,38 @@ struct GaussState {
     bool ok;
 };
 
+// A parameter value: float32, or IEEE half widened to float32 (the FP16 storage of trained
+// scenes, read by the render path only).
+template <typename T>
+__device__ __forceinline__ float ldp(const float *p, int64_t k) {
+    if constexpr (std::is_same<T, __half>::value) return __half2float(reinterpret_cast<const __half *>(p)[k]);
+    else return p[k];
+}
+
+template <typename T = float>
 __device__ __forceinline__ GaussState load_state(const GaussPtrs &g, int64_t i) {
     GaussState s;
     s.M = 1.f;
-    if (g.mask) s.M = (g.mask[i] > g.tau_m) ? 1.f : 0.f;
+    if (g.mask) s.M = (ldp<T>(g.mask, i) > g.tau_m) ? 1.f : 0.f;
     s.deg = g.deg_max;
     if (g.sh_degree) s.deg = min(s.deg, (int)g.sh_degree[i]);
     s.band[0] = true;
 #pragma unroll
     for (int l = 1; l <= 3; l++) {
         bool on = l <= s.deg;
-        if (g.shmask) on = on && (g.shmask[3 * i + l - 1] > g.tau_sh);
+        if (g.shmask) on = on && (ldp<T>(g.shmask, 3 * i + l - 1) > g.tau_sh);
         s.band[l] = on;
     }
-    s.mu = make_float3(g.means[3 * i], g.means[3 * i + 1], g.means[3 * i + 2]);
-    float ls0 = g.log_scales[3 * i], ls1 = g.log_scales[3 * i + 1], ls2 = g.log_scales[3 * i + 2];
+    s.mu = make_float3(ldp<T>(g.means, 3 * i), ldp<T>(g.means, 3 * i + 1), ldp<T>(g.means, 3 * i + 2));
+    float ls0 = ldp<T>(g.log_scales, 3 * i), ls1 = ldp<T>(g.log_scales, 3 * i + 1),
+          ls2 = ldp<T>(g.log_scales, 3 * i + 2);
     s.scale[0] = s.M * expf(ls0);
     s.scale[1] = s.M * expf(ls1);
     s.scale[2] = s.M * expf(ls2);
-    s.sig_o = sigmoidf_(g.opac[i]);
+    s.sig_o = sigmoidf_(ldp<T>(g.opac, i));
     s.op = s.M * s.sig_o;
-    float4 q = make_float4(g.quats[4 * i], g.quats[4 * i + 1], g.quats[4 * i + 2], g.quats[4 * i + 3]);
+    float4 q = make_float4(ldp<T>(g.quats, 4 * i), ldp<T>(g.quats, 4 * i + 1), ldp<T>(g.quats, 4 * i + 2),
+                            ldp<T>(g.quats, 4 * i + 3));
     float qq = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
     s.qnorm = sqrtf(qq);
     float inv = 1.f / s.qnorm;
@@ -206,14 +221,16 @@ struct ShCoeffs {
     float3 f[16];
 };
 
+template <typename T = float>
 __device__ __forceinline__ void load_sh(const GaussPtrs &g, int64_t i, const GaussState &s,
                                         ShCoeffs &sh) {
-    sh.f[0] = make_float3(g.sh_dc[3 * i], g.sh_dc[3 * i + 1], g.sh_dc[3 * i + 2]);
-    const float *r = g.sh_rest ? g.sh_rest + 45 * i : nullptr;
+    sh.f[0] = make_float3(ldp<T>(g.sh_dc, 3 * i), ldp<T>(g.sh_dc, 3 * i + 1), ldp<T>(g.sh_dc, 3 * i + 2));
+    const int64_t r = 45 * i;
 #pragma unroll
     for (int k = 1; k < 16; k++) {
-        if (r && s.deg >= band_of(k))
-            sh.f[k] = make_float3(r[3 * (k - 1)], r[3 * (k - 1) + 1], r[3 * (k - 1) + 2]);
+        if (g.sh_rest && s.deg >= band_of(k))
+            sh.f[k] = make_float3(ldp<T>(g.sh_rest, r + 3 * (k - 1)), ldp<T>(g.sh_rest, r + 3 * (k - 1) + 1),
+                                  ldp<T>(g.sh_rest, r + 3 * (k - 1) + 2));
         else
             sh.f[k] = make_float3(0.f, 0.f, 0.f);
     }
@@ -237,6 +254,7 @@ __device__ __forceinline__ float3 sh_raw(const GaussState &s, const ShCoeffs &sh
 // shared memory as one contiguous run per warp: full-sector stores instead of four 16-byte
 // pieces per 64-byte record from each thread. Records of Gaussians not visible in a view
 // hold zeros; nothing reads them.
+template <typename T>
 __global__ void __launch_bounds__(128) k_preprocess(GaussPtrs g, const __grid_constant__ CamBatch cb,
                                                     float4 *__restrict__ splats,
                                                     int32_t *__restrict__ radii,
@@ -253,10 +271,10 @@ __global__ void __launch_bounds__(128) k_preprocess(GaussPtrs g, const __grid_co
     const bool inb = i0 < n;
     const int64_t i = inb ? i0 : wfirst;
     const int wn = (int)min((int64_t)32, n - wfirst);  // Gaussians of this warp
-    GaussState s = load_state(g, i);
+    GaussState s = load_state<T>(g, i);
     if (!inb) s.ok = false;
     ShCoeffs sh;
-    if (s.ok) load_sh(g, i, s, sh);
+    if (s.ok) load_sh<T>(g, i, s, sh);
     for (int v = 0; v < cb.V; v++) {
         const DevCam &c = cb.c[v];
         const int64_t r = (int64_t)v * n + i;
@@ -655,8 +673,12 @@ void launch_preprocess(const GaussPtrs &g, const CamBatch &cb, float4 *splats, i
     const int bs = 128;
     const int64_t grid = (g.n + bs - 1) / bs;
     count_launch();
-    k_preprocess<<<(unsigned)grid, bs, 0, st>>>(g, cb, splats, radii, tiles_touched, depth_bits,
-                                                 reinterpret_cast<float4 *>(zero_grads));
+    if (g.half)
+        k_preprocess<__half><<<(unsigned)grid, bs, 0, st>>>(g, cb, splats, radii, tiles_touched, depth_bits,
+                                                            reinterpret_cast<float4 *>(zero_grads));
+    else
+        k_preprocess<float><<<(unsigned)grid, bs, 0, st>>>(g, cb, splats, radii, tiles_touched, depth_bits,
+                                                           reinterpret_cast<float4 *>(zero_grads));
 }
 
 void launch_preprocess_backward(const GaussPtrs &g, const CamBatch &cb, const float4 *sgrads,

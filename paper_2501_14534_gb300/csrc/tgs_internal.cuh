@@ -47,6 +47,7 @@ struct GaussPtrs {
     float tau_m, tau_sh;   // thresholds on the logits
     int support;
     float near_z;
+    int half;              // parameters stored as IEEE half (render path only)
 };
 
 struct GradPtrs {
@@ -216,6 +217,9 @@ void launch_fused_l1(int tile, int ppt, const float4 *splats, const uint32_t *id
 int64_t ssim_scratch_floats(const int *W, const int *H, int V);
 void launch_l1_dssim(int V, const int *W, const int *H, const float *const *x, const float *const *y,
                      float *const *grad, float lam, float *scratch, float *loss, cudaStream_t st);
+
+// half.cu: float32 -> IEEE half, round to nearest even (n values)
+void launch_to_half(const float *src, uint16_t *dst, int64_t n, cudaStream_t st);
 
 // compact.cu: kept Gaussians (not removed, and M = 1 if masked) copied in order; block_counts:
 // compact_blocks(n) + 1 words of scratch, the last one receiving the number kept

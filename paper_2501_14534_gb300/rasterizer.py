@@ -57,14 +57,21 @@ class Gaussians:
     def n(self):
         return self.means.shape[0]
 
+    @property
+    def half(self):
+        """FP16 storage: every parameter array holds float16 (render path only)."""
+        return self.means.dtype == torch.float16
+
     def struct(self):
+        dt = torch.float16 if self.half else torch.float32
         for k in PARAM_KEYS:
-            _check_tensor(getattr(self, k), k)
+            _check_tensor(getattr(self, k), k, dt)
         _check_tensor(self.sh_degree, "sh_degree", torch.uint8)
         deg = self.sh_degree_max
         if deg is None:
             deg = 3 if self.sh_rest is not None else 0
-        return B.tgs_gaussians(self.n, deg, 0, _p(self.means), _p(self.log_scales),
+        return B.tgs_gaussians(self.n, deg, B.TGS_PARAM_F16 if self.half else B.TGS_PARAM_F32,
+                               _p(self.means), _p(self.log_scales),
                                _p(self.quats), _p(self.opacity_logits), _p(self.sh_dc),
                                _p(self.sh_rest), _p(self.sh_degree), _p(self.mask_logits),
                                _p(self.sh_mask_logits))
@@ -346,6 +353,17 @@ class Rasterizer:
             _ptr_array(images) if images is not None else None, C.byref(self._grad_struct(grads)),
             C.byref(self._stats_struct(stats)), _p(loss), flags, _stream()),
             "tgs_train_step_batched")
+
+    # ---- FP16 storage ----
+
+    @staticmethod
+    def to_half(g: Gaussians):
+        """The Gaussians with every parameter rounded to IEEE half (ties to even), for
+        rendering from FP16 storage."""
+        out = {k: torch.empty(v.shape, device="cuda", dtype=torch.float16) for k, v in g.params().items()}
+        hp = B.tgs_half_params(*[_p(out.get(k)) for k in PARAM_KEYS])
+        B.check(B.lib.tgs_params_to_half(C.byref(g.struct()), C.byref(hp), _stream()), "tgs_params_to_half")
+        return Gaussians(**out, sh_degree=g.sh_degree, sh_degree_max=g.sh_degree_max)
 
     # ---- compaction ----
 

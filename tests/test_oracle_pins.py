@@ -834,3 +834,15 @@ def test_compacting_masked_gaussians_leaves_the_image_unchanged():
     a = oracle.render(scene, cam, st)["image"]
     b = oracle.render(out, cam, st)["image"]
     np.testing.assert_array_equal(a, b)
+
+
+# ---- FP16 storage ---------------------------------------------------------------------------
+
+def test_half_rounding_is_ieee_nearest_even():
+    # binary16: 10 fraction bits, max 65504, smallest subnormal 2^-24
+    x = np.array([1.0 / 3.0, 65504.0, 65519.0, 65520.0, 2.0 ** -24, 2.0 ** -26, 1.0 + 2.0 ** -11,
+                  1.0 + 3.0 * 2.0 ** -11, -2.5, 1e-8], np.float64)
+    want = [0.333251953125, 65504.0, 65504.0, np.inf, 2.0 ** -24, 0.0, 1.0, 1.0 + 2.0 ** -9, -2.5, 0.0]
+    scene = {"means": x.reshape(-1, 1)}
+    got = oracle.to_half(scene)["means"].reshape(-1)
+    np.testing.assert_array_equal(got.astype(np.float64), want)
