@@ -508,11 +508,26 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_colour(GaussPtrs
                                                         const float4 *__restrict__ sgrads,
                                                         const int32_t *__restrict__ radii,
                                                         GradPtrs out, int no_sh_rest) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
+    // a warp's 32 Gaussians have consecutive rows of 45 SH rest coefficients: the rows come in
+    // and the gradients go out as one contiguous run per warp through shared memory (stride 45,
+    // odd: each thread reads its own row without bank conflicts)
+    constexpr int kRest = 45;
+    __shared__ float s_rows[kBwdThreads / 32][32 * kRest];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t n = g.n;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t wfirst = i0 - lane;
+    if (wfirst >= n) return;  // the whole warp is past the end
+    const bool inb = i0 < n;
+    const int64_t i = inb ? i0 : wfirst;
+    const int wn = (int)min((int64_t)32, n - wfirst);
+    float *rows = s_rows[w];
+    if (g.sh_rest)
+        for (int u = lane; u < kRest * wn; u += 32) rows[u] = g.sh_rest[kRest * wfirst + u];
+    __syncwarp();
     const float *rec = reinterpret_cast<const float *>(sgrads);  // 12 floats per (view, Gaussian)
     GaussState s = load_state(g, i);
+    if (!inb) s.ok = false;
     ShCoeffs sh;
     float3 g_mu = make_float3(0.f, 0.f, 0.f);
     float3 g_f[16];
@@ -524,7 +539,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_colour(GaussPtrs
 #pragma unroll 8
         for (int v = 0; v < cb.V; v++)
             if (radii[(int64_t)v * n + i] > 0) vis |= 1ull << v;
-        load_sh(g, i, s, sh);
+        sh.f[0] = make_float3(g.sh_dc[3 * i], g.sh_dc[3 * i + 1], g.sh_dc[3 * i + 2]);
+#pragma unroll
+        for (int k = 1; k < 16; k++) {
+            const float *r = rows + kRest * lane + 3 * (k - 1);
+            sh.f[k] = (g.sh_rest && s.deg >= band_of(k)) ? make_float3(r[0], r[1], r[2]) : make_float3(0.f, 0.f, 0.f);
+        }
         float3 nrgb = make_float3(0.f, 0.f, 0.f);
         if (vis & 1ull) nrgb = make_float3(rec[12 * i + 6], rec[12 * i + 7], rec[12 * i + 8]);
         for (int v = 0; v < cb.V; v++) {
@@ -575,20 +595,26 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_colour(GaussPtrs
             const float sm = sigmoidf_(g.shmask[3 * i + l - 1]);
             g_shm[l - 1] = g_band[l] * sm * (1.f - sm);
         }
+    if (out.sh_rest && !no_sh_rest) {
+        __syncwarp();  // every thread has read its own row
+#pragma unroll
+        for (int k = 1; k < 16; k++) {
+            float *r = rows + kRest * lane + 3 * (k - 1);
+            r[0] = g_f[k].x;
+            r[1] = g_f[k].y;
+            r[2] = g_f[k].z;
+        }
+        __syncwarp();
+        float *dst = out.sh_rest + kRest * wfirst;
+        for (int u = lane; u < kRest * wn; u += 32) dst[u] = acc ? dst[u] + rows[u] : rows[u];
+    }
+    if (!inb) return;  // a lane past the end holds another Gaussian's index
     out_write(out.means, 3 * i + 0, g_mu.x, acc);
     out_write(out.means, 3 * i + 1, g_mu.y, acc);
     out_write(out.means, 3 * i + 2, g_mu.z, acc);
     out_write(out.sh_dc, 3 * i + 0, g_f[0].x, acc);
     out_write(out.sh_dc, 3 * i + 1, g_f[0].y, acc);
     out_write(out.sh_dc, 3 * i + 2, g_f[0].z, acc);
-    if (out.sh_rest && !no_sh_rest) {
-#pragma unroll
-        for (int k = 1; k < 16; k++) {
-            out_write(out.sh_rest, 45 * i + 3 * (k - 1) + 0, g_f[k].x, acc);
-            out_write(out.sh_rest, 45 * i + 3 * (k - 1) + 1, g_f[k].y, acc);
-            out_write(out.sh_rest, 45 * i + 3 * (k - 1) + 2, g_f[k].z, acc);
-        }
-    }
 #pragma unroll
     for (int l = 0; l < 3; l++) out_write(out.shmask, 3 * i + l, g_shm[l], acc);
 }
