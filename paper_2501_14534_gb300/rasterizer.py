@@ -407,6 +407,13 @@ class Rasterizer:
                                        _p(scores), _stream()), "tgs_significance")
         return scores
 
+    @staticmethod
+    def pruning_fractions(rounds=6, first=0.6, decay=0.7):
+        """Fraction of the Gaussians each significance pruning round removes: the first rate
+        decayed by a constant factor per round (Sec. "Implementation details": 6 rounds, 60 %
+        first, decay 0.7)."""
+        return [first * decay ** k for k in range(rounds)]
+
     def prune_select(self, scores, fraction):
         """bool [n]: the floor(fraction n) lowest scores (equal scores: lower index first)."""
         scores = scores.contiguous()
