@@ -44,9 +44,9 @@ ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 # 2 px/thread, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; the command
 # is in profiles/k_fused_l1_300k_8x1280x832_tile32_ppt2.md). Reported only while the kernel's
 # sources and the code that launches it are the ones measured (their sha256 below), else null.
-FUSED_TRAFFIC = {"bytes": 759252224 + 277401344, "tile": 32, "ppt": 2,
+FUSED_TRAFFIC = {"bytes": 718457344 + 96854016, "tile": 32, "ppt": 2,
                  "sources": ("fused.cu", "blend_common.cuh", "tgs_internal.cuh", "api.cu"),
-                 "sha256": "d6c1468a1fab921847158d5ab68cac28864fc90c9d637b569d8cbd54ce01b0b0"}
+                 "sha256": "cc74fd57e338fde486bf9de8879cbab239d673303cfc183c29aeb7391ca3219f"}
 
 
 def fused_traffic(cfg, n, views):
