@@ -73,6 +73,8 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--tile", type=int, default=16)
     p.add_argument("--ppt", type=int, default=1)
+    p.add_argument("--pruning-round", action="store_true",
+                   help="also time a significance pruning round (hits, score, selection, compaction)")
     p.add_argument("--step-only", action="store_true",
                    help="stop after the timed batched steps (for launch lists under a profiler)")
     return p.parse_args()
@@ -435,34 +437,35 @@ def main():
     # ---- a significance pruning round on the same scene (Eq. significance-score): ray hits
     # over the views, score, selection of the lowest 60 %, compaction of every parameter array
     pruning = None
-    try:
-        def prune_round():
-            # each stage bracketed by events with the device idle before it, so that a gap on
-            # the host (a first launch, an allocation) is not counted as device time
-            ms = []
-            out = []
-            stages = [lambda: plain.count_hits(g, cams), lambda: plain.significance(g, out[0], 0.9),
-                      lambda: plain.prune_select(out[1], 0.6), lambda: plain.compact(g, out[2], masked=True)[0]]
-            for f in stages:
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                out.append(f())
-                e1.record()
-                torch.cuda.synchronize()
-                ms.append(e0.elapsed_time(e1))
-            return ms, out[3]
+    if args.pruning_round:
+        try:
+            def prune_round():
+                # each stage bracketed by events with the device idle before it, so that a gap on
+                # the host (a first launch, an allocation) is not counted as device time
+                ms = []
+                out = []
+                stages = [lambda: plain.count_hits(g, cams), lambda: plain.significance(g, out[0], 0.9),
+                          lambda: plain.prune_select(out[1], 0.6), lambda: plain.compact(g, out[2], masked=True)[0]]
+                for f in stages:
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    out.append(f())
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                return ms, out[3]
 
-        prune_round()   # first launches and buffer growth, untimed
-        ms, kept = prune_round()
-        # kept rows read and written, index map written, removal flag and mask logit read
-        moved = 2 * kept.n * 252 + 4 * kept.n + 5 * g.n
-        pruning = {"gaussians": g.n, "kept": kept.n, "count_hits_ms": ms[0], "significance_ms": ms[1],
-                   "prune_select_ms": ms[2], "compact_ms": ms[3],
-                   "compact_GBps": moved / ms[3] / 1e6}
-        del kept
-    except Exception as e:  # reported, not fatal
-        print(f"[bench] pruning round failed: {e}", file=sys.stderr)
+            prune_round()   # first launches and buffer growth, untimed
+            ms, kept = prune_round()
+            # kept rows read and written, index map written, removal flag and mask logit read
+            moved = 2 * kept.n * 252 + 4 * kept.n + 5 * g.n
+            pruning = {"gaussians": g.n, "kept": kept.n, "count_hits_ms": ms[0], "significance_ms": ms[1],
+                       "prune_select_ms": ms[2], "compact_ms": ms[3],
+                       "compact_GBps": moved / ms[3] / 1e6}
+            del kept
+        except Exception as e:  # reported, not fatal
+            print(f"[bench] pruning round failed: {e}", file=sys.stderr)
 
     # algorithmic work of the blend stages: pairs examined per pixel (forward) and pairs up to
     # the last contributor (backward), from a forward with per-pixel counters at the tile size
