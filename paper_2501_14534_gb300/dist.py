@@ -30,7 +30,8 @@ def reduce_max(x: float, device="cpu") -> float:
 
 def allreduce_grads(grads: dict, stats: dict | None = None, views_per_rank=None):
     """Sums the gradient tensors over ranks in place, and the statistics (gradient-norm
-    accumulator and visibility count summed, max radius maxed).
+    accumulator, visibility count and ray hits of the significance score summed, max radius
+    maxed).
 
     With a loss that is a mean over the views of the whole step, each rank's gradients are
     already weighted by 1/(total views); pass ``views_per_rank`` = (this rank's views, total
@@ -49,7 +50,7 @@ def allreduce_grads(grads: dict, stats: dict | None = None, views_per_rank=None)
             t.mul_(scale)
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
     if stats:
-        for k in ("grad_norm_accum", "vis_count"):
+        for k in ("grad_norm_accum", "vis_count", "hit_count"):
             if stats.get(k) is not None:
                 dist.all_reduce(stats[k], op=dist.ReduceOp.SUM)
         if stats.get("max_radius") is not None:

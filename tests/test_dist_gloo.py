@@ -27,13 +27,15 @@ def _worker(rank, world, port, out):
     grads = {"means": torch.full((n, 3), float(rank + 1)), "opacity_logits": torch.arange(n, dtype=torch.float32) * (rank + 1)}
     stats = {"grad_norm_accum": torch.full((n,), 0.5 * (rank + 1)),
              "vis_count": torch.full((n,), rank + 1, dtype=torch.int32),
-             "max_radius": torch.tensor([3, 9, 1, 7, 2], dtype=torch.int32) * (1 + rank * (torch.arange(n) % 2))}
+             "max_radius": torch.tensor([3, 9, 1, 7, 2], dtype=torch.int32) * (1 + rank * (torch.arange(n) % 2)),
+             "hit_count": torch.arange(n, dtype=torch.int32) * (10 + rank)}
     dist.allreduce_grads(grads, stats)
     res["means"] = grads["means"].tolist()
     res["op"] = grads["opacity_logits"].tolist()
     res["acc"] = stats["grad_norm_accum"].tolist()
     res["cnt"] = stats["vis_count"].tolist()
     res["maxr"] = stats["max_radius"].tolist()
+    res["hits"] = stats["hit_count"].tolist()
     g2 = {"x": torch.ones(3)}
     dist.allreduce_grads(g2, None, views_per_rank=(3 if rank == 0 else 1, 4))
     res["scaled"] = g2["x"].tolist()
@@ -62,4 +64,5 @@ def test_two_gloo_ranks_reduce_grads_stats_and_times():
         assert r["acc"] == [1.5] * 5
         assert r["cnt"] == [3] * 5
         assert r["maxr"] == [3, 18, 1, 14, 2]
+        assert r["hits"] == [0, 21, 42, 63, 84]                           # k (10 + 11)
         assert r["scaled"] == [1.0] * 3                                   # 3/4 + 1/4
