@@ -97,3 +97,34 @@ def test_loss_weights_and_view_mean():
     ls, _ = oracle.l1_dssim(imgs, tgts, 1.0)
     ref = np.mean([1.0 - oracle.ssim_maps(i, t)[0].mean() for i, t in zip(imgs, tgts)])
     assert math.isclose(ls, ref, rel_tol=1e-12)
+
+
+def test_ssim_map_equals_brute_force_per_pixel():
+    # every output pixel summed tap by tap from the definition, with its own window weights
+    rng = np.random.default_rng(6)
+    H, W = 7, 9
+    x = rng.random((2, H, W))
+    y = rng.random((2, H, W))
+    g1 = [math.exp(-(t * t) / (2 * 1.5 ** 2)) for t in range(-5, 6)]
+    z = sum(a * b for a in g1 for b in g1)
+    C1, C2 = 0.01 ** 2, 0.03 ** 2
+    S, _ = oracle.ssim_maps(x, y)
+    for c in range(2):
+        for py in range(H):
+            for px in range(W):
+                mx = my = exx = eyy = exy = 0.0
+                for i in range(-5, 6):
+                    for j in range(-5, 6):
+                        qy, qx = py + i, px + j
+                        if not (0 <= qy < H and 0 <= qx < W):
+                            continue
+                        wgt = g1[i + 5] * g1[j + 5] / z
+                        a, b = x[c, qy, qx], y[c, qy, qx]
+                        mx += wgt * a
+                        my += wgt * b
+                        exx += wgt * a * a
+                        eyy += wgt * b * b
+                        exy += wgt * a * b
+                vx, vy, cov = exx - mx * mx, eyy - my * my, exy - mx * my
+                ref = ((2 * mx * my + C1) * (2 * cov + C2)) / ((mx * mx + my * my + C1) * (vx + vy + C2))
+                assert abs(S[c, py, px] - ref) < 1e-12, (c, py, px)
