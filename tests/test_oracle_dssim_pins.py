@@ -1,6 +1,7 @@
 """Pins of the oracle's L1 + D-SSIM loss (Eq. loss3dgs) to things other than itself: a library
 Gaussian filter, closed forms for constant images (borders included), the maximum of SSIM at
-identical images, symmetry, and FP64 central differences of the gradient."""
+identical images, symmetry, a tap-by-tap evaluation of the map at every pixel, and FP64
+central differences of the gradient."""
 import math
 
 import numpy as np
