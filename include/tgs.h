@@ -310,7 +310,7 @@ tgs_status tgs_count_hits(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera
    views, alpha_j = M_j sigmoid(o_j) the opacity the blend uses and gamma_j = min(V_j / V_q, 1)
    the volume V_j = s_x s_y s_z (masked scales M exp(l)) relative to V_q, the volume at rank
    floor(quantile * (n - 1)) of all n volumes in ascending order (gamma = 1 where V_q = 0).
-   quantile in [0, 1] (the paper: the 90% largest, 0.9). Uses the context's mask threshold.
+   quantile in [0, 1] (the paper normalises at the 90 % point: 0.9). Uses the context's mask threshold.
    Asynchronous; TGS_ERR_INVALID_ARG for a null pointer or a quantile outside [0, 1]. */
 tgs_status tgs_significance(tgs_ctx *ctx, const tgs_gaussians *g, const uint32_t *hit_count,
                             double quantile, float *scores, tgs_stream stream);

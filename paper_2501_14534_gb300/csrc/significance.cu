@@ -5,7 +5,8 @@
 // GS_j = hits_j * alpha_j * gamma_j with alpha_j = M_j sigmoid(o_j) (the opacity the blend
 // uses) and gamma_j = min(V_j / V_q, 1): V_j = s_x s_y s_z with the masked scales M exp(l),
 // V_q the volume at rank floor(q (n - 1)) of all volumes sorted ascending (the paper's
-// normalisation by "the 90% largest" volume, q = 0.9), gamma = 1 where V_q = 0.
+// normalisation by the volume at the 90 % point of the sorted volumes, q = 0.9), gamma = 1
+// where V_q = 0.
 #include "tgs_internal.cuh"
 
 namespace tgs {

@@ -401,7 +401,7 @@ class Rasterizer:
 
     def significance(self, g: Gaussians, hit_count, quantile=0.9):
         """Significance score of each Gaussian (float32 [n]) from its ray hits, opacity and
-        volume; quantile picks the reference volume (the paper's 90% largest)."""
+        volume; quantile picks the reference volume (the paper's choice: 0.9)."""
         scores = torch.empty(g.n, device="cuda", dtype=torch.float32)
         B.check(B.lib.tgs_significance(self._h, C.byref(g.struct()), _p(hit_count), float(quantile),
                                        _p(scores), _stream()), "tgs_significance")
