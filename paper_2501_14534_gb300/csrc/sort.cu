@@ -238,9 +238,11 @@ k_count_keys(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict
             }
         }
         __syncwarp();
+        // every record's count is written, 0 for one not visible: the emission reads the counts
+        // of all records, and this buffer may hold anything from an earlier use
+        if (j < n) ki.cnt[j] = s_c[w][lane];
         if (valid) {
             const uint32_t c = s_c[w][lane];
-            ki.cnt[j] = c;
             ki.km[j] = make_uint2(s_m[w][lane][0], s_m[w][lane][1]);
             ki.rx[j] = rx;
             ki.ry[j] = ry;
