@@ -56,6 +56,8 @@
  * unless stated). A tgs_ctx owns a device scratch arena (sort buffers, splat records, key
  * lists) that it grows on demand outside stream capture and frees in tgs_destroy. Nothing is
  * freed across the ABI. Calls are asynchronous on the given stream except where stated.
+ * The calls on one context share its arena: they must not overlap on the GPU (issue them on
+ * one stream, or give each stream or host thread a context of its own).
  *
  * Errors: every call returns a tgs_status; no C++ exception crosses the ABI. Errors found on
  * the device (key capacity overflow, a bounded wait that ran out) are recorded in a device
