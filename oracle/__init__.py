@@ -378,6 +378,54 @@ def compact(scene, st: Settings, remove=None, masked=True):
     return out, idx
 
 
+# ---- mask losses of Eq. loss3dgs --------------------------------------------------------------
+#
+# The training loss adds lambda_m L_m + lambda_sh L_sh (Eq. loss3dgs, lambda_m = lambda_sh = 0.05,
+# Sec. "Implementation details"); the paper defers both definitions to the cited works and fixes
+# one property: the masking loss of each SH band is weighted by the band's number of
+# coefficients (Sec. "Spherical Harmonic (SH) Masking"). Reading used here:
+#   L_m  = (1/N) sum_n sigmoid(m_n)                        (mean soft volume mask)
+#   L_sh = (1/N) sum_n sum_{l=1..3} w_l sigmoid(m_n^l),    w_l = (2l + 1) / 15
+# where 2l + 1 is the number of coefficients of band l per colour channel and 15 their total
+# over bands 1..3, so the weights sum to 1 and both losses lie in (0, 1). Every Gaussian and
+# every band counts, visible or not. The gradients are the plain derivatives of these soft
+# masks (no straight-through step is involved).
+
+MASK_LAMBDA = 0.05
+SH_MASK_LAMBDA = 0.05
+
+
+def sh_band_weights():
+    """w_l for l = 1, 2, 3: the share of band l among the 15 rest coefficients per channel."""
+    counts = np.array([2 * l + 1 for l in (1, 2, 3)], np.float64)
+    return counts / counts.sum()
+
+
+def mask_loss(scene, lam_m=MASK_LAMBDA, lam_sh=SH_MASK_LAMBDA):
+    """lambda_m L_m + lambda_sh L_sh (reading above) and its gradients with respect to the
+    mask logits: (loss, {"mask_logits": [N], "sh_mask_logits": [N,3]}); an absent logit
+    array contributes nothing and gets no gradient."""
+    sig = lambda x: 1.0 / (1.0 + np.exp(-x))
+    loss = 0.0
+    grads = {"mask_logits": None, "sh_mask_logits": None}
+    m = scene.get("mask_logits")
+    if m is not None:
+        m = np.asarray(m, np.float64)
+        n = m.shape[0]
+        s = sig(m)
+        loss += lam_m * s.sum() / max(n, 1)
+        grads["mask_logits"] = lam_m * s * (1.0 - s) / max(n, 1)
+    b = scene.get("sh_mask_logits")
+    if b is not None:
+        b = np.asarray(b, np.float64).reshape(-1, 3)
+        n = b.shape[0]
+        s = sig(b)
+        w = sh_band_weights()
+        loss += lam_sh * (s * w).sum() / max(n, 1)
+        grads["sh_mask_logits"] = lam_sh * w * s * (1.0 - s) / max(n, 1)
+    return loss, grads
+
+
 # ---- FP16 storage (Sec. "Experiments", setup: parameters kept as 16-bit halves after training) --
 
 def to_half(scene):

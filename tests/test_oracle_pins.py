@@ -846,3 +846,48 @@ def test_half_rounding_is_ieee_nearest_even():
     scene = {"means": x.reshape(-1, 1)}
     got = oracle.to_half(scene)["means"].reshape(-1)
     np.testing.assert_array_equal(got.astype(np.float64), want)
+
+
+# ---- mask losses of Eq. loss3dgs ------------------------------------------------------------
+
+def test_mask_losses_closed_forms():
+    """Closed forms of the reading: sigmoid(0) = 1/2 gives L_m = L_sh = 1/2; a saturated logit
+    of one band alone gives that band's share of the rest coefficients, (2l + 1) / 15 -- the
+    weighting by the number of coefficients per band (Sec. "Spherical Harmonic (SH) Masking")."""
+    n = 7
+    zero = {"mask_logits": np.zeros(n), "sh_mask_logits": np.zeros((n, 3))}
+    loss, g = oracle.mask_loss(zero, 1.0, 0.0)
+    assert abs(loss - 0.5) < 1e-15
+    np.testing.assert_allclose(g["mask_logits"], 0.25 / n, rtol=1e-15)
+    loss, g = oracle.mask_loss(zero, 0.0, 1.0)
+    assert abs(loss - 0.5) < 1e-15
+    for l, coeffs in [(1, 3), (2, 5), (3, 7)]:
+        b = np.full((n, 3), -60.0)
+        b[:, l - 1] = 60.0
+        loss, _ = oracle.mask_loss({"sh_mask_logits": b}, 0.0, 1.0)
+        assert abs(loss - coeffs / 15.0) < 1e-12, (l, loss)
+    # the volume mask: mean of sigmoid over the Gaussians, weight lambda_m
+    m = np.array([-60.0, 60.0, 60.0, 0.0])
+    loss, _ = oracle.mask_loss({"mask_logits": m}, 0.05, 0.0)
+    assert abs(loss - 0.05 * 2.5 / 4) < 1e-12
+    # an absent array contributes nothing
+    loss, g = oracle.mask_loss({"mask_logits": None, "sh_mask_logits": None})
+    assert loss == 0.0 and g["mask_logits"] is None and g["sh_mask_logits"] is None
+
+
+def test_mask_losses_gradient_fd():
+    rng = np.random.default_rng(17)
+    sc = {"mask_logits": rng.normal(2.0, 1.5, size=9), "sh_mask_logits": rng.normal(1.0, 2.0, size=(9, 3))}
+    _, g = oracle.mask_loss(sc, 0.05, 0.05)
+    for key in ("mask_logits", "sh_mask_logits"):
+        a = sc[key]
+        for idx in np.ndindex(a.shape):
+            h = 1e-6
+            old = a[idx]
+            a[idx] = old + h
+            lp, _ = oracle.mask_loss(sc, 0.05, 0.05)
+            a[idx] = old - h
+            lm, _ = oracle.mask_loss(sc, 0.05, 0.05)
+            a[idx] = old
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[key][idx]) <= 1e-9 * max(1.0, abs(fd)), (key, idx, fd, g[key][idx])
