@@ -5,10 +5,15 @@ binning, forward blend, L1 loss, backward blend, preprocess backward) over 16 vi
 SH-band masks at eps = 0.5).
 
 Prints one JSON line. value = views per second of the batched step with inputs resident in
-HBM; e2e = the same through the C ABI with the Gaussian parameters and target images copied
-from pinned host memory every step and the loss read back. Also reports the plain
-single-view path (views/s) and forward-only render FPS for comparison, the roofline of the
-dominant kernel, and the FP64 CPU oracle timed on the host cores on a bounded sample.
+HBM; e2e = the same through one C-ABI call per step with the Gaussian parameters and target
+images in pinned host memory (tgs_train_step_batched_host: the library copies them in, the
+copies of one step overlapping the previous step's compute, and copies the loss back).
+Also reports the plain single-view path (views/s, at tile 16 and at its best configuration)
+and forward-only render FPS for comparison, a significance pruning round, the roofline of the
+dominant kernel against peaks measured on the GPU (tgs_measure_peaks), a sub-record for each of
+the other four workloads (10K plain, 500K mixed-resolution batch, 300K render-only at
+1920x1080, 3M large scene), and the FP64 CPU oracle timed on the host cores on a bounded
+sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 run under torchrun: every rank renders its own 16 views (replicas; weak scaling).
@@ -38,8 +43,9 @@ OPS_EVAL = 11        # offset, exponent, skip tests, ex2, alpha: every evaluated
 OPS_BLEND = 7        # 1 - a, T update, stop test, weight, 3 colour FMAs: contributing pairs
 OPS_BWD = 51         # evaluation again + T recovery, colour-behind update, dL/da and the 9
                      # gradient terms: contributing pairs (skipped pairs not counted)
-# float32 lanes: 152 SMs x 128 lanes x 2.07 GHz max SM clock
-ALU_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+# special-function operations per contributing pair: ex2 in the forward, ex2 and the
+# reciprocal of the T recovery in the backward
+SFU_PER_CONTRIB = 3
 # DRAM bytes (read + write) of one fused-blend launch on the default workload at tile 32,
 # 2 px/thread, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; the command
 # is in profiles/k_fused_l1_300k_8x1280x832_tile32_ppt2.md). Reported only while the kernel's
@@ -71,10 +77,11 @@ def parse():
     p.add_argument("--views", type=int, default=N_VIEWS)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--no-workloads", action="store_true",
+                   help="skip the sub-records of the 10K, 500K, 300K and 3M workloads")
+    p.add_argument("--no-pruning-round", action="store_true")
     p.add_argument("--tile", type=int, default=16)
     p.add_argument("--ppt", type=int, default=1)
-    p.add_argument("--pruning-round", action="store_true",
-                   help="also time a significance pruning round (hits, score, selection, compaction)")
     p.add_argument("--step-only", action="store_true",
                    help="stop after the timed batched steps (for launch lists under a profiler)")
     return p.parse_args()
@@ -152,6 +159,71 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def dist(per_ms):
+    """Median, p10 and p90 of per-step times (ms)."""
+    a = np.asarray(per_ms, np.float64)
+    return {"median": float(np.median(a)), "p10": float(np.percentile(a, 10)),
+            "p90": float(np.percentile(a, 90))}
+
+
+def timed(torch, fn, steps, stream):
+    """Runs fn steps times back to back on stream with an event after each; returns the total
+    and the per-step times in ms."""
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for i in range(steps):
+            fn()
+            ev[i + 1].record(stream)
+    stream.synchronize()
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    return ev[0].elapsed_time(ev[-1]), per
+
+
+# ---- algorithmic work and the floor of a step (the roofline of the whole path) ----------
+#
+# bytes / ops per unit as stated in DESIGN.md: preprocess reads each Gaussian's 252 B once for
+# all views and writes a 48 B record per (view, Gaussian); binning scans 8 B per record and
+# moves 12 B per key written plus 24 B per key per 8-bit sort pass over 32 depth bits and the
+# tile bits, and reads 8 B per key for the ranges; the blend is bound by FP32 issue (ops per
+# pair above) or the SFU (SFU_PER_CONTRIB per contributing pair), whichever is slower, plus
+# 40 B per key gathered; the preprocess backward reads 252 B and writes 252 B + 12 B of
+# statistics per Gaussian and reads 36 B per (view, Gaussian).
+
+def key_passes(total_tiles):
+    return (32 + max(1, int(np.ceil(np.log2(max(total_tiles, 2))))) + 7) // 8
+
+
+def step_floor_ms(n, V, K, tiles, pixels, P_eval, P_contrib, peaks, hbm_gbs, backward=True, gbytes_param=252):
+    """Per-stage floors (ms) of one step from its algorithmic work and the measured peaks."""
+    hbm = hbm_gbs * 1e9
+    fp32 = peaks["fp32_fma_per_s"]
+    sfu = peaks["ex2_per_s"]
+    st = {}
+    st["preprocess"] = (gbytes_param * n + 48 * V * n) / hbm * 1e3
+    st["binning"] = (8 * V * n + K * (12 + 24 * key_passes(tiles) + 8)) / hbm * 1e3
+    ops = P_eval * OPS_EVAL + P_contrib * OPS_BLEND + (P_contrib * OPS_BWD if backward else 0)
+    sfu_ops = P_contrib * (SFU_PER_CONTRIB if backward else 1)
+    gather = (40 * K * (2 if backward else 1) + (24 if backward else 12) * pixels) / hbm
+    st["blend"] = max(ops / fp32, sfu_ops / sfu, gather) * 1e3
+    if backward:
+        st["preprocess_backward"] = ((252 + 252 + 12) * n + 36 * V * n) / hbm * 1e3
+    return st
+
+
+def pair_counts(R, g, cams, tile, ppt, eps_mask, eps_sh):
+    """Exact (pixel, fragment) pair counts of these views at this tile size, from a forward
+    with per-pixel counters: evaluated (pixel in the splat's rect, before the pixel stopped)
+    and contributing (blended)."""
+    counter = R.Rasterizer(tile=tile, ppt=ppt, eps_mask=eps_mask, eps_sh=eps_sh)
+    Pe = Pc = 0
+    for c in cams:
+        o = counter.forward(g, [c], want_examined=True, want_counts=True)[0]
+        Pe += int(o["n_eval"].sum().item())
+        Pc += int(o["n_contrib"].sum().item())
+    return Pe, Pc
+
+
 def cpu_baseline(w, fraction=1.0 / 64, threads=None):
     """The FP64 oracle on the host cores for ONE view: preprocess, key sort, forward blend,
     L1 loss, backward blend and preprocess backward. The per-tile blend work (forward and
@@ -226,6 +298,209 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---- the other workloads ------------------------------------------------------------------
+
+def _floor_record(st_ms, measured_ms):
+    floor = sum(st_ms.values())
+    return {"bound": "step", "floor_ms": floor, "measured_ms": measured_ms, "frac": floor / measured_ms,
+            "stage_floor_ms": st_ms,
+            "note": "sum of the stage floors (HBM stages at the measured copy bandwidth, blend at the "
+                    "measured FP32 issue / SFU rate) over the measured step"}
+
+
+def bench_c1(torch, R, stream, peaks, hbm_gbs, steps):
+    """10K Gaussians, 128x128, plain single-view fwd+bwd (tile 16), L1 to a seeded target."""
+    from paper_2501_14534_gb300 import synth
+    w = synth.workload(1)
+    g = R.Gaussians.from_numpy(w["scene"])
+    cam = w["cams"][0]
+    tgt = torch.from_numpy(w["targets"][0]).cuda()
+    rast = R.Rasterizer(tile=16, ppt=1, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
+    loss = torch.zeros(1, device="cuda")
+    dimg = torch.empty_like(tgt)
+    grads = rast.alloc_grads(g)
+    stats = rast.alloc_stats(g.n)
+    count = 3 * cam.width * cam.height
+
+    def view():
+        outs = rast.forward(g, [cam])
+        rast.l1_loss(outs[0]["image"], tgt, 1.0 / count, loss, dimg)
+        rast.backward(g, [cam], outs, [dimg], grads, stats)
+
+    with torch.cuda.stream(stream):
+        for _ in range(5):
+            view()
+    stream.synchronize()
+    n_t = max(20, steps)
+    total, per = timed(torch, view, n_t, stream)
+    # the same view through the batched step (one launch of each stage, no host sync)
+    brast = R.Rasterizer(tile=16, ppt=1, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
+    brast.plan(g, [cam])
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            brast.train_step_batched(g, [cam], [tgt], grads, None, loss, graph=True)
+    stream.synchronize()
+    btotal, bper = timed(torch, lambda: brast.train_step_batched(g, [cam], [tgt], grads, None, loss, graph=True),
+                         n_t, stream)
+    Pe, Pc = pair_counts(R, g, [cam], 16, 1, w["eps_mask"], w["eps_sh"])
+    K = brast.plan(g, [cam])
+    fl = step_floor_ms(g.n, 1, K, 64, count // 3, Pe, Pc, peaks, hbm_gbs)
+    d = dist(per)
+    return {"workload": w["name"], "metric": "plain fwd+bwd views/s", "value": 1000.0 * n_t / total,
+            "unit": "views/s", "ms_per_step": d, "batched_step_views_per_s": 1000.0 * n_t / btotal,
+            "batched_ms_per_step": dist(bper), "keys": K, "pairs": {"evaluated": Pe, "contributing": Pc},
+            "roofline": _floor_record(fl, d["median"])}
+
+
+def bench_c3(torch, R, stream, peaks, hbm_gbs, steps, autotune=True):
+    """500K Gaussians, 16 mixed-resolution views (4 x 320x208, 6 x 640x416, 6 x 1280x832) in
+    one batched step (persistent fused launch, CUDA graph), tile and pixels per thread tuned."""
+    from paper_2501_14534_gb300 import synth
+    w = synth.workload(3)
+    cams = w["cams"]
+    V = len(cams)
+    g = R.Gaussians.from_numpy(w["scene"])
+    tg = [torch.from_numpy(t).cuda() for t in w["targets"]]
+    rast = R.Rasterizer(tile=16, ppt=1, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
+    tuned = rast.autotune(g, cams, tg) if autotune else None
+    K = rast.plan(g, cams, headroom=1.15)
+    grads = rast.alloc_grads(g)
+    stats = rast.alloc_stats(g.n)
+    loss = torch.zeros(1, device="cuda")
+
+    def step():
+        rast.train_step_batched(g, cams, tg, grads, stats, loss, graph=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            step()
+    stream.synchronize()
+    rast.poll()
+    total, per = timed(torch, step, steps, stream)
+    rast.poll()
+    cfg = rast.config
+    pixels = sum(c.width * c.height for c in cams)
+    Pe, Pc = pair_counts(R, g, cams, cfg.tile, cfg.ppt, w["eps_mask"], w["eps_sh"])
+    tiles = rast.num_tiles(cams)
+    fl = step_floor_ms(g.n, V, K, tiles, pixels, Pe, Pc, peaks, hbm_gbs)
+    d = dist(per)
+    ms = total / steps
+    return {"workload": w["name"], "metric": "fwd+bwd views/s (batched step)", "value": V * 1000.0 / ms,
+            "unit": "views/s", "pixels_per_s": pixels * 1000.0 / ms, "ms_per_step": d,
+            "tile": cfg.tile, "ppt": cfg.ppt, "autotuned": tuned is not None, "keys": K,
+            "pairs": {"evaluated": Pe, "contributing": Pc}, "roofline": _floor_record(fl, d["median"])}
+
+
+def bench_c4(torch, R, stream, peaks, hbm_gbs):
+    """300K Gaussians with a per-Gaussian SH degree, 100 hemisphere poses at 1920x1080,
+    forward only (the plain path, one view at a time): FPS = 100 / total."""
+    from paper_2501_14534_gb300 import synth
+    w = synth.workload(4)
+    cams = w["cams"]
+    g = R.Gaussians.from_numpy(w["scene"])
+    rast = R.Rasterizer(tile=16, ppt=1, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
+    outs = rast._alloc_views(cams[:1], g.n, want_state=False)
+
+    def render(c):
+        rast.forward(g, [c], want_state=False, outs=outs)
+
+    with torch.cuda.stream(stream):
+        for c in cams[:5]:
+            render(c)
+    stream.synchronize()
+    it = iter(range(len(cams)))
+    total, per = timed(torch, lambda: render(cams[next(it)]), len(cams), stream)
+    # algorithmic work: SH coefficients read only up to each Gaussian's degree
+    deg = w["scene"]["sh_degree"].astype(np.int64)
+    param_bytes = float(np.mean(4 * (3 + 3 + 4 + 1 + 3) + 12 * ((deg + 1) ** 2 - 1)))
+    Pe = Pc = K = 0
+    counter = R.Rasterizer(tile=16, ppt=1, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
+    for c in cams[:10]:   # pair and key counts of 10 poses, scaled to the 100
+        o = counter.forward(g, [c], want_examined=True, want_counts=True)[0]
+        Pe += int(o["n_eval"].sum().item())
+        Pc += int(o["n_contrib"].sum().item())
+        sp, rd = counter.preprocess(g, [c])
+        K += counter.bin(sp, rd, g.n, [c], want_keys=False)[3]
+    f = len(cams) / 10
+    fl = {k: v * f for k, v in step_floor_ms(g.n, 10, K, 10 * 8160, 10 * 1920 * 1080, Pe, Pc, peaks, hbm_gbs,
+                                              backward=False, gbytes_param=10 * param_bytes).items()}
+    # the 10-view floor counts the parameter read once per view, as a view-by-view render does
+    algo_bytes = f * ((param_bytes + 48) * g.n * 10 + K * (12 + 24 * key_passes(8160) + 8 + 40)
+                      + 12 * 1920 * 1080 * 10)
+    d = dist(per)
+    return {"workload": w["name"], "metric": "render FPS (forward only)", "value": 1000.0 * len(cams) / total,
+            "unit": "FPS", "ms_per_frame": d, "achieved_GBps": algo_bytes / (total * 1e-3) / 1e9,
+            "keys_per_frame": K / 10, "pairs_per_frame": {"evaluated": Pe / 10, "contributing": Pc / 10},
+            "roofline": _floor_record(fl, total)}
+
+
+def bench_c5(torch, R, stream, peaks, hbm_gbs, steps):
+    """3M Gaussians (256 blobs), 8 views of 1600x1064: the batched step, and the per-view
+    checkpointed autograd path (forward of the 8 views keeping only T_final and last per view,
+    then the backward re-binning each view); views/s and peak device memory."""
+    from paper_2501_14534_gb300 import synth
+    w = synth.workload(5)
+    cams = w["cams"]
+    V = len(cams)
+    torch.cuda.synchronize()
+    torch.cuda.reset_peak_memory_stats()
+    g = R.Gaussians.from_numpy(w["scene"])
+    tg = [torch.from_numpy(t).cuda() for t in w["targets"]]
+    rast = R.Rasterizer(tile=16, ppt=1, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
+    for k in R.PARAM_KEYS:
+        t = getattr(g, k)
+        if t is not None:
+            t.requires_grad_(True)
+    n_t = max(3, min(steps, 10))
+
+    def ckpt_step():
+        imgs = R.rasterize(rast, g, cams)
+        loss = sum((im - t).abs().mean() for im, t in zip(imgs, tg)) / V
+        loss.backward()
+
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            ckpt_step()
+    stream.synchronize()
+    total, per = timed(torch, ckpt_step, n_t, stream)
+    peak_ckpt = torch.cuda.max_memory_allocated() + rast.arena_bytes()
+    for k in R.PARAM_KEYS:
+        t = getattr(g, k)
+        if t is not None:
+            t.grad = None
+            t.requires_grad_(False)
+    # the batched step on the same scene and views
+    brast = R.Rasterizer(tile=16, ppt=1, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
+    brast.autotune(g, cams, tg)
+    K = brast.plan(g, cams, headroom=1.15)
+    grads = brast.alloc_grads(g)
+    loss = torch.zeros(1, device="cuda")
+
+    def bstep():
+        brast.train_step_batched(g, cams, tg, grads, None, loss, graph=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            bstep()
+    stream.synchronize()
+    brast.poll()
+    btotal, bper = timed(torch, bstep, n_t, stream)
+    cfg = brast.config
+    pixels = sum(c.width * c.height for c in cams)
+    Pe, Pc = pair_counts(R, g, cams, cfg.tile, cfg.ppt, w["eps_mask"], w["eps_sh"])
+    fl = step_floor_ms(g.n, V, K, brast.num_tiles(cams), pixels, Pe, Pc, peaks, hbm_gbs)
+    d = dist(per)
+    bd = dist(bper)
+    return {"workload": w["name"], "metric": "fwd+bwd views/s (per-view checkpointed autograd)",
+            "value": V * 1000.0 * n_t / total, "unit": "views/s", "ms_per_step": d,
+            "peak_device_bytes_checkpointed": int(peak_ckpt),
+            "batched_step_views_per_s": V * 1000.0 * n_t / btotal, "batched_ms_per_step": bd,
+            "batched_tile": cfg.tile, "batched_ppt": cfg.ppt, "keys": K,
+            "peak_device_bytes": int(torch.cuda.max_memory_allocated() + rast.arena_bytes() + brast.arena_bytes()),
+            "pairs": {"evaluated": Pe, "contributing": Pc},
+            "roofline": _floor_record(fl, bd["median"])}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -238,11 +513,16 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        import torch.distributed as dist_
+        dist_.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2501_14534_gb300 import build as tgs_build
     tgs_build.build()
     from paper_2501_14534_gb300 import rasterizer as R
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        peaks = R.Rasterizer.measure_peaks()
+    hbm_gbs, peak_kind = load_peaks()
 
     w = workload(args.n, args.views)
     cams = w["cams"]
@@ -259,7 +539,6 @@ def main():
     grads = rast.alloc_grads(g)
     stats = rast.alloc_stats(g.n)
     loss = torch.zeros(1, device="cuda")
-    stream = torch.cuda.Stream()
 
     def barrier():
         if world > 1:
@@ -278,19 +557,13 @@ def main():
     kernels = rast.kernels_per_step()
 
     # ---- timed region: K batched steps back to back (inputs in HBM, larger than L2) ----
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-            for _ in range(args.steps):
-                step()
-            e1.record(stream)
-        stream.synchronize()
+        total_ms, per_step = timed(torch, step, args.steps, stream)
     barrier()
     from paper_2501_14534_gb300 import dist as tgs_dist
-    ms_total = tgs_dist.reduce_max(e0.elapsed_time(e1), device="cuda")   # max over ranks
+    ms_total = tgs_dist.reduce_max(total_ms, device="cuda")   # max over ranks
     rast.poll()
     ms_step = ms_total / args.steps
     value = V * world / (ms_step / 1000.0)
@@ -313,26 +586,22 @@ def main():
     if args.step_only:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "views/s", "partial": True,
-                              "ms_per_step": ms_step, "stage_ms": stage_ms,
+                              "ms_per_step": ms_step, "step_ms": dist(per_step), "stage_ms": stage_ms,
                               "kernels_per_step": kernels}), flush=True)
         if world > 1:
             torch.distributed.destroy_process_group()
         return
 
     # ---- A/B: the same step with separate forward, loss and backward kernels ----
-    rast.set_profiling(False)
     unfused = None
     try:
         with torch.cuda.stream(stream):
             for _ in range(2):
                 rast.train_step_batched(g, cams, targets, grads, stats, loss, graph=True, fused=False)
-            u0, u1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            u0.record(stream)
-            for _ in range(3):
-                rast.train_step_batched(g, cams, targets, grads, stats, loss, graph=True, fused=False)
-            u1.record(stream)
         stream.synchronize()
-        unfused = V * world / (u0.elapsed_time(u1) / 3 / 1000.0)
+        t, _ = timed(torch, lambda: rast.train_step_batched(g, cams, targets, grads, stats, loss, graph=True,
+                                                             fused=False), 3, stream)
+        unfused = V * world / (t / 3 / 1000.0)
     except Exception as e:  # reported, not fatal
         print(f"[bench] unfused A/B failed: {e}", file=sys.stderr)
 
@@ -342,13 +611,10 @@ def main():
         with torch.cuda.stream(stream):
             for _ in range(2):
                 rast.train_step_batched(g, cams, targets, grads, stats, loss, graph=True, dssim=True)
-            d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            d0.record(stream)
-            for _ in range(3):
-                rast.train_step_batched(g, cams, targets, grads, stats, loss, graph=True, dssim=True)
-            d1.record(stream)
         stream.synchronize()
-        dssim = {"views_per_s": V * world / (d0.elapsed_time(d1) / 3 / 1000.0)}
+        t, _ = timed(torch, lambda: rast.train_step_batched(g, cams, targets, grads, stats, loss, graph=True,
+                                                             dssim=True), 3, stream)
+        dssim = {"views_per_s": V * world / (t / 3 / 1000.0)}
         rast.set_profiling(True)
         with torch.cuda.stream(stream):
             for _ in range(2):   # the first captures the profiled graph
@@ -364,88 +630,81 @@ def main():
         rast.set_profiling(False)
         print(f"[bench] D-SSIM step failed: {e}", file=sys.stderr)
 
-    # ---- e2e: inputs from pinned host memory each step, loss read back ----
-    host = {k: t.detach().cpu().pin_memory() for k, t in g.params().items()}
+    # ---- e2e: one C-ABI call per step with the inputs in pinned host memory (the library
+    # copies them in on its upload stream and copies the loss back) ----
+    hostg = R.Gaussians(**{k: t.detach().cpu().pin_memory() for k, t in g.params().items()},
+                        sh_degree_max=g.sh_degree_max)
     host_t = [t.cpu().pin_memory() for t in targets]
-    h2d = sum(t.numel() * t.element_size() for t in host.values()) + \
+    h2d = sum(t.numel() * t.element_size() for t in hostg.params().values()) + \
         sum(t.numel() * t.element_size() for t in host_t)
     loss_host = torch.zeros(1).pin_memory()
-    rast.set_profiling(False)
+    camarr = R.cameras_array(cams)
+
+    def e2e_step():
+        rast.train_step_batched_host(hostg, cams, host_t, grads, stats, loss_host, graph=True, cams_struct=camarr)
+
     with torch.cuda.stream(stream):
-        step()
+        for _ in range(3):   # both buffer sets filled and their graphs captured
+            e2e_step()
     stream.synchronize()
-    n_e2e = max(2, min(args.steps, 5))
+    n_e2e = max(5, min(args.steps, 20))
     barrier()
     torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for _ in range(n_e2e):
-            for k, t in g.params().items():
-                t.copy_(host[k], non_blocking=True)
-            for t, h in zip(targets, host_t):
-                t.copy_(h, non_blocking=True)
-            step()
-            loss_host.copy_(loss, non_blocking=True)
-        a1.record(stream)
-    stream.synchronize()
-    e2e_ms = a0.elapsed_time(a1) / n_e2e
+    e2e_total, e2e_per = timed(torch, e2e_step, n_e2e, stream)
+    torch.cuda.synchronize()   # the last loss copy has landed in loss_host
+    e2e_ms = e2e_total / n_e2e
     e2e_value = V * world / (e2e_ms / 1000.0)
 
     # ---- the plain single-view path and forward-only FPS on the same views ----
-    plain = R.Rasterizer(tile=16, ppt=1, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
-    pl_loss = torch.zeros(1, device="cuda")
-    dimg = [torch.empty_like(t) for t in targets]
-    pgrads = plain.alloc_grads(g)
-    pstats = plain.alloc_stats(g.n)
+    def plain_rate(tile, ppt, backward=True, gg=None):
+        gg = gg or g
+        plain = R.Rasterizer(tile=tile, ppt=ppt, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
+        pl_loss = torch.zeros(1, device="cuda")
+        dimg = [torch.empty_like(t) for t in targets]
+        pgrads = plain.alloc_grads(gg) if backward else None
+        pstats = plain.alloc_stats(gg.n) if backward else None
 
-    def plain_view(v, backward=True):
-        outs = plain.forward(g, [cams[v]])
-        if backward:
-            plain.l1_loss(outs[0]["image"], targets[v], 1.0 / (3 * W * H * V), pl_loss, dimg[v])
-            plain.backward(g, [cams[v]], outs, [dimg[v]], pgrads, pstats, accumulate=v > 0)
-        return outs
+        def one(v):
+            outs = plain.forward(gg, [cams[v]])
+            if backward:
+                plain.l1_loss(outs[0]["image"], targets[v], 1.0 / (3 * W * H * V), pl_loss, dimg[v])
+                plain.backward(gg, [cams[v]], outs, [dimg[v]], pgrads, pstats, accumulate=v > 0)
 
-    for v in range(min(V, 3)):
-        plain_view(v)
-    torch.cuda.synchronize()
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record()
-    for v in range(V):
-        plain_view(v)
-    p1.record()
-    torch.cuda.synchronize()
-    plain_vps = V / (p0.elapsed_time(p1) / 1000.0)
-    p0.record()
-    for v in range(V):
-        plain_view(v, backward=False)
-    p1.record()
-    torch.cuda.synchronize()
-    render_fps = V / (p0.elapsed_time(p1) / 1000.0)
+        with torch.cuda.stream(stream):
+            for v in range(min(V, 3)):
+                one(v)
+        stream.synchronize()
+        it = iter(range(V))
+        t, _ = timed(torch, lambda: one(next(it)), V, stream)
+        return V / (t / 1000.0)
+
+    plain_vps = plain_rate(16, 1)
+    plain_by_cfg = {}
+    for tl, pp in [(8, 1), (8, 2), (16, 2), (16, 4), (32, 2), (32, 4)]:
+        plain_by_cfg[f"{tl}x{pp}"] = plain_rate(tl, pp)
+    plain_by_cfg["16x1"] = plain_vps
+    best_cfg = max(plain_by_cfg, key=plain_by_cfg.get)
+    plain_best = plain_by_cfg[best_cfg]
+    render_fps = plain_rate(16, 1, backward=False)
     # the same render from FP16 parameter storage (the paper's post-processing)
     gh = R.Rasterizer.to_half(g)
-    for v in range(min(V, 3)):
-        plain.forward(gh, [cams[v]])
-    p0.record()
-    for v in range(V):
-        plain.forward(gh, [cams[v]])
-    p1.record()
-    torch.cuda.synchronize()
-    render_fps_fp16 = V / (p0.elapsed_time(p1) / 1000.0)
+    render_fps_fp16 = plain_rate(16, 1, backward=False, gg=gh)
     del gh
 
     # ---- a significance pruning round on the same scene (Eq. significance-score): ray hits
     # over the views, score, selection of the lowest 60 %, compaction of every parameter array
     pruning = None
-    if args.pruning_round:
+    if not args.no_pruning_round:
         try:
+            prast = R.Rasterizer(tile=16, ppt=1, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
+
             def prune_round():
                 # each stage bracketed by events with the device idle before it, so that a gap on
                 # the host (a first launch, an allocation) is not counted as device time
                 ms = []
                 out = []
-                stages = [lambda: plain.count_hits(g, cams), lambda: plain.significance(g, out[0], 0.9),
-                          lambda: plain.prune_select(out[1], 0.6), lambda: plain.compact(g, out[2], masked=True)[0]]
+                stages = [lambda: prast.count_hits(g, cams), lambda: prast.significance(g, out[0], 0.9),
+                          lambda: prast.prune_select(out[1], 0.6), lambda: prast.compact(g, out[2], masked=True)[0]]
                 for f in stages:
                     torch.cuda.synchronize()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -458,38 +717,36 @@ def main():
 
             prune_round()   # first launches and buffer growth, untimed
             ms, kept = prune_round()
+            prast.poll()
+            # a binning of the pruned scene in the same context (its scratch reused)
+            sp, rd = prast.preprocess(kept, cams[:1])
+            K_pruned = prast.bin(sp, rd, kept.n, cams[:1], want_keys=False)[3]
+            prast.poll()
             # kept rows read and written, index map written, removal flag and mask logit read
             moved = 2 * kept.n * 252 + 4 * kept.n + 5 * g.n
             pruning = {"gaussians": g.n, "kept": kept.n, "count_hits_ms": ms[0], "significance_ms": ms[1],
                        "prune_select_ms": ms[2], "compact_ms": ms[3],
-                       "compact_GBps": moved / ms[3] / 1e6}
+                       "compact_GBps": moved / ms[3] / 1e6, "keys_view0_after": K_pruned}
             del kept
         except Exception as e:  # reported, not fatal
             print(f"[bench] pruning round failed: {e}", file=sys.stderr)
 
-    # algorithmic work of the blend stages: pairs examined per pixel (forward) and pairs up to
-    # the last contributor (backward), from a forward with per-pixel counters at the tile size
-    # of the batched step
+    # ---- roofline of the dominant kernel: algorithmic work from exact pair counts at the
+    # batched step's tile size, over the stage's average CUDA-event time ----
     cfg = rast.config
-    counter = R.Rasterizer(tile=cfg.tile, ppt=cfg.ppt, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
-    P_exam = P_eval = P_contrib = 0
-    for v in range(V):
-        o = counter.forward(g, [cams[v]], want_examined=True, want_counts=True)[0]
-        P_exam += int(o["n_examined"].sum().item())
-        P_eval += int(o["n_eval"].sum().item())
-        P_contrib += int(o["n_contrib"].sum().item())
-    hbm_gbs, peak_kind = load_peaks()
+    P_eval, P_contrib = pair_counts(R, g, cams, cfg.tile, cfg.ppt, w["eps_mask"], w["eps_sh"])
     n = g.n
     bytes_pre = n * 252 + V * n * (48 + 4 + 4 + 4 + 48)
     bytes_pbwd = n * (252 + 252 + 12 * 2) + V * n * (48 + 4)
     ops_fwd = P_eval * OPS_EVAL + P_contrib * OPS_BLEND
     ops_bwd = P_contrib * OPS_BWD
+    fp32_peak = peaks["fp32_fma_per_s"] / 1e12
     work = {
-        "fused_blend": ("alu", (ops_fwd + ops_bwd) / 1e12, ALU_PEAK_TOPS, "Tops/s"),
+        "fused_blend": ("alu", (ops_fwd + ops_bwd) / 1e12, fp32_peak, "Tops/s"),
         "preprocess": ("hbm", bytes_pre / 1e9, hbm_gbs, "GB/s"),
         "preprocess_backward": ("hbm", bytes_pbwd / 1e9, hbm_gbs, "GB/s"),
-        "blend_forward": ("alu", ops_fwd / 1e12, ALU_PEAK_TOPS, "Tops/s"),
-        "blend_backward": ("alu", ops_bwd / 1e12, ALU_PEAK_TOPS, "Tops/s"),
+        "blend_forward": ("alu", ops_fwd / 1e12, fp32_peak, "Tops/s"),
+        "blend_backward": ("alu", ops_bwd / 1e12, fp32_peak, "Tops/s"),
     }
     dom = max((k for k in stage_ms if k in work), key=lambda k: stage_ms[k])
     bound, units, peak, unit = work[dom]
@@ -497,8 +754,33 @@ def main():
     roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak,
                 "traffic": fused_traffic(cfg, n, V) if dom == "fused_blend" else None,
-                "peak_source": (f"{peak_kind} hbm_gbs" if bound == "hbm" else
-                                "152 SMs x 128 FP32 lanes x 2.07 GHz")}
+                "peak_source": (f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)" if bound == "hbm" else
+                                "measured: scalar fma.rn.f32 issue rate of tgs_measure_peaks")}
+    if dom == "fused_blend":
+        sfu_ops = SFU_PER_CONTRIB * P_contrib
+        roofline["sfu"] = {"achieved": sfu_ops / (stage_ms[dom] / 1000.0) / 1e12,
+                           "peak": peaks["ex2_per_s"] / 1e12, "unit": "T ops/s",
+                           "frac": sfu_ops / (stage_ms[dom] / 1000.0) / peaks["ex2_per_s"]}
+    floor = step_floor_ms(n, V, K_keys, rast.num_tiles(cams), V * W * H, P_eval, P_contrib, peaks, hbm_gbs)
+    step_roofline = _floor_record(floor, dist(per_step)["median"])
+
+    # ---- the other workloads ----
+    subs = None
+    if not args.no_workloads and rank == 0:
+        subs = {}
+        for key, fn in [("plain_10k_128x128", lambda: bench_c1(torch, R, stream, peaks, hbm_gbs, args.steps)),
+                        ("batched_500k_16_mixed_views", lambda: bench_c3(torch, R, stream, peaks, hbm_gbs,
+                                                                         args.steps, not args.no_autotune)),
+                        ("render_300k_1920x1080_100_poses", lambda: bench_c4(torch, R, stream, peaks, hbm_gbs)),
+                        ("large_3m_8x1600x1064", lambda: bench_c5(torch, R, stream, peaks, hbm_gbs, args.steps))]:
+            try:
+                t0 = time.time()
+                subs[key] = fn()
+                print(f"[bench] {key}: {time.time() - t0:.1f} s", file=sys.stderr)
+            except Exception as e:  # reported, not fatal
+                subs[key] = {"error": str(e)}
+                print(f"[bench] {key} failed: {e}", file=sys.stderr)
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -510,6 +792,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": "views/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "step_ms": dist(per_step),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": w["name"], "global_batch": V * world, "views_per_gpu": V,
@@ -517,14 +800,22 @@ def main():
                        "tile": cfg.tile, "ppt": cfg.ppt, "autotuned": tuned is not None,
                        "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (252 MB params)"},
             "e2e": {"value": e2e_value, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms},
-            "plain_views_per_s": plain_vps, "render_fps": render_fps, "render_fps_fp16_params": render_fps_fp16,
+                    "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms, "step_ms": dist(e2e_per),
+                    "api": "tgs_train_step_batched_host (pinned host inputs, copies on the library's upload "
+                           "stream overlapping the previous step)"},
+            "plain_views_per_s": plain_vps, "plain_best": {"config": best_cfg, "views_per_s": plain_best},
+            "plain_by_config": plain_by_cfg,
+            "render_fps": render_fps, "render_fps_fp16_params": render_fps_fp16,
             "pruning_round": pruning,
             "unfused_views_per_s": unfused, "l1_dssim_step": dssim,
             "speedup_vs_plain": value / world / plain_vps,
+            "speedup_vs_plain_best": value / world / plain_best,
             "stage_ms": stage_ms,
-            "pairs": {"examined": P_exam, "evaluated": P_eval, "contributing": P_contrib},
-            "roofline": roofline, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "pairs": {"evaluated": P_eval, "contributing": P_contrib},
+            "peaks": {k: peaks[k] for k in ("fp32_fma_per_s", "fp32x2_fma_per_s", "ex2_per_s", "rcp_per_s")},
+            "roofline": roofline, "step_roofline": step_roofline,
+            "workloads": subs,
+            "cpu_baseline": cpu, "clocks": clk.summary(),
             "gpu_launches": kernels * args.steps,
         }
         print(json.dumps(line), flush=True)

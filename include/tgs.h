@@ -60,8 +60,10 @@
  * one stream, or give each stream or host thread a context of its own).
  *
  * Errors: every call returns a tgs_status; no C++ exception crosses the ABI. Errors found on
- * the device (key capacity overflow, a bounded wait that ran out) are recorded in a device
- * status word and returned by tgs_poll_status (which synchronises the stream).
+ * the device (key capacity overflow, key counts that fail the emission's consistency check)
+ * are recorded in a device status word and returned by tgs_poll_status (which synchronises
+ * the stream). No kernel waits on another block or launch, so no call can hang on the device;
+ * the work of every kernel is bounded by its launch sizes and the key capacity.
  */
 #ifndef TGS_H
 #define TGS_H
@@ -78,10 +80,15 @@ typedef int32_t tgs_status;
 #define TGS_ERR_INVALID_ARG 1   /* a pointer, size or setting is out of range */
 #define TGS_ERR_CUDA 2          /* a CUDA runtime call failed */
 #define TGS_ERR_CAPACITY 3      /* more (Gaussian, tile) keys than the key capacity */
-#define TGS_ERR_TIMEOUT 4       /* a bounded device wait ran out; the results are invalid */
+#define TGS_ERR_TIMEOUT 4       /* reserved: no kernel of the library waits on another, so no call
+                                   returns it */
 #define TGS_ERR_OOM 5           /* device memory for the scratch arena could not be had */
 #define TGS_ERR_NOT_SUPPORTED 6 /* e.g. a tile size or launch shape that is not compiled */
 #define TGS_ERR_SCRATCH_LIMIT 7 /* input larger than the fixed scratch of tgs_bin_noalloc */
+#define TGS_ERR_INCONSISTENT 8  /* a device-side check of scratch data failed: the per-record key
+                                   counts of a block did not add up to the keys the count pass
+                                   scanned for it; that block emitted no keys and the step's
+                                   results are invalid (returned by tgs_poll_status) */
 
 #define TGS_SUPPORT_BOX3 0      /* 3-sigma square box (3DGS) */
 #define TGS_SUPPORT_ALPHA 1     /* smallest box outside which a < 1/255 */
@@ -109,7 +116,7 @@ typedef struct {
     float near_plane;      /* default 0.2 */
     float bg[3];           /* background colour (default 0) */
     int64_t key_capacity;  /* (Gaussian, tile) keys the batched path may hold; 0 = sized by tgs_plan */
-    int64_t spin_limit;    /* iterations of any bounded device wait (default 1 << 22) */
+    int64_t spin_limit;    /* reserved (no kernel waits on another); ignored, default 0 */
     float ssim_lambda;     /* lambda_SSIM of Eq. loss3dgs for TGS_LOSS_DSSIM, in [0, 1] (default 0.2) */
     int32_t reserved0;
 } tgs_config;
@@ -235,6 +242,24 @@ tgs_status tgs_train_step_batched(tgs_ctx *ctx, const tgs_gaussians *g, const tg
                                   int32_t V, const float *const *targets, float *const *images,
                                   const tgs_grads *grads, const tgs_stats *stats,
                                   float *loss_out, uint32_t flags, tgs_stream stream);
+/* The batched step for a caller whose parameters and target images live in host memory (a
+   data loader on the CPU, an application without device buffers of its own): one call copies
+   every parameter array of g_host (host pointers, same layouts as tgs_gaussians, float32) and
+   the V target images (host [3,H,W] each) into device buffers the context owns, runs
+   tgs_train_step_batched on them, and copies the loss into *loss_host (host float, may be
+   NULL). grads and stats are device memory, as for tgs_train_step_batched.
+   The copies go on an upload stream of the context, one cudaMemcpyAsync per array, into one
+   of two buffer sets used in turn, so that the next call's copies overlap this call's step;
+   the step waits for its copies, and the copies into a set wait for the step that last read
+   it. Host buffers should be pinned (cudaHostAlloc / cudaHostRegister) for the copies to be
+   asynchronous, and must not change until the copies have run (e.g. until the next call
+   returns, or a stream synchronisation). With TGS_USE_GRAPH each buffer set keeps its own
+   captured graph. Not capturable (TGS_ERR_NOT_SUPPORTED inside stream capture); the first
+   calls, and any call with larger inputs than before, allocate (and synchronise). */
+tgs_status tgs_train_step_batched_host(tgs_ctx *ctx, const tgs_gaussians *g_host, const tgs_camera *cams,
+                                       int32_t V, const float *const *targets_host, const tgs_grads *grads,
+                                       const tgs_stats *stats, float *loss_host, uint32_t flags,
+                                       tgs_stream stream);
 /* Times the batched step for tile in {8, 16, 32} x ppt in {1, 2, 4} and keeps the fastest in
    the context's config. cache_path (may be NULL) is a JSON file read first and written after. */
 tgs_status tgs_autotune(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
@@ -316,6 +341,12 @@ tgs_status tgs_count_hits(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera
    Asynchronous; TGS_ERR_INVALID_ARG for a null pointer or a quantile outside [0, 1]. */
 tgs_status tgs_significance(tgs_ctx *ctx, const tgs_gaussians *g, const uint32_t *hit_count,
                             double quantile, float *scores, tgs_stream stream);
+/* The significance-pruning schedule (Sec. "Implementation details": pruning applied a fixed
+   number of times, 60 % of the Gaussians the first time, the rate decayed by a constant factor
+   each time): fractions[r] = first * decay^r for r < rounds (host array of rounds doubles).
+   The paper's values are rounds = 6, first = 0.6, decay = 0.7. Host-only, no device work.
+   TGS_ERR_INVALID_ARG for rounds < 0, first or decay outside [0, 1], or a null fractions. */
+tgs_status tgs_prune_schedule(int32_t rounds, double first, double decay, double *fractions);
 /* The Gaussians a pruning round removes: prune [n] (device bytes) = 1 for the
    floor(fraction * n) lowest scores (equal scores: lower index first), 0 for the others.
    scores [n] device float, non-negative. fraction in [0, 1]. Asynchronous. */
@@ -370,6 +401,23 @@ const char *tgs_stage_name(tgs_ctx *ctx, int32_t i);
 /* Kernels the most recent batched step launched (for a graph replay: the kernel nodes of the
    graph). */
 int64_t tgs_kernels_per_step(const tgs_ctx *ctx);
+/* Device bytes the context's scratch arena holds now (every buffer it has allocated). */
+size_t tgs_arena_bytes(const tgs_ctx *ctx);
+
+/* Arithmetic peaks of the current GPU, measured by microbenchmark kernels (each thread runs 8
+   independent chains of one instruction over a grid of SMs x 2048 threads; about 20 ms in
+   all): the denominators of the roofline of the blend kernels, which are bound by FP32
+   instruction issue and the special-function unit (SFU) rather than by memory.
+   Synchronises the stream. Allocates a small buffer (freed before returning). */
+typedef struct {
+    double fp32_fma_per_s;   /* scalar fma.rn.f32 per second over all lanes (FP32 issue rate) */
+    double fp32x2_fma_per_s; /* FP32 FMAs per second issued as packed fma.rn.f32x2 pairs */
+    double ex2_per_s;        /* ex2.approx.ftz.f32 per second (SFU) */
+    double rcp_per_s;        /* rcp.approx.ftz.f32 per second (SFU) */
+    int32_t sms;             /* streaming multiprocessors */
+    double ms;               /* device time of the timed launches */
+} tgs_peaks;
+tgs_status tgs_measure_peaks(tgs_peaks *out, tgs_stream stream);
 
 /* Number of tiles of a view at the context's tile size, and bytes of scratch the batched
    path needs for n Gaussians and these views at the current key capacity. */

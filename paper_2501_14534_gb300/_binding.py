@@ -17,6 +17,7 @@ TGS_ERR_TIMEOUT = 4
 TGS_ERR_OOM = 5
 TGS_ERR_NOT_SUPPORTED = 6
 TGS_ERR_SCRATCH_LIMIT = 7
+TGS_ERR_INCONSISTENT = 8
 TGS_NOALLOC_MAX_RECORDS = 131072
 TGS_NOALLOC_MAX_KEYS = 524288
 TGS_SUPPORT_BOX3 = 0
@@ -70,6 +71,11 @@ class tgs_stats(C.Structure):
     _fields_ = [("grad_norm_accum", _vp), ("vis_count", _vp), ("max_radius", _vp), ("hit_count", _vp)]
 
 
+class tgs_peaks(C.Structure):
+    _fields_ = [("fp32_fma_per_s", C.c_double), ("fp32x2_fma_per_s", C.c_double), ("ex2_per_s", C.c_double),
+                ("rcp_per_s", C.c_double), ("sms", C.c_int32), ("ms", C.c_double)]
+
+
 _ctx_p = C.c_void_p
 _cfgp = C.POINTER(tgs_config)
 class tgs_half_params(C.Structure):
@@ -103,6 +109,8 @@ SIGNATURES = {
     "tgs_plan": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, C.c_double, C.POINTER(C.c_int64)]),
     "tgs_train_step_batched": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _pp, _pp, _gradp,
                                            _statp, _vp, C.c_uint32, _vp]),
+    "tgs_train_step_batched_host": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _pp, _gradp, _statp, _vp,
+                                                C.c_uint32, _vp]),
     "tgs_autotune": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _pp, C.c_char_p, _vp]),
     "tgs_preprocess": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _vp, _vp, _vp]),
     "tgs_bin": (C.c_int32, [_ctx_p, _vp, _vp, C.c_int64, _camp, C.c_int32, _vp, _vp, _vp,
@@ -117,10 +125,13 @@ SIGNATURES = {
     "tgs_count_hits": (C.c_int32, [_ctx_p, C.POINTER(tgs_gaussians), _camp, C.c_int32, _vp, _vp]),
     "tgs_significance": (C.c_int32, [_ctx_p, C.POINTER(tgs_gaussians), _vp, C.c_double, _vp, _vp]),
     "tgs_prune_select": (C.c_int32, [_ctx_p, _vp, C.c_int64, C.c_double, _vp, _vp]),
+    "tgs_prune_schedule": (C.c_int32, [C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_double)]),
     "tgs_set_profiling": (C.c_int32, [_ctx_p, C.c_int32]),
+    "tgs_measure_peaks": (C.c_int32, [C.POINTER(tgs_peaks), _vp]),
     "tgs_stage_times": (C.c_int32, [_ctx_p, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),
     "tgs_stage_name": (C.c_char_p, [_ctx_p, C.c_int32]),
     "tgs_kernels_per_step": (C.c_int64, [_ctx_p]),
+    "tgs_arena_bytes": (C.c_size_t, [_ctx_p]),
     "tgs_num_tiles": (C.c_int64, [_ctx_p, _camp, C.c_int32]),
     "tgs_workspace_bytes": (C.c_size_t, [_ctx_p, C.c_int64, _camp, C.c_int32]),
 }

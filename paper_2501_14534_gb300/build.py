@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtgs.so")
-SOURCES = ["preprocess.cu", "sort.cu", "blend.cu", "fused.cu", "api.cu", "noalloc.cu", "significance.cu", "ssim.cu", "compact.cu", "half.cu"]
+SOURCES = ["preprocess.cu", "sort.cu", "blend.cu", "fused.cu", "api.cu", "noalloc.cu", "significance.cu", "ssim.cu", "compact.cu", "half.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

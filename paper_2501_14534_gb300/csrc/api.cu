@@ -43,10 +43,27 @@ struct tgs_ctx {
     int state_tile = 0;
     uint32_t *state_ids = nullptr;  // where the sorted ids of that binning live
     uint32_t *sorted_tk = nullptr;  // sorted tile keys of the last binning
-    // captured batched step
-    cudaGraphExec_t graph = nullptr;
-    std::vector<unsigned char> graph_key;
+    // captured batched steps, keyed by every argument the recorded launches depend on
+    // (a few, so that alternating input buffers each keep their graph)
+    struct Graph {
+        std::vector<unsigned char> key;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t used = 0;
+    };
+    std::vector<Graph> graphs;
+    uint64_t graph_clock = 0;
     cudaStream_t side = nullptr;
+    // tgs_train_step_batched_host: two sets of device copies of a step's inputs, filled on an
+    // upload stream while the previous step computes
+    struct Stage {
+        Buf params, targets;
+        cudaEvent_t copied = nullptr, consumed = nullptr;
+        bool used = false;
+    };
+    Stage stage[2];
+    int stage_next = 0;
+    cudaStream_t upload = nullptr;
+    Buf lossbuf;
     // measurement
     bool profiling = false;
     cudaEvent_t stage_ev[TGS_MAX_STAGES + 1] = {};
@@ -58,6 +75,12 @@ struct tgs_ctx {
 namespace {
 
 tgs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TGS_OK : TGS_ERR_CUDA; }
+
+void drop_graphs(tgs_ctx *c) {
+    for (auto &gr : c->graphs)
+        if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    c->graphs.clear();
+}
 
 #define TGS_CHECK(x)                                   \
     do {                                               \
@@ -345,7 +368,7 @@ void tgs_default_config(tgs_config *cfg) {
     cfg->eps_sh = 0.1f;
     cfg->near_plane = 0.2f;
     cfg->key_capacity = 0;
-    cfg->spin_limit = (int64_t)1 << 22;
+    cfg->spin_limit = 0;  // reserved
     cfg->ssim_lambda = 0.2f;
 }
 
@@ -355,10 +378,11 @@ const char *tgs_status_string(tgs_status s) {
         case TGS_ERR_INVALID_ARG: return "invalid argument";
         case TGS_ERR_CUDA: return "CUDA runtime error";
         case TGS_ERR_CAPACITY: return "key capacity exceeded";
-        case TGS_ERR_TIMEOUT: return "bounded device wait ran out";
+        case TGS_ERR_TIMEOUT: return "reserved status (timeout)";
         case TGS_ERR_OOM: return "out of device memory";
         case TGS_ERR_NOT_SUPPORTED: return "not supported";
         case TGS_ERR_SCRATCH_LIMIT: return "input exceeds the fixed scratch of tgs_bin_noalloc";
+        case TGS_ERR_INCONSISTENT: return "device consistency check of the key counts failed";
         default: return "unknown status";
     }
 }
@@ -399,7 +423,15 @@ void tgs_destroy(tgs_ctx *c) {
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     if (c->h_counts) cudaFreeHost(c->h_counts);
-    if (c->graph) cudaGraphExecDestroy(c->graph);
+    drop_graphs(c);
+    for (auto &sg : c->stage) {
+        if (sg.params.p) cudaFree(sg.params.p);
+        if (sg.targets.p) cudaFree(sg.targets.p);
+        if (sg.copied) cudaEventDestroy(sg.copied);
+        if (sg.consumed) cudaEventDestroy(sg.consumed);
+    }
+    if (c->lossbuf.p) cudaFree(c->lossbuf.p);
+    if (c->upload) cudaStreamDestroy(c->upload);
     if (c->side) cudaStreamDestroy(c->side);
     for (cudaEvent_t e : c->stage_ev)
         if (e) cudaEventDestroy(e);
@@ -416,11 +448,7 @@ tgs_status tgs_set_config(tgs_ctx *c, const tgs_config *cfg) {
     if (!c || !cfg || !valid_cfg(*cfg)) return TGS_ERR_INVALID_ARG;
     c->cfg = *cfg;
     c->state_valid = false;
-    if (c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-        c->graph_key.clear();
-    }
+    drop_graphs(c);
     return TGS_OK;
 }
 
@@ -433,7 +461,7 @@ tgs_status tgs_poll_status(tgs_ctx *c, tgs_stream stream) {
     h = c->h_counts[2];
     TGS_CHECK(cudaMemsetAsync(c->status.p, 0, sizeof(uint32_t), st));
     TGS_CHECK(cudaStreamSynchronize(st));
-    if (h & kStatusTimeout) return TGS_ERR_TIMEOUT;
+    if (h & kStatusInconsistent) return TGS_ERR_INCONSISTENT;
     if (h & kStatusCapacity) return TGS_ERR_CAPACITY;
     return TGS_OK;
 }
@@ -692,6 +720,18 @@ tgs_status tgs_significance(tgs_ctx *c, const tgs_gaussians *g, const uint32_t *
     return last_error();
 }
 
+tgs_status tgs_prune_schedule(int32_t rounds, double first, double decay, double *fractions) {
+    if (rounds < 0 || !(first >= 0.0 && first <= 1.0) || !(decay >= 0.0 && decay <= 1.0) ||
+        (rounds > 0 && !fractions))
+        return TGS_ERR_INVALID_ARG;
+    double f = first;
+    for (int r = 0; r < rounds; r++) {
+        fractions[r] = f;
+        f *= decay;
+    }
+    return TGS_OK;
+}
+
 tgs_status tgs_prune_select(tgs_ctx *c, const float *scores, int64_t n, double fraction, uint8_t *prune,
                             tgs_stream stream) {
     if (!c || n < 0 || !(fraction >= 0.0 && fraction <= 1.0)) return TGS_ERR_INVALID_ARG;
@@ -767,11 +807,7 @@ tgs_status tgs_plan(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, 
     c->cfg.key_capacity = cap;
     TGS_TRY(ensure_keys(c, cap, cb.total_tiles, st));
     if (keys_out) *keys_out = K;
-    if (c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-        c->graph_key.clear();
-    }
+    drop_graphs(c);
     return last_error();
 }
 
@@ -931,10 +967,16 @@ tgs_status tgs_train_step_batched(tgs_ctx *c, const tgs_gaussians *g, const tgs_
     put(&c->cfg, sizeof c->cfg);
     void *arena[] = {c->splats.p, c->tk0.p, c->hist.p, c->images.p, c->pixstate.p};
     put(arena, sizeof arena);
-    if (!c->graph || key != c->graph_key) {
-        if (c->graph) {
-            cudaGraphExecDestroy(c->graph);
-            c->graph = nullptr;
+    tgs_ctx::Graph *hit = nullptr;
+    for (auto &gr : c->graphs)
+        if (gr.key == key) hit = &gr;
+    if (!hit) {
+        constexpr size_t kMaxGraphs = 4;
+        if (c->graphs.size() >= kMaxGraphs) {  // evict the least recently used
+            auto lru = std::min_element(c->graphs.begin(), c->graphs.end(),
+                                        [](const tgs_ctx::Graph &a, const tgs_ctx::Graph &b) { return a.used < b.used; });
+            cudaGraphExecDestroy(lru->exec);
+            c->graphs.erase(lru);
         }
         cudaGraph_t graph = nullptr;
         TGS_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -945,24 +987,104 @@ tgs_status tgs_train_step_batched(tgs_ctx *c, const tgs_gaussians *g, const tgs_
             return s;
         }
         TGS_CHECK(e);
-        e = cudaGraphInstantiate(&c->graph, graph, 0);
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
         TGS_CHECK(e);
-        c->graph_key = key;
+        c->graphs.push_back(tgs_ctx::Graph{key, exec, 0});
+        hit = &c->graphs.back();
     }
-    TGS_CHECK(cudaGraphLaunch(c->graph, st));
+    hit->used = ++c->graph_clock;
+    TGS_CHECK(cudaGraphLaunch(hit->exec, st));
     return TGS_OK;
+}
+
+tgs_status tgs_train_step_batched_host(tgs_ctx *c, const tgs_gaussians *gh, const tgs_camera *cams, int32_t V,
+                                       const float *const *targets_host, const tgs_grads *grads,
+                                       const tgs_stats *stats, float *loss_host, uint32_t flags, tgs_stream stream) {
+    if (!c || !gh || !cams || !targets_host || V <= 0 || V > kMaxViews || gh->n < 0 ||
+        gh->param_dtype != TGS_PARAM_F32)
+        return TGS_ERR_INVALID_ARG;
+    for (int v = 0; v < V; v++)
+        if (!targets_host[v] || cams[v].width <= 0 || cams[v].height <= 0) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (capturing(st)) return TGS_ERR_NOT_SUPPORTED;
+    const int64_t n = gh->n;
+    // the parameter arrays, each in a 256-byte aligned segment of one device buffer
+    struct Arr {
+        const void *src;
+        size_t bytes;
+    } arr[9] = {{gh->means, 12 * (size_t)n},        {gh->log_scales, 12 * (size_t)n},
+                {gh->quats, 16 * (size_t)n},        {gh->opacity_logits, 4 * (size_t)n},
+                {gh->sh_dc, 12 * (size_t)n},        {gh->sh_rest, 180 * (size_t)n},
+                {gh->mask_logits, 4 * (size_t)n},   {gh->sh_mask_logits, 12 * (size_t)n},
+                {gh->sh_degree, (size_t)n}};
+    if (gh->sh_degree_max == 0 || !gh->sh_rest) arr[5].src = nullptr;
+    size_t off[9], pb = 0;
+    for (int i = 0; i < 9; i++) {
+        off[i] = pb;
+        if (arr[i].src) pb += (arr[i].bytes + 255) / 256 * 256;
+    }
+    size_t toff[kMaxViews], tb = 0;
+    for (int v = 0; v < V; v++) {
+        toff[v] = tb;
+        tb += (12 * (size_t)cams[v].width * cams[v].height + 255) / 256 * 256;
+    }
+    tgs_ctx::Stage &sg = c->stage[c->stage_next];
+    c->stage_next ^= 1;
+    if (!c->upload) TGS_CHECK(cudaStreamCreateWithFlags(&c->upload, cudaStreamNonBlocking));
+    if (!sg.copied) TGS_CHECK(cudaEventCreateWithFlags(&sg.copied, cudaEventDisableTiming));
+    if (!sg.consumed) TGS_CHECK(cudaEventCreateWithFlags(&sg.consumed, cudaEventDisableTiming));
+    if (sg.params.bytes < pb || sg.targets.bytes < tb) {
+        // growing frees the old buffers: no copy or step may still use them
+        TGS_CHECK(cudaStreamSynchronize(c->upload));
+        TGS_CHECK(cudaStreamSynchronize(st));
+        TGS_TRY(ensure(sg.params, pb, st));
+        TGS_TRY(ensure(sg.targets, tb, st));
+        sg.used = false;
+        drop_graphs(c);  // the graphs of the old buffers' addresses
+    }
+    TGS_TRY(ensure(c->lossbuf, sizeof(float), st));
+    // the copies wait for the step that last read this set of buffers
+    if (sg.used) TGS_CHECK(cudaStreamWaitEvent(c->upload, sg.consumed, 0));
+    unsigned char *pd = as<unsigned char>(sg.params);
+    for (int i = 0; i < 9; i++)
+        if (arr[i].src && arr[i].bytes)
+            TGS_CHECK(cudaMemcpyAsync(pd + off[i], arr[i].src, arr[i].bytes, cudaMemcpyHostToDevice, c->upload));
+    unsigned char *td = as<unsigned char>(sg.targets);
+    const float *tdev[kMaxViews];
+    for (int v = 0; v < V; v++) {
+        const size_t bytes = 12 * (size_t)cams[v].width * cams[v].height;
+        TGS_CHECK(cudaMemcpyAsync(td + toff[v], targets_host[v], bytes, cudaMemcpyHostToDevice, c->upload));
+        tdev[v] = reinterpret_cast<const float *>(td + toff[v]);
+    }
+    TGS_CHECK(cudaEventRecord(sg.copied, c->upload));
+    TGS_CHECK(cudaStreamWaitEvent(st, sg.copied, 0));
+    tgs_gaussians gd = *gh;
+    auto dp = [&](int i) { return arr[i].src ? reinterpret_cast<const float *>(pd + off[i]) : nullptr; };
+    gd.means = dp(0);
+    gd.log_scales = dp(1);
+    gd.quats = dp(2);
+    gd.opacity_logits = dp(3);
+    gd.sh_dc = dp(4);
+    gd.sh_rest = dp(5);
+    gd.mask_logits = dp(6);
+    gd.sh_mask_logits = dp(7);
+    gd.sh_degree = arr[8].src ? pd + off[8] : nullptr;
+    float *loss_dev = as<float>(c->lossbuf);
+    const tgs_status s = tgs_train_step_batched(c, &gd, cams, V, tdev, nullptr, grads, stats, loss_dev, flags, stream);
+    TGS_CHECK(cudaEventRecord(sg.consumed, st));
+    sg.used = true;
+    if (s != TGS_OK) return s;
+    if (loss_host) TGS_CHECK(cudaMemcpyAsync(loss_host, loss_dev, sizeof(float), cudaMemcpyDeviceToHost, st));
+    return last_error();
 }
 
 tgs_status tgs_set_profiling(tgs_ctx *c, int32_t on) {
     if (!c) return TGS_ERR_INVALID_ARG;
     if (on && !c->stage_ev[0])
         for (auto &e : c->stage_ev) TGS_CHECK(cudaEventCreate(&e));
-    if ((bool)on != c->profiling && c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-        c->graph_key.clear();
-    }
+    if ((bool)on != c->profiling) drop_graphs(c);
     c->profiling = on != 0;
     return TGS_OK;
 }
@@ -982,6 +1104,18 @@ const char *tgs_stage_name(tgs_ctx *c, int32_t i) {
 }
 
 int64_t tgs_kernels_per_step(const tgs_ctx *c) { return c ? c->kernels_per_step : -1; }
+
+size_t tgs_arena_bytes(const tgs_ctx *c) {
+    if (!c) return 0;
+    const Buf *bufs[] = {&c->splats, &c->radii, &c->tt, &c->dbits, &c->pos, &c->ck0, &c->cv0, &c->ck1,
+                         &c->cv1, &c->offsets, &c->tk0, &c->tv0, &c->tk1, &c->tv1, &c->ranges, &c->hist,
+                         &c->partials, &c->sgrads, &c->counts, &c->status, &c->pixstate, &c->dimg,
+                         &c->images, &c->items, &c->kmask, &c->viskeys, &c->ssim, &c->cbuf, &c->lossbuf,
+                         &c->stage[0].params, &c->stage[0].targets, &c->stage[1].params, &c->stage[1].targets};
+    size_t b = 0;
+    for (const Buf *x : bufs) b += x->bytes;
+    return b;
+}
 
 tgs_status tgs_autotune(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
                         const float *const *targets, const char *cache_path, tgs_stream stream) {
@@ -1016,9 +1150,16 @@ tgs_status tgs_autotune(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *ca
     const int tiles[3] = {8, 16, 32}, ppts[3] = {1, 2, 4};
     float best = 1e30f;
     tgs_config best_cfg = c->cfg, base = c->cfg;
-    cudaEvent_t e0, e1;
-    TGS_CHECK(cudaEventCreate(&e0));
-    TGS_CHECK(cudaEventCreate(&e1));
+    struct Events {  // destroyed on every return path
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~Events() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    TGS_CHECK(cudaEventCreate(&ev.e[0]));
+    TGS_CHECK(cudaEventCreate(&ev.e[1]));
+    cudaEvent_t e0 = ev.e[0], e1 = ev.e[1];
     for (int tl : tiles)
         for (int pp : ppts) {
             tgs_config cf = base;
@@ -1043,8 +1184,6 @@ tgs_status tgs_autotune(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *ca
                 best_cfg = cf;
             }
         }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     best_cfg.key_capacity = 0;
     TGS_TRY(tgs_set_config(c, &best_cfg));
     TGS_TRY(tgs_plan(c, g, cams, V, 1.25, nullptr));

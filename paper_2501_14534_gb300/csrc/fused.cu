@@ -119,15 +119,31 @@ template <int TILE, int PPT, bool HITS>
 void fused_launch_t(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const uint32_t *order,
                     int *counter, const CamBatch &cb, const PixPtrs &px, const float *bg, float *sgrads,
                     float *loss, uint16_t *vis_keys, uint32_t *hits, uint32_t n_gauss, cudaStream_t st) {
-    static std::once_flag once;
-    static int per_sm = 1, sms = 1;
-    std::call_once(once, [] {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        per_sm = fused_blocks_per_sm<TILE, PPT, HITS>();
-    });
-    int grid = sms * per_sm;
+    // persistent grid: SMs x resident CTAs per SM, found once per device
+    constexpr int kDevices = 64;
+    static std::mutex mu;
+    static int grid_of[kDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    int grid = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        const bool cached = dev >= 0 && dev < kDevices && grid_of[dev] > 0;
+        if (cached) {
+            grid = grid_of[dev];
+        } else {
+            int sms = 1;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+                cudaGetLastError();
+                sms = 1;
+            }
+            grid = sms * fused_blocks_per_sm<TILE, PPT, HITS>();
+            if (dev >= 0 && dev < kDevices) grid_of[dev] = grid;
+        }
+    }
     if (grid > cb.total_tiles) grid = cb.total_tiles;
     if (grid < 1) grid = 1;
     count_launch();

@@ -450,13 +450,20 @@ __device__ __forceinline__ int select_bit(uint32_t lo, uint32_t hi, uint32_t k) 
 // (coalesced stores, balanced work): the lane of position p finds its record by binary search
 // over the prefix sums, and its tile as the k-th set bit of the record's kept-tile mask.
 // Records of more than 64 rect tiles (no mask) are done by the whole warp, 32 tiles at a time.
+//
+// The work is bounded by the data the count pass scanned, whatever the count buffer holds: a
+// block first checks that its records' counts add up to the keys the count pass scanned for
+// it (block_off[b + 1] - block_off[b]) and that no record claims more tiles than the batch
+// has; otherwise it sets kStatusInconsistent and emits nothing. A warp also stops at the key
+// capacity, so a count beyond the capacity costs no more than the capacity.
 __global__ void __launch_bounds__(kScanThreads)
 k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ block_off,
        const uint32_t *n_dev, int64_t n_cap, const KeyInfo ki, const float4 *__restrict__ splats,
        uint32_t n_gauss, uint32_t n_magic, const __grid_constant__ CamBatch cb, uint32_t *__restrict__ tile_keys,
        uint32_t *__restrict__ tile_vals, const uint32_t *K_dev, int64_t key_cap, uint32_t *status) {
     constexpr int NW = kScanThreads / 32;
-    __shared__ uint32_t s_wtot[NW];
+    __shared__ uint64_t s_wtot[NW];
+    __shared__ int s_bad;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (int64_t)*K_dev > key_cap) atomicOr(status, kStatusCapacity);
@@ -464,20 +471,41 @@ k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ blo
     const int64_t base = (int64_t)blockIdx.x * kScanTile;
     if (base >= n) return;  // uniform across the block
     const int64_t wbase = base + (int64_t)w * 32 * kScanItems;
-    uint32_t wsum = 0u;
+    uint64_t wsum = 0u;
+    bool bad = false;
 #pragma unroll
     for (int q = 0; q < kScanItems; q++) {
         const int64_t j = wbase + q * 32 + lane;
-        wsum += j < n ? ki.cnt[j] : 0u;
+        const uint32_t c = j < n ? ki.cnt[j] : 0u;
+        bad = bad || c > (uint32_t)cb.total_tiles;
+        wsum += c;
     }
-    wsum = __reduce_add_sync(full, wsum);
-    if (lane == 0) s_wtot[w] = wsum;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) wsum += __shfl_xor_sync(full, wsum, o);
+    bad = __any_sync(full, bad);
+    if (lane == 0) s_wtot[w] = bad ? ~(uint64_t)0 : wsum;
     __syncthreads();
+    if (threadIdx.x == 0) {
+        // the counts must add up to the keys the count pass scanned for this block
+        uint64_t sum = 0u;
+        bool b = false;
+        for (int q = 0; q < NW; q++) {
+            b = b || s_wtot[q] == ~(uint64_t)0;
+            sum += s_wtot[q];
+        }
+        const uint64_t end = blockIdx.x + 1 < gridDim.x ? block_off[blockIdx.x + 1] : *K_dev;
+        b = b || end < block_off[blockIdx.x] || sum != end - block_off[blockIdx.x];
+        if (b) atomicOr(status, kStatusInconsistent);
+        s_bad = b ? 1 : 0;
+    }
+    __syncthreads();
+    if (s_bad) return;  // uniform across the block
     int64_t off = (int64_t)block_off[blockIdx.x];
-    for (int q = 0; q < w; q++) off += s_wtot[q];
+    for (int q = 0; q < w; q++) off += (int64_t)s_wtot[q];
     const int B = cb.tile, lb = __ffs(cb.tile) - 1;
 #pragma unroll 1
     for (int q = 0; q < kScanItems; q++) {
+        if (off >= key_cap) break;  // uniform across the warp: every later key is beyond capacity
         const int64_t j = wbase + q * 32 + lane;
         const bool valid = j < n;
         const uint32_t cnt = valid ? ki.cnt[j] : 0u;
@@ -546,7 +574,8 @@ k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ blo
                 kept += __popc(kb);
             }
         }
-        for (uint32_t p0 = 0; p0 < total; p0 += 32) {
+        const uint32_t lim = (int64_t)total < key_cap - off ? total : (uint32_t)(key_cap - off);
+        for (uint32_t p0 = 0; p0 < lim; p0 += 32) {
             const uint32_t p = p0 + (uint32_t)lane;
             int o = 0;
 #pragma unroll

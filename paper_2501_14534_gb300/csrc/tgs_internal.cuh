@@ -75,7 +75,7 @@ inline void count_launch(int k = 1) { g_launches += k; }
 // Device status word bits.
 constexpr uint32_t kNoDepth = 0xffffffffu;  // depth key of a record that is not visible
 constexpr uint32_t kStatusCapacity = 1u;
-constexpr uint32_t kStatusTimeout = 2u;
+constexpr uint32_t kStatusInconsistent = 2u;  // a consistency check of scratch data failed
 
 __device__ __forceinline__ int view_of_tile(const CamBatch &cb, int gt) {
     int lo = 0, hi = cb.V - 1;

@@ -32,11 +32,11 @@ def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _check_tensor(t, name, dtype=torch.float32):
+def _check_tensor(t, name, dtype=torch.float32, host=False):
     if t is None:
         return
-    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
-        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if t.is_cuda == host or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {'host' if host else 'CUDA'} {dtype} tensor")
 
 
 @dataclasses.dataclass
@@ -62,11 +62,13 @@ class Gaussians:
         """FP16 storage: every parameter array holds float16 (render path only)."""
         return self.means.dtype == torch.float16
 
-    def struct(self):
+    def struct(self, host=False):
+        """The tgs_gaussians of these tensors (device tensors; host=True: host tensors, for
+        tgs_train_step_batched_host)."""
         dt = torch.float16 if self.half else torch.float32
         for k in PARAM_KEYS:
-            _check_tensor(getattr(self, k), k, dt)
-        _check_tensor(self.sh_degree, "sh_degree", torch.uint8)
+            _check_tensor(getattr(self, k), k, dt, host)
+        _check_tensor(self.sh_degree, "sh_degree", torch.uint8, host)
         deg = self.sh_degree_max
         if deg is None:
             deg = 3 if self.sh_rest is not None else 0
@@ -354,6 +356,22 @@ class Rasterizer:
             C.byref(self._stats_struct(stats)), _p(loss), flags, _stream()),
             "tgs_train_step_batched")
 
+    def train_step_batched_host(self, g_host: Gaussians, cams, targets_host, grads, stats=None, loss_host=None,
+                                graph=False, cams_struct=None):
+        """The batched step from host tensors (pinned for asynchronous copies): the library
+        copies the parameters and targets to the device, runs the step and copies the loss
+        into loss_host (a host float tensor [1]); see tgs_train_step_batched_host."""
+        flags = B.TGS_USE_GRAPH if graph else 0
+        for i, t in enumerate(targets_host):
+            _check_tensor(t, f"targets_host[{i}]", host=True)
+        if loss_host is not None:
+            _check_tensor(loss_host, "loss_host", host=True)
+        camarr = cams_struct if cams_struct is not None else cameras_array(cams)
+        B.check(B.lib.tgs_train_step_batched_host(
+            self._h, C.byref(g_host.struct(host=True)), camarr, len(camarr), _ptr_array(targets_host),
+            C.byref(self._grad_struct(grads)), C.byref(self._stats_struct(stats)), _p(loss_host), flags,
+            _stream()), "tgs_train_step_batched_host")
+
     # ---- FP16 storage ----
 
     @staticmethod
@@ -409,10 +427,11 @@ class Rasterizer:
 
     @staticmethod
     def pruning_fractions(rounds=6, first=0.6, decay=0.7):
-        """Fraction of the Gaussians each significance pruning round removes: the first rate
-        decayed by a constant factor per round (Sec. "Implementation details": 6 rounds, 60 %
-        first, decay 0.7)."""
-        return [first * decay ** k for k in range(rounds)]
+        """Fraction of the Gaussians each significance pruning round removes (tgs_prune_schedule;
+        Sec. "Implementation details": 6 rounds, 60 % first, decay 0.7)."""
+        out = (C.c_double * max(rounds, 1))()
+        B.check(B.lib.tgs_prune_schedule(int(rounds), float(first), float(decay), out), "tgs_prune_schedule")
+        return [float(out[k]) for k in range(rounds)]
 
     def prune_select(self, scores, fraction):
         """bool [n]: the floor(fraction n) lowest scores (equal scores: lower index first)."""
@@ -434,6 +453,18 @@ class Rasterizer:
 
     def kernels_per_step(self):
         return int(B.lib.tgs_kernels_per_step(self._h))
+
+    def arena_bytes(self):
+        """Device bytes of this context's scratch arena."""
+        return int(B.lib.tgs_arena_bytes(self._h))
+
+    @staticmethod
+    def measure_peaks():
+        """FP32 FMA (scalar and packed) and SFU (ex2, rcp) rates of the current GPU, per second
+        (tgs_measure_peaks)."""
+        p = B.tgs_peaks()
+        B.check(B.lib.tgs_measure_peaks(C.byref(p), _stream()), "tgs_measure_peaks")
+        return {k: getattr(p, k) for k, _ in p._fields_}
 
     def autotune(self, g: Gaussians, cams, targets, cache_path=None):
         B.check(B.lib.tgs_autotune(self._h, C.byref(g.struct()), cameras_array(cams), len(cams),

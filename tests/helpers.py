@@ -6,7 +6,8 @@ Comparison rules (tolerances of the parity tests):
     oracle puts within 1e-5 relative of an integer boundary (counted);
   - images: max |gpu - oracle| <= 1e-4 over pixels whose every blend decision is clear of its
     threshold by more than the float32 uncertainty (the oracle's per-pixel margin >= 1);
-  - gradients: per tensor ||g - g*|| / ||g*|| <= 1e-3.
+  - gradients: per tensor ||g - g*|| / ||g*|| <= 1e-3, and per element
+    |g - g*| <= 1e-3 |g*| + 1e-3 max |g*| (check_grad).
 """
 import numpy as np
 
@@ -57,3 +58,31 @@ def image_compare(gpu, ref, margin):
     diff = np.abs(np.asarray(gpu, np.float64) - ref).max(axis=0)
     m = float(diff[clear].max()) if clear.any() else 0.0
     return m, 1.0 - clear.mean()
+
+
+def elem_err(a, b, rtol=GRAD_RTOL, stol=GRAD_RTOL):
+    """Largest |a - b| / (rtol |b| + stol max|b|) over the elements (<= 1 passes); b is the
+    reference. An all-zero reference requires an all-zero a."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    scale = float(np.abs(b).max()) if b.size else 0.0
+    if scale == 0.0:
+        return 0.0 if not np.any(a) else float("inf")
+    return float((np.abs(a - b) / (rtol * np.abs(b) + stol * scale)).max())
+
+
+def check_grad(got, ref, name, rel=GRAD_RTOL, elem=GRAD_RTOL):
+    """Per-tensor relative L2 error <= rel and per-element |g - g*| <= elem |g*| + elem max|g*|."""
+    e = rel_err(got, ref)
+    r = elem_err(got, ref, elem, elem)
+    assert e <= rel and r <= 1.0, (name, "rel", e, "elem", r)
+    return e, r
+
+
+def zero_margin_pixels(dl, margin):
+    """dL/dimage with the pixels whose blend decisions are within the float32 uncertainty set
+    to 0: every gradient term of a pixel is proportional to its dL/dC, so such a pixel then
+    contributes nothing on either side, whichever way its decisions fall."""
+    dl = np.array(dl, copy=True)
+    dl[:, np.asarray(margin) < 1.0] = 0.0
+    return dl

@@ -40,7 +40,7 @@ def test_struct_layouts_match_header(lib, tmp_path):
     structs = {"tgs_config": lib.tgs_config, "tgs_gaussians": lib.tgs_gaussians,
                "tgs_camera": lib.tgs_camera, "tgs_view_out": lib.tgs_view_out,
                "tgs_grads": lib.tgs_grads, "tgs_stats": lib.tgs_stats,
-               "tgs_half_params": lib.tgs_half_params}
+               "tgs_half_params": lib.tgs_half_params, "tgs_peaks": lib.tgs_peaks}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tgs.h"', "int main(void){"]
     for s, cls in structs.items():
         lines.append(f'printf("{s} %zu\\n", sizeof({s}));')

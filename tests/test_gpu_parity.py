@@ -8,8 +8,8 @@ import pytest
 import oracle
 from paper_2501_14534_gb300 import synth
 
-from helpers import (GRAD_RTOL, IMAGE_ATOL, cull_data, gpu_lists, image_compare, rel_err,
-                     splats_to_oracle)
+from helpers import (GRAD_RTOL, IMAGE_ATOL, check_grad, cull_data, gpu_lists, image_compare,
+                     rel_err, splats_to_oracle, zero_margin_pixels)
 
 pytestmark = pytest.mark.gpu
 
@@ -24,6 +24,11 @@ def R():
     build.build()
     from paper_2501_14534_gb300 import rasterizer as R
     return R
+
+
+# Largest fraction of pixels an end-to-end image comparison (float32 preprocess on the GPU,
+# float64 in the oracle) may exclude as decision-margin cases.
+EXCL_E2E = 0.05
 
 
 def settings_for(tile=16, eps=(0.05, 0.1), support=0, bg=(0.0, 0.0, 0.0)):
@@ -159,6 +164,7 @@ def test_blend_forward_matches_oracle_on_same_records(R, case):
         ref = oracle.blend(gs, cam.width, cam.height, st.tile, st.bg, margins=True, lists=lists)
         img = np_(outs[v]["image"])
         m, excl = image_compare(img, ref["image"], ref["margin"])
+        print(f"EXCL blend_same_records {case} view={v} {excl:.3e}")
         assert m <= IMAGE_ATOL, (m, excl)
         assert excl < 2e-3
         clear = ref["margin"] >= 1.0
@@ -179,8 +185,9 @@ def test_forward_end_to_end_matches_fp64_oracle(R, case):
     for v, cam in enumerate(cams):
         ref = oracle.render(scene, cam, st, margins=True)
         m, excl = image_compare(np_(outs[v]["image"]), ref["image"], ref["margin"])
+        print(f"EXCL forward_e2e {case} view={v} {excl:.3e}")
         assert m <= IMAGE_ATOL, (m, excl)
-        assert excl < 0.05, excl
+        assert excl < EXCL_E2E, excl
         assert np.array_equal(np_(outs[v]["radii"]) > 0, ref["splats"]["radius"] > 0) or \
             np.sum((np_(outs[v]["radii"]) > 0) != (ref["splats"]["radius"] > 0)) <= 2
 
@@ -211,20 +218,24 @@ def test_blend_backward_matches_oracle_on_same_records(R, case):
     splats, radii = rast.preprocess(g, cams)
     ids, _, ranges, K = rast.bin(splats, radii, g.n, cams, want_keys=False)
     outs = rast.blend_forward(splats, ids, ranges, cams)
-    rng = np.random.default_rng(7)
-    dls = [rng.normal(size=(3, c.height, c.width)).astype(np.float32) for c in cams]
-    sg = np_(rast.blend_backward(splats, ids, ranges, cams, outs,
-                                 [torch.from_numpy(d).cuda() for d in dls]))
     rec, rad = np_(splats), np_(radii)
     n = g.n
+    rng = np.random.default_rng(7)
+    dls, gss = [], []
     for v, cam in enumerate(cams):
         gs = splats_to_oracle(rec[v * n:(v + 1) * n], rad[v * n:(v + 1) * n])
-        ref = oracle.blend_backward(gs, cam.width, cam.height, dls[v], st.tile, st.bg)
+        fwd = oracle.blend(gs, cam.width, cam.height, st.tile, st.bg, margins=True)
+        d = rng.normal(size=(3, cam.height, cam.width))
+        dls.append(zero_margin_pixels(d, fwd["margin"]).astype(np.float32))
+        gss.append(gs)
+    sg = np_(rast.blend_backward(splats, ids, ranges, cams, outs,
+                                 [torch.from_numpy(d).cuda() for d in dls]))
+    for v, cam in enumerate(cams):
+        ref = oracle.blend_backward(gss[v], cam.width, cam.height, dls[v], st.tile, st.bg)
         got = sg[v * n:(v + 1) * n, :9]
         for name, cols in [("mean2d", [0, 1]), ("conic", [2, 3, 4]), ("opacity", [5]),
                            ("rgb", [6, 7, 8])]:
-            e = rel_err(got[:, cols], ref[:, cols])
-            assert e <= GRAD_RTOL, (name, e)
+            check_grad(got[:, cols], ref[:, cols], name)
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -246,8 +257,7 @@ def test_preprocess_backward_matches_oracle_on_same_splat_grads(R, case):
         g9[rad[v * n:(v + 1) * n] == 0] = 0.0
         oracle.preprocess_backward(scene, cam, st, g9, ref, rstats)
     for k, t in grads.items():
-        e = rel_err(np_(t), ref[k])
-        assert e <= 1e-4, (k, e)
+        check_grad(np_(t), ref[k], k, rel=1e-4)
     assert np.array_equal(np_(stats["vis_count"]), rstats["count"])
     assert np.array_equal(np_(stats["max_radius"]), rstats["max_radius"])
     np.testing.assert_allclose(np_(stats["grad_norm_accum"]), rstats["accum"], rtol=1e-5, atol=1e-6)
@@ -260,12 +270,14 @@ def test_backward_end_to_end_matches_fp64_oracle(R, case):
     g = gpu_scene(R, scene)
     outs = rast.forward(g, cams)
     rng = np.random.default_rng(11)
-    dls = [rng.normal(size=(3, c.height, c.width)).astype(np.float32) for c in cams]
+    # pixels with a decision within the float32 uncertainty get dL/dC = 0 on both sides
+    dls = [zero_margin_pixels(rng.normal(size=(3, c.height, c.width)),
+                              oracle.render(scene, c, st, margins=True)["margin"]).astype(np.float32)
+           for c in cams]
     grads, stats = rast.backward(g, cams, outs, [torch.from_numpy(d).cuda() for d in dls])
     ref, rstats, _ = oracle.grad(scene, cams, st, [d.astype(np.float64) for d in dls])
     for k, t in grads.items():
-        e = rel_err(np_(t), ref[k])
-        assert e <= GRAD_RTOL, (k, e)
+        check_grad(np_(t), ref[k], k)
     cnt = np_(stats["vis_count"])
     assert np.sum(cnt != rstats["count"]) <= 2
     same = cnt == rstats["count"]
@@ -300,16 +312,17 @@ def test_autograd_function_matches_oracle(R):
             t.requires_grad_(True)
     imgs = R.rasterize(rast, g, cams)
     rng = np.random.default_rng(5)
-    ws = [rng.normal(size=(3, c.height, c.width)) for c in cams]
-    loss = sum((im * torch.from_numpy(w).float().cuda()).sum() for im, w in zip(imgs, ws))
+    ws = [zero_margin_pixels(rng.normal(size=(3, c.height, c.width)),
+                             oracle.render(scene, c, st, margins=True)["margin"]).astype(np.float32)
+          for c in cams]
+    loss = sum((im * torch.from_numpy(w).cuda()).sum() for im, w in zip(imgs, ws))
     loss.backward()
-    ref, _, _ = oracle.grad(scene, cams, st, ws)
+    ref, _, _ = oracle.grad(scene, cams, st, [w.astype(np.float64) for w in ws])
     for k in R.PARAM_KEYS:
         t = getattr(g, k)
         if t is None:
             continue
-        e = rel_err(np_(t.grad), ref[k])
-        assert e <= GRAD_RTOL, (k, e)
+        check_grad(np_(t.grad), ref[k], k)
 
 
 def batched_case(n=4000):
@@ -339,13 +352,27 @@ def test_batched_train_step_matches_oracle(R, tile, ppt, fused):
     refs = [oracle.render(scene, c, st, margins=True) for c in cams]
     for v in range(len(cams)):
         m, excl = image_compare(np_(images[v]), refs[v]["image"], refs[v]["margin"])
-        assert m <= IMAGE_ATOL and excl < 0.05
+        assert m <= IMAGE_ATOL and excl < EXCL_E2E, (m, excl)
+        print(f"EXCL batched_step tile={tile} ppt={ppt} view={v} {excl:.3e}")
     ref_loss, dls = oracle.l1([r["image"] for r in refs], targets)
     assert abs(float(loss.item()) - ref_loss) <= 1e-5 * abs(ref_loss)
+    # gradients: a pixel with a decision within the float32 uncertainty gets dL/dC = 0 on both
+    # sides -- on the GPU through a target equal to its rendered value there (sign(0) = 0), in
+    # the oracle by zeroing its L1 gradient there
+    tg2 = []
+    for v in range(len(cams)):
+        t = np.array(targets[v], dtype=np.float32, copy=True)
+        amb = refs[v]["margin"] < 1.0
+        t[:, amb] = np_(images[v])[:, amb]
+        tg2.append(torch.from_numpy(t).cuda())
+        dls[v] = zero_margin_pixels(dls[v], refs[v]["margin"])
+    grads = rast.alloc_grads(g)
+    stats = rast.alloc_stats(g.n)
+    rast.train_step_batched(g, cams, tg2, grads, stats, loss, fused=fused)
+    rast.poll()
     ref, rstats, _ = oracle.grad(scene, cams, st, dls)
     for k, t in grads.items():
-        e = rel_err(np_(t), ref[k])
-        assert e <= GRAD_RTOL, (k, e)
+        check_grad(np_(t), ref[k], k)
     assert np.sum(np_(stats["vis_count"]) != rstats["count"]) <= 2
 
 
@@ -369,6 +396,37 @@ def test_graph_replay_equals_direct_step(R):
     assert abs(loss_d.item() - loss_g.item()) <= 1e-6 * abs(loss_d.item())
     for k in direct:
         np.testing.assert_allclose(np_(graphed[k]), np_(direct[k]), rtol=1e-4, atol=1e-7)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_host_buffer_step_equals_device_step(R, graph):
+    """tgs_train_step_batched_host (parameters and targets in pinned host memory, copied by
+    the library on its upload stream into two alternating buffer sets) gives the loss and
+    gradients of the device-resident step, on consecutive calls with changing inputs."""
+    scene, cams, targets, st = batched_case(3000)
+    rast = make_rast(R, st)
+    g = gpu_scene(R, scene)
+    rast.plan(g, cams)
+    hostg = R.Gaussians(**{k: t.detach().cpu().pin_memory() for k, t in g.params().items()},
+                        sh_degree_max=g.sh_degree_max)
+    s = torch.cuda.Stream()
+    for call in range(4):
+        # a different target set each call: a copy landing in the wrong buffer set would show
+        tgt = [np.ascontiguousarray(np.roll(t, call, axis=2)) for t in targets]
+        host_t = [torch.from_numpy(t).pin_memory() for t in tgt]
+        dev_t = [torch.from_numpy(t).cuda() for t in tgt]
+        with torch.cuda.stream(s):
+            ref = rast.alloc_grads(g)
+            loss_d = torch.zeros(1, device="cuda")
+            rast.train_step_batched(g, cams, dev_t, ref, None, loss_d, graph=graph)
+            got = rast.alloc_grads(g)
+            loss_h = torch.zeros(1).pin_memory()
+            rast.train_step_batched_host(hostg, cams, host_t, got, None, loss_h, graph=graph)
+        s.synchronize()
+        rast.poll()
+        assert abs(loss_h.item() - loss_d.item()) <= 1e-6 * abs(loss_d.item()), call
+        for k in ref:
+            np.testing.assert_allclose(np_(got[k]), np_(ref[k]), rtol=1e-4, atol=1e-7, err_msg=f"{call} {k}")
 
 
 def test_key_capacity_overflow_is_reported_then_recovered(R):

@@ -166,3 +166,66 @@ def test_pruning_round_on_the_benchmark_scene(R):
     assert prune.sum() == math.floor(0.6 * g.n)
     np.testing.assert_array_equal(prune, oracle.prune_select(s, 0.6))
     assert s[prune].max() <= s[~prune].min()
+
+
+def _keys_oracle(rec, rad, cams, n, tile):
+    """The key oracle's sorted keys, ids and ranges of V views' float32 records (views
+    concatenated as the library numbers them)."""
+    from helpers import cull_data, splats_to_oracle
+    ek, ev, er, toff = [], [], [], 0
+    for v, cam in enumerate(cams):
+        r_v, d_v = rec[v * n:(v + 1) * n], rad[v * n:(v + 1) * n]
+        gs = splats_to_oracle(r_v, d_v)
+        k, vv, r = oracle.keys(gs["radius"], gs["rect"], r_v[:, 11], cam.width, cam.height, tile,
+                               tile_offset=toff, value_offset=v * n, cull=cull_data(r_v))
+        base = sum(len(x) for x in ek)
+        r = r.copy()
+        r[r[:, 1] > 0] += base
+        ek.append(k)
+        ev.append(vv)
+        er.append(r)
+        toff += r.shape[0]
+    return np.concatenate(ek), np.concatenate(ev), np.concatenate(er)
+
+
+def _bin_and_compare(R, rast, g, cams, st):
+    """Bins g's records in rast's context and in a fresh one; both must equal the key oracle."""
+    splats, radii = rast.preprocess(g, cams)
+    ids, keys, ranges, K = rast.bin(splats, radii, g.n, cams)
+    fresh = make_rast(R, st)
+    ids_f, keys_f, ranges_f, K_f = fresh.bin(splats, radii, g.n, cams)
+    assert K == K_f > 0
+    assert torch.equal(ids, ids_f) and torch.equal(keys, keys_f) and torch.equal(ranges, ranges_f)
+    ek, ev, er = _keys_oracle(np_(splats), np_(radii), cams, g.n, st.tile)
+    assert np.array_equal(np_(keys).view(np.uint64), ek)
+    assert np.array_equal(np_(ids).view(np.uint32), ev)
+    assert np.array_equal(np_(ranges).view(np.uint32), er)
+    return K
+
+
+def test_binning_after_significance_and_compaction_in_one_context(R):
+    """The per-record scratch of a context is reused: the volumes of tgs_significance and the
+    key counts of an earlier binning with more visible records must not leak into a later
+    binning. One context runs a pruning round (hits, score, selection), bins again, compacts
+    and bins the smaller scene; every binning equals a fresh context's and the key oracle."""
+    scene, cams, st = case(3000)
+    rast = make_rast(R, st)
+    g = R.Gaussians.from_numpy(scene)
+    K0 = _bin_and_compare(R, rast, g, cams, st)
+    hits = rast.count_hits(g, cams)
+    scores = rast.significance(g, hits, 0.9)
+    prune = rast.prune_select(scores, 0.6)
+    # the hit-counting binnings after tgs_significance reused the count scratch for volumes
+    hits2 = rast.count_hits(g, cams)
+    assert torch.equal(hits2, hits)
+    assert _bin_and_compare(R, rast, g, cams, st) == K0
+    kept, _ = rast.compact(g, prune, masked=True)
+    assert 0 < kept.n < g.n
+    K1 = _bin_and_compare(R, rast, kept, cams, st)
+    assert K1 < K0
+    # a second pruning round in the same context
+    scores = rast.significance(kept, rast.count_hits(kept, cams), 0.9)
+    kept2, _ = rast.compact(kept, rast.prune_select(scores, 0.6 * 0.7), masked=True)
+    assert 0 < kept2.n < kept.n
+    assert _bin_and_compare(R, rast, kept2, cams, st) < K1
+    rast.poll()

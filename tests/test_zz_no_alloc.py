@@ -44,6 +44,40 @@ def _noalloc(B, R, splats, radii, n, cams, tile, capacity):
     return st, int(K.value), ids, keys, ranges
 
 
+def _compare_with_bin(B, R, rast, g, cams, tile, tag):
+    splats, radii = rast.preprocess(g, cams)
+    ids_ref, keys_ref, ranges_ref, K = rast.bin(splats, radii, g.n, cams)
+    torch.cuda.synchronize()
+    assert 0 < K <= B.TGS_NOALLOC_MAX_KEYS and g.n * len(cams) <= B.TGS_NOALLOC_MAX_RECORDS
+    st, K2, ids, keys, ranges = _noalloc(B, R, splats, radii, g.n, cams, tile, K)
+    assert st == B.TGS_OK, B.lib.tgs_status_string(st)
+    assert K2 == K, (tag, K2, K)
+    assert torch.equal(ids[:K], ids_ref), tag
+    assert torch.equal(keys[:K], keys_ref), tag
+    assert torch.equal(ranges, ranges_ref), tag
+    return K
+
+
+@pytest.mark.parametrize("tile", [16, 8])
+def test_bin_noalloc_larger_then_smaller_scenes(tile):
+    """The array keeps what the previous call left in it: a call with more visible records
+    and keys, then calls with fewer (the same Gaussians mostly masked out, then fewer
+    Gaussians), must each equal tgs_bin bit for bit."""
+    B, R = _setup()
+    scene = synth.blob_scene(30000, 8, 23, log_scale=(-3.2, 0.5))
+    cams = synth.ring_cameras(2, [(160, 104), (96, 64)])
+    rast = R.Rasterizer(tile=tile, ppt=2 if tile == 8 else 1, eps_mask=0.5, eps_sh=0.5)
+    K_big = _compare_with_bin(B, R, rast, R.Gaussians.from_numpy(scene), cams, tile, "all")
+    fewer = dict(scene)
+    m = np.array(scene["mask_logits"], copy=True)
+    m[np.random.default_rng(4).random(m.shape[0]) < 0.7] = -5.0   # 70 % masked: not visible
+    fewer["mask_logits"] = m
+    K_fewer = _compare_with_bin(B, R, rast, R.Gaussians.from_numpy(fewer), cams, tile, "masked")
+    small = {k: (v[:7000] if isinstance(v, np.ndarray) else v) for k, v in scene.items()}
+    K_small = _compare_with_bin(B, R, rast, R.Gaussians.from_numpy(small), cams, tile, "fewer")
+    assert K_big > K_fewer and K_big > K_small
+
+
 @pytest.mark.parametrize("tile", [16, 8])
 def test_bin_noalloc_equals_bin_on_consecutive_calls(tile):
     B, R = _setup()
