@@ -102,6 +102,10 @@ typedef int32_t tgs_status;
 #define TGS_UNFUSED 8u          /* batched step: separate forward, loss and backward kernels (A/B) */
 #define TGS_LOSS_DSSIM 16u      /* batched step: loss (1 - lambda) L1 + lambda D-SSIM (Eq. loss3dgs),
                                    lambda = tgs_config.ssim_lambda; implies separate kernels */
+#define TGS_MASK_LOSS 32u       /* add the mask losses lambda_m L_m + lambda_sh L_sh of Eq. loss3dgs
+                                   (see tgs_mask_loss) to the gradients of the mask logits, folded
+                                   into the preprocess backward (once per call, not per view), and,
+                                   in the batched step, to the loss */
 
 typedef struct tgs_ctx tgs_ctx;
 typedef void *tgs_stream; /* a cudaStream_t; NULL is the legacy default stream */
@@ -118,6 +122,8 @@ typedef struct {
     int64_t key_capacity;  /* (Gaussian, tile) keys the batched path may hold; 0 = sized by tgs_plan */
     int64_t spin_limit;    /* reserved (no kernel waits on another); ignored, default 0 */
     float ssim_lambda;     /* lambda_SSIM of Eq. loss3dgs for TGS_LOSS_DSSIM, in [0, 1] (default 0.2) */
+    float lambda_mask;     /* lambda_m of Eq. loss3dgs for TGS_MASK_LOSS, >= 0 (default 0.05) */
+    float lambda_sh_mask;  /* lambda_sh of Eq. loss3dgs for TGS_MASK_LOSS, >= 0 (default 0.05) */
     int32_t reserved0;
 } tgs_config;
 
@@ -221,6 +227,19 @@ tgs_status tgs_l1_loss(const float *image, const float *target, int64_t count, f
 tgs_status tgs_l1_dssim_loss(tgs_ctx *ctx, const tgs_camera *cams, int32_t V, const float *const *images,
                              const float *const *targets, float lambda, float *loss_accum,
                              float *const *grads, tgs_stream stream);
+
+/* Mask losses of Eq. loss3dgs: adds lambda_m L_m + lambda_sh L_sh (tgs_config.lambda_mask,
+   lambda_sh_mask) to *loss_accum (device float, or NULL) and their gradients to
+   grads->mask_logits and grads->sh_mask_logits (device, always added to; NULL fields and absent
+   logit arrays are skipped). The paper fixes the weights (0.05 each) and that each SH band's
+   masking loss is weighted by its number of coefficients (Sec. "Spherical Harmonic (SH)
+   Masking"), and leaves the definitions to the cited works; this library takes
+     L_m  = (1/N) sum_n sigmoid(m_n),
+     L_sh = (1/N) sum_n sum_{l=1..3} (2l + 1) / 15 * sigmoid(m_n^l),
+   over every Gaussian and band, visible or not. The batched step, tgs_backward and
+   tgs_preprocess_backward do the same when given TGS_MASK_LOSS. Asynchronous. */
+tgs_status tgs_mask_loss(tgs_ctx *ctx, const tgs_gaussians *g, float *loss_accum, const tgs_grads *grads,
+                         tgs_stream stream);
 
 /* --- the batched path ---------------------------------------------------------------- */
 

@@ -29,6 +29,7 @@ TGS_NO_SH_REST_GRAD = 2
 TGS_USE_GRAPH = 4
 TGS_UNFUSED = 8
 TGS_LOSS_DSSIM = 16
+TGS_MASK_LOSS = 32
 TGS_COMPACT_MASKED = 1
 TGS_PARAM_F32 = 0
 TGS_PARAM_F16 = 1
@@ -41,7 +42,8 @@ class tgs_config(C.Structure):
     _fields_ = [("tile", C.c_int32), ("ppt", C.c_int32), ("support", C.c_int32),
                 ("low_pass", C.c_float), ("eps_mask", C.c_float), ("eps_sh", C.c_float),
                 ("near_plane", C.c_float), ("bg", C.c_float * 3), ("key_capacity", C.c_int64),
-                ("spin_limit", C.c_int64), ("ssim_lambda", C.c_float), ("reserved0", C.c_int32)]
+                ("spin_limit", C.c_int64), ("ssim_lambda", C.c_float), ("lambda_mask", C.c_float),
+                ("lambda_sh_mask", C.c_float), ("reserved0", C.c_int32)]
 
 
 class tgs_gaussians(C.Structure):
@@ -106,6 +108,7 @@ SIGNATURES = {
     "tgs_l1_dssim_loss": (C.c_int32, [_ctx_p, _camp, C.c_int32, _pp, _pp, C.c_float, _vp, _pp, _vp]),
     "tgs_params_to_half": (C.c_int32, [_gp, C.POINTER(tgs_half_params), _vp]),
     "tgs_compact": (C.c_int32, [_ctx_p, _gp, _vp, C.c_uint32, _gradp, _vp, _vp, C.POINTER(C.c_int64), _vp]),
+    "tgs_mask_loss": (C.c_int32, [_ctx_p, _gp, _vp, _gradp, _vp]),
     "tgs_plan": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, C.c_double, C.POINTER(C.c_int64)]),
     "tgs_train_step_batched": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _pp, _pp, _gradp,
                                            _statp, _vp, C.c_uint32, _vp]),

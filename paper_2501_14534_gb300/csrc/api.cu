@@ -126,7 +126,8 @@ T *as(Buf &b) { return reinterpret_cast<T *>(b.p); }
 bool valid_cfg(const tgs_config &c) {
     return blend_supported(c.tile, c.ppt) && (c.support == TGS_SUPPORT_BOX3 || c.support == TGS_SUPPORT_ALPHA) &&
            c.low_pass >= 0.f && c.eps_mask > 0.f && c.eps_mask < 1.f && c.eps_sh > 0.f && c.eps_sh < 1.f &&
-           c.near_plane > 0.f && c.key_capacity >= 0 && c.ssim_lambda >= 0.f && c.ssim_lambda <= 1.f;
+           c.near_plane > 0.f && c.key_capacity >= 0 && c.ssim_lambda >= 0.f && c.ssim_lambda <= 1.f &&
+           c.lambda_mask >= 0.f && c.lambda_mask < 1e30f && c.lambda_sh_mask >= 0.f && c.lambda_sh_mask < 1e30f;
 }
 
 tgs_status make_batch(const tgs_config &cfg, const tgs_camera *cams, int V, CamBatch &cb) {
@@ -336,6 +337,13 @@ GradPtrs grad_ptrs(const tgs_grads *g, const tgs_stats *s, int acc) {
     return o;
 }
 
+// The mask losses of Eq. loss3dgs folded into the preprocess backward (TGS_MASK_LOSS).
+void with_mask_loss(const tgs_config &cfg, int64_t n, GradPtrs &o) {
+    if (n <= 0) return;
+    o.lam_m_n = (float)((double)cfg.lambda_mask / (double)n);
+    o.lam_sh_n = (float)((double)cfg.lambda_sh_mask / (double)n);
+}
+
 bool same_cam(const tgs_camera &a, const tgs_camera &b) { return memcmp(&a, &b, sizeof a) == 0; }
 bool same_g(const tgs_gaussians &a, const tgs_gaussians &b) { return memcmp(&a, &b, sizeof a) == 0; }
 
@@ -370,6 +378,8 @@ void tgs_default_config(tgs_config *cfg) {
     cfg->key_capacity = 0;
     cfg->spin_limit = 0;  // reserved
     cfg->ssim_lambda = 0.2f;
+    cfg->lambda_mask = 0.05f;
+    cfg->lambda_sh_mask = 0.05f;
 }
 
 const char *tgs_status_string(tgs_status s) {
@@ -573,6 +583,7 @@ tgs_status tgs_preprocess_backward(tgs_ctx *c, const tgs_gaussians *g, const tgs
     TGS_TRY(make_batch(c->cfg, cams, V, cb));
     TGS_TRY(make_gauss(c->cfg, g, gp));
     GradPtrs o = grad_ptrs(grads, stats, (flags & TGS_ACCUMULATE) ? 1 : 0);
+    if (flags & TGS_MASK_LOSS) with_mask_loss(c->cfg, g->n, o);
     launch_preprocess_backward(gp, cb, reinterpret_cast<const float4 *>(splat_grads), radii, o,
                                (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, 0, (cudaStream_t)stream);
     return last_error();
@@ -601,6 +612,15 @@ tgs_status tgs_l1_dssim_loss(tgs_ctx *c, const tgs_camera *cams, int32_t V, cons
     cudaStream_t st = (cudaStream_t)stream;
     TGS_TRY(ensure(c->ssim, sizeof(float) * (size_t)ssim_scratch_floats(W, H, V), st));
     launch_l1_dssim(V, W, H, images, targets, grads, lambda, as<float>(c->ssim), loss_accum, st);
+    return last_error();
+}
+
+tgs_status tgs_mask_loss(tgs_ctx *c, const tgs_gaussians *g, float *loss_accum, const tgs_grads *grads,
+                         tgs_stream stream) {
+    if (!c || !g || g->n < 0 || g->param_dtype != TGS_PARAM_F32) return TGS_ERR_INVALID_ARG;
+    launch_mask_loss(g->mask_logits, g->sh_mask_logits, g->n, c->cfg.lambda_mask, c->cfg.lambda_sh_mask, loss_accum,
+                     (grads && g->mask_logits) ? grads->mask_logits : nullptr,
+                     (grads && g->sh_mask_logits) ? grads->sh_mask_logits : nullptr, (cudaStream_t)stream);
     return last_error();
 }
 
@@ -669,6 +689,7 @@ tgs_status tgs_backward(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *ca
                               cb, px, c->cfg.bg, as<float>(c->sgrads), st);
         const int acc = ((flags & TGS_ACCUMULATE) || v > 0) ? 1 : 0;
         GradPtrs o = grad_ptrs(grads, stats, acc);
+        if ((flags & TGS_MASK_LOSS) && v == 0) with_mask_loss(c->cfg, g->n, o);  // once, not per view
         launch_preprocess_backward(gp, cb, as<float4>(c->sgrads), as<int32_t>(c->radii), o,
                                    (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, 0, st);
         TGS_TRY(last_error());
@@ -898,9 +919,13 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
     }
     mark(c, stage++, "preprocess_backward", st);
     GradPtrs o = grad_ptrs(grads, stats, (flags & TGS_ACCUMULATE) ? 1 : 0);
+    if (flags & TGS_MASK_LOSS) with_mask_loss(c->cfg, n, o);
     // the fused blend leaves pixel sums (moments) in the gradient records
     launch_preprocess_backward(gp, cb, as<float4>(c->sgrads), as<int32_t>(c->radii), o,
                                (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, split ? 0 : 1, st);
+    if ((flags & TGS_MASK_LOSS) && loss_out)  // the value of the mask terms (Eq. loss3dgs)
+        launch_mask_loss(g->mask_logits, g->sh_mask_logits, n, c->cfg.lambda_mask, c->cfg.lambda_sh_mask, loss_out,
+                         nullptr, nullptr, st);
     mark(c, stage, "end", st);
     c->kernels_per_step = g_launches - launches0;
     return last_error();

@@ -595,6 +595,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_colour(GaussPtrs
             const float sm = sigmoidf_(g.shmask[3 * i + l - 1]);
             g_shm[l - 1] = g_band[l] * sm * (1.f - sm);
         }
+    if (out.lam_sh_n != 0.f && g.shmask)  // lambda_sh L_sh of Eq. loss3dgs, every Gaussian and band
+#pragma unroll
+        for (int l = 1; l <= 3; l++) {
+            const float sm = sigmoidf_(g.shmask[3 * i + l - 1]);
+            g_shm[l - 1] += out.lam_sh_n * ((float)(2 * l + 1) / 15.f) * sm * (1.f - sm);
+        }
     if (out.sh_rest && !no_sh_rest) {
         __syncwarp();  // every thread has read its own row
 #pragma unroll
@@ -679,6 +685,10 @@ __global__ void __launch_bounds__(kBwdThreads, 5) k_preprocess_bwd_geom(GaussPtr
     float g_shm[3] = {0.f, 0.f, 0.f};
     const float no_band[4] = {0.f, 0.f, 0.f, 0.f};  // the colour kernel did the band masks
     if (any) gauss_backward(g, i, s, g_S, g_op, no_band, g_q, g_ls, g_o, g_m, g_shm);
+    if (out.lam_m_n != 0.f && g.mask) {  // lambda_m L_m of Eq. loss3dgs, every Gaussian
+        const float sm = sigmoidf_(g.mask[i]);
+        g_m += out.lam_m_n * sm * (1.f - sm);
+    }
 #pragma unroll
     for (int k = 0; k < 3; k++) {
         if (out.means) out.means[3 * i + k] += (k == 0 ? g_mu.x : (k == 1 ? g_mu.y : g_mu.z));
@@ -690,7 +700,51 @@ __global__ void __launch_bounds__(kBwdThreads, 5) k_preprocess_bwd_geom(GaussPtr
     out_write(out.mask, i, g_m, acc);
 }
 
+// lambda_m L_m + lambda_sh L_sh over the Gaussians (Eq. loss3dgs): per block one partial sum,
+// added to *loss; the gradients of the soft masks added to gmask / gshmask when given.
+__global__ void __launch_bounds__(256) k_mask_loss(const float *__restrict__ mask, const float *__restrict__ shmask,
+                                                   int64_t n, float lam_m, float lam_sh, float inv_n,
+                                                   float *__restrict__ loss, float *__restrict__ gmask,
+                                                   float *__restrict__ gshmask) {
+    float acc = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (mask) {
+            const float sm = sigmoidf_(mask[i]);
+            acc += lam_m * sm;
+            if (gmask) gmask[i] += lam_m * inv_n * sm * (1.f - sm);
+        }
+        if (shmask)
+#pragma unroll
+            for (int l = 1; l <= 3; l++) {
+                const float w = (float)(2 * l + 1) / 15.f;
+                const float sm = sigmoidf_(shmask[3 * i + l - 1]);
+                acc += lam_sh * w * sm;
+                if (gshmask) gshmask[3 * i + l - 1] += lam_sh * w * inv_n * sm * (1.f - sm);
+            }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ float s[8];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0 && loss) {
+        float x = 0.f;
+        for (int q = 0; q < (int)(blockDim.x >> 5); q++) x += s[q];
+        atomicAdd(loss, x * inv_n);
+    }
+}
+
 }  // namespace
+
+void launch_mask_loss(const float *mask, const float *shmask, int64_t n, float lam_m, float lam_sh, float *loss,
+                      float *gmask, float *gshmask, cudaStream_t st) {
+    if (n <= 0 || (!mask && !shmask) || (!loss && !gmask && !gshmask)) return;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    count_launch();
+    k_mask_loss<<<(unsigned)blocks, 256, 0, st>>>(mask, shmask, n, lam_m, lam_sh, (float)(1.0 / (double)n), loss,
+                                                   gmask, gshmask);
+}
 
 void launch_preprocess(const GaussPtrs &g, const CamBatch &cb, float4 *splats, int32_t *radii,
                        uint32_t *tiles_touched, uint32_t *depth_bits, float *zero_grads,

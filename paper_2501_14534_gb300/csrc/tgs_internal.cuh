@@ -55,6 +55,9 @@ struct GradPtrs {
     float *stat_accum;
     int32_t *stat_count, *stat_maxr;
     int accumulate;
+    // mask losses of Eq. loss3dgs folded into the mask-logit gradients (0: none): lambda_m / N
+    // and lambda_sh / N
+    float lam_m_n, lam_sh_n;
 };
 
 struct PixPtrs {
@@ -138,6 +141,10 @@ __device__ __forceinline__ bool tile_keep(float mx, float my, float a, float b, 
 
 // ---- launchers implemented in the .cu files --------------------------------------------
 
+// preprocess.cu: lambda_m L_m + lambda_sh L_sh (Eq. loss3dgs) over n Gaussians added to *loss
+// (if not null) and their gradients added to gmask / gshmask (if not null)
+void launch_mask_loss(const float *mask, const float *shmask, int64_t n, float lam_m, float lam_sh, float *loss,
+                      float *gmask, float *gshmask, cudaStream_t st);
 // preprocess.cu. depth_bits [n*V]: the depth key of every record (kNoDepth where not
 // visible); tiles_touched (may be null): visibility flags.
 void launch_preprocess(const GaussPtrs &g, const CamBatch &cb, float4 *splats, int32_t *radii,

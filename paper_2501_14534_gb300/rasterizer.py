@@ -125,10 +125,12 @@ class Rasterizer:
     """One libtgs context (its settings and its scratch arena) on the current device."""
 
     def __init__(self, tile=16, ppt=1, support=B.TGS_SUPPORT_BOX3, low_pass=0.3, eps_mask=0.05,
-                 eps_sh=0.1, near=0.2, bg=(0.0, 0.0, 0.0), key_capacity=0, ssim_lambda=0.2):
+                 eps_sh=0.1, near=0.2, bg=(0.0, 0.0, 0.0), key_capacity=0, ssim_lambda=0.2,
+                 lambda_mask=0.05, lambda_sh_mask=0.05):
         cfg = B.tgs_config()
         B.lib.tgs_default_config(C.byref(cfg))
         cfg.ssim_lambda = ssim_lambda
+        cfg.lambda_mask, cfg.lambda_sh_mask = lambda_mask, lambda_sh_mask
         cfg.tile, cfg.ppt, cfg.support = tile, ppt, support
         cfg.low_pass, cfg.eps_mask, cfg.eps_sh, cfg.near_plane = low_pass, eps_mask, eps_sh, near
         for i in range(3):
@@ -233,12 +235,13 @@ class Rasterizer:
                            _p(stats.get("max_radius")), _p(stats.get("hit_count")))
 
     def backward(self, g: Gaussians, cams, outs, dL_dimages, grads=None, stats=None,
-                 accumulate=False, no_sh_rest=False):
+                 accumulate=False, no_sh_rest=False, mask_loss=False):
         if grads is None:
             grads = self.alloc_grads(g, no_sh_rest)
         if stats is None:
             stats = self.alloc_stats(g.n)
-        flags = (B.TGS_ACCUMULATE if accumulate else 0) | (B.TGS_NO_SH_REST_GRAD if no_sh_rest else 0)
+        flags = ((B.TGS_ACCUMULATE if accumulate else 0) | (B.TGS_NO_SH_REST_GRAD if no_sh_rest else 0) |
+                 (B.TGS_MASK_LOSS if mask_loss else 0))
         dl = [d.contiguous() for d in dL_dimages]
         B.check(B.lib.tgs_backward(self._h, C.byref(g.struct()), cameras_array(cams), len(cams),
                                    self._out_structs(outs), _ptr_array(dl),
@@ -270,6 +273,17 @@ class Rasterizer:
                                         float(lam), _p(loss), _ptr_array(grads), _stream()),
                 "tgs_l1_dssim_loss")
         return loss, grads
+
+    def mask_loss(self, g: Gaussians, loss=None, grads=None):
+        """Adds lambda_m L_m + lambda_sh L_sh of Eq. loss3dgs to loss (device float [1], zeros if
+        None) and their gradients to grads["mask_logits"] / grads["sh_mask_logits"] when given;
+        returns loss (tgs_mask_loss)."""
+        if loss is None:
+            loss = torch.zeros(1, device="cuda", dtype=torch.float32)
+        B.check(B.lib.tgs_mask_loss(self._h, C.byref(g.struct()), _p(loss),
+                                    C.byref(self._grad_struct(grads)) if grads else None, _stream()),
+                "tgs_mask_loss")
+        return loss
 
     # ---- individual steps -----------------------------------------------------------------
 
@@ -345,10 +359,10 @@ class Rasterizer:
 
     def train_step_batched(self, g: Gaussians, cams, targets, grads, stats=None, loss=None,
                            images=None, graph=False, accumulate=False, no_sh_rest=False,
-                           cams_struct=None, fused=True, dssim=False):
+                           cams_struct=None, fused=True, dssim=False, mask_loss=False):
         flags = ((B.TGS_USE_GRAPH if graph else 0) | (B.TGS_ACCUMULATE if accumulate else 0) |
                  (B.TGS_NO_SH_REST_GRAD if no_sh_rest else 0) | (0 if fused else B.TGS_UNFUSED) |
-                 (B.TGS_LOSS_DSSIM if dssim else 0))
+                 (B.TGS_LOSS_DSSIM if dssim else 0) | (B.TGS_MASK_LOSS if mask_loss else 0))
         camarr = cams_struct if cams_struct is not None else cameras_array(cams)
         B.check(B.lib.tgs_train_step_batched(
             self._h, C.byref(g.struct()), camarr, len(camarr), _ptr_array(targets),

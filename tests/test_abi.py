@@ -114,3 +114,6 @@ def test_defaults_are_the_papers_constants(lib):
     assert len(fr) == pc["prune_rounds"] and fr[0] == pc["first_prune_fraction"]
     assert all(abs(b / a - pc["prune_decay"]) < 1e-12 for a, b in zip(fr, fr[1:]))
     assert oracle.SSIM_WINDOW == pc["ssim_window"]
+    for name, lib_v, orc_v in [("lambda_mask", cfg.lambda_mask, oracle.MASK_LAMBDA),
+                               ("lambda_sh_mask", cfg.lambda_sh_mask, oracle.SH_MASK_LAMBDA)]:
+        assert abs(lib_v - pc[name]) < 1e-7 and orc_v == pc[name] and ctor[name].default == pc[name], name

@@ -28,7 +28,7 @@ def R():
 
 # Largest fraction of pixels an end-to-end image comparison (float32 preprocess on the GPU,
 # float64 in the oracle) may exclude as decision-margin cases.
-EXCL_E2E = 0.05
+EXCL_E2E = 0.04
 
 
 def settings_for(tile=16, eps=(0.05, 0.1), support=0, bg=(0.0, 0.0, 0.0)):
@@ -427,6 +427,56 @@ def test_host_buffer_step_equals_device_step(R, graph):
         assert abs(loss_h.item() - loss_d.item()) <= 1e-6 * abs(loss_d.item()), call
         for k in ref:
             np.testing.assert_allclose(np_(got[k]), np_(ref[k]), rtol=1e-4, atol=1e-7, err_msg=f"{call} {k}")
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_batched_step_with_mask_losses_matches_oracle(R, fused):
+    """TGS_MASK_LOSS: the step's loss gains lambda_m L_m + lambda_sh L_sh and the mask-logit
+    gradients their derivatives (Eq. loss3dgs, reading in the oracle); every other gradient
+    is the one without the flag."""
+    scene, cams, targets, st = batched_case(3000)
+    rast = make_rast(R, st)
+    g = gpu_scene(R, scene)
+    tg = [torch.from_numpy(t).cuda() for t in targets]
+    rast.plan(g, cams)
+    base, with_m = rast.alloc_grads(g), rast.alloc_grads(g)
+    l0, l1 = torch.zeros(1, device="cuda"), torch.zeros(1, device="cuda")
+    rast.train_step_batched(g, cams, tg, base, None, l0, fused=fused)
+    rast.train_step_batched(g, cams, tg, with_m, None, l1, fused=fused, mask_loss=True)
+    rast.poll()
+    ref_loss, ref = oracle.mask_loss(scene, 0.05, 0.05)
+    assert abs((l1.item() - l0.item()) - ref_loss) <= 1e-5 * ref_loss + 1e-6 * l0.item()
+    for k in base:
+        if k in ("mask_logits", "sh_mask_logits"):
+            # the difference of two runs also holds float-atomic noise of the render part
+            check_grad(np_(with_m[k]) - np_(base[k]), ref[k], k, rel=1e-4, elem=1e-3)
+        else:
+            assert rel_err(np_(with_m[k]), np_(base[k])) <= 1e-5, k
+
+
+def test_mask_loss_call_and_backward_flag(R):
+    """tgs_mask_loss alone, and TGS_MASK_LOSS on the plain backward (added once, not per view)."""
+    scene, cams, st = masked_case()
+    rast = make_rast(R, st)
+    rast.set(lambda_mask=0.3, lambda_sh_mask=0.7)
+    g = gpu_scene(R, scene)
+    grads = {k: torch.zeros_like(v) for k, v in g.params().items()}
+    loss = rast.mask_loss(g, grads=grads)
+    torch.cuda.synchronize()
+    ref_loss, ref = oracle.mask_loss(scene, 0.3, 0.7)
+    assert abs(loss.item() - ref_loss) <= 1e-5 * ref_loss
+    check_grad(np_(grads["mask_logits"]), ref["mask_logits"], "mask_logits", rel=1e-5, elem=1e-4)
+    check_grad(np_(grads["sh_mask_logits"]), ref["sh_mask_logits"], "sh_mask_logits", rel=1e-5, elem=1e-4)
+    assert torch.all(grads["means"] == 0)
+    outs = rast.forward(g, cams)
+    # with dL/dimage = 0 the render part is exactly 0: the flag's gradients alone, once
+    zero = [torch.zeros((3, c.height, c.width), device="cuda") for c in cams]
+    b, _ = rast.backward(g, cams, outs, zero, mask_loss=True)
+    for k in ("mask_logits", "sh_mask_logits"):
+        check_grad(np_(b[k]), ref[k], k, rel=1e-5, elem=1e-4)
+    for k in b:
+        if k not in ("mask_logits", "sh_mask_logits"):
+            assert torch.all(b[k] == 0), k
 
 
 def test_key_capacity_overflow_is_reported_then_recovered(R):
