@@ -426,6 +426,79 @@ def mask_loss(scene, lam_m=MASK_LAMBDA, lam_sh=SH_MASK_LAMBDA):
     return loss, grads
 
 
+# ---- densification by clone and split (3DGS, which the paper keeps) ----------------------------
+#
+# The paper densifies as 3DGS does (Sec. "Implementation details": standard densification every
+# 100 iterations until 15K, and again from 20K to 20.5K) from the 2D-mean gradient magnitudes
+# (Sec. "Preliminaries"); it states no rule of its own. Reading used here, 3DGS's clone and split
+# driven by the statistics the preprocess backward accumulates (the per-view norms of dL/d mean2d
+# in pixel units summed over the views where the Gaussian is visible, and the visibility count):
+#   avg_n   = accum_n / count_n  (float32 division; 0 where count_n = 0)
+#   chosen  = avg_n >= tau_g     (float32)
+#   large   = max_k l_nk > float32(log(scale_threshold))   (log-scales, float32; the threshold is
+#             3DGS's percent_dense x scene extent, compared in the log domain so that no exp
+#             rounding can flip the decision)
+#   clone   = chosen and not large: an identical copy is added;
+#   split   = chosen and large: the Gaussian is replaced by 2 children with means
+#             mu + R(q / |q|) (exp(l) * z_c) for caller-drawn standard normals z_c = normals[n, c]
+#             and log-scales l - log(1.6) (3DGS divides the scales by 0.8 N, N = 2); every other
+#             parameter (mask logits included) is copied.
+# New order: the Gaussians not split, in order; then the clones, in order; then the first children
+# of the split Gaussians, in order; then their second children (3DGS appends the clones, then the
+# children as N stacked copies of the selection, then drops the split originals).
+
+SPLIT_CHILDREN = 2
+SPLIT_SCALE_DIVISOR = 0.8 * SPLIT_CHILDREN
+
+
+def densify(scene, accum, count, grad_threshold, scale_threshold, normals):
+    """Clone and split (reading above). normals: float [n, 2, 3] standard normals (only the rows
+    of split Gaussians are read). Returns (scene, src, n_clone, n_split) with src[new] = the old
+    index each new row comes from."""
+    n = np.shape(scene["means"])[0]
+    acc = np.asarray(accum, np.float32)
+    cnt = np.asarray(count, np.int64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        avg = np.where(cnt > 0, acc / cnt.astype(np.float32), np.float32(0.0)).astype(np.float32)
+    chosen = (cnt > 0) & (avg >= np.float32(grad_threshold))
+    ls = np.asarray(scene["log_scales"], np.float32)
+    large = ls.max(axis=1) > np.float32(np.log(np.float64(scale_threshold)))
+    clone = chosen & ~large
+    split = chosen & large
+    keep_idx = np.flatnonzero(~split)
+    clone_idx = np.flatnonzero(clone)
+    split_idx = np.flatnonzero(split)
+    src = np.concatenate([keep_idx, clone_idx, split_idx, split_idx]).astype(np.int64)
+    out = dict(scene)
+    for k in SCENE_KEYS:
+        if scene.get(k) is not None:
+            out[k] = np.asarray(scene[k])[src].copy()
+    # the children's means and log-scales
+    z = np.asarray(normals, np.float64).reshape(n, SPLIT_CHILDREN, 3)
+    q = np.asarray(scene["quats"], np.float64)[split_idx]
+    q = q / np.linalg.norm(q, axis=1, keepdims=True)
+    R = np.stack([_rotation(qq) for qq in q]) if split_idx.size else np.zeros((0, 3, 3))
+    s = np.exp(np.asarray(scene["log_scales"], np.float64)[split_idx])
+    mu = np.asarray(scene["means"], np.float64)[split_idx]
+    base = keep_idx.size + clone_idx.size
+    means = np.asarray(out["means"], np.float64)
+    log_scales = np.asarray(out["log_scales"], np.float64)
+    for c in range(SPLIT_CHILDREN):
+        rows = slice(base + c * split_idx.size, base + (c + 1) * split_idx.size)
+        means[rows] = mu + np.einsum("nij,nj->ni", R, s * z[split_idx, c])
+        log_scales[rows] = np.log(s / SPLIT_SCALE_DIVISOR)
+    out["means"], out["log_scales"] = means, log_scales
+    return out, src, int(clone_idx.size), int(split_idx.size)
+
+
+def _rotation(q):
+    """Rotation matrix of a unit quaternion (w, x, y, z)."""
+    w, x, y, z = q
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
 # ---- FP16 storage (Sec. "Experiments", setup: parameters kept as 16-bit halves after training) --
 
 def to_half(scene):

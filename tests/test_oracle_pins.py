@@ -891,3 +891,98 @@ def test_mask_losses_gradient_fd():
             a[idx] = old
             fd = (lp - lm) / (2 * h)
             assert abs(fd - g[key][idx]) <= 1e-9 * max(1.0, abs(fd)), (key, idx, fd, g[key][idx])
+
+
+# ---- densification (clone and split) --------------------------------------------------------
+
+def _densify_3dgs_procedure(scene, accum, count, tau_g, scale_thr, normals):
+    """The same reading as 3DGS carries it out, step by step with Python lists: clone appends
+    copies (their gradient statistics padded with zeros), split then selects on the extended
+    set, appends the children as two stacked blocks of the selection and drops the originals."""
+    keys = [k for k in oracle.SCENE_KEYS if scene.get(k) is not None]
+    rows = [{k: np.array(scene[k][i], copy=True) for k in keys} for i in range(len(scene["means"]))]
+    src = list(range(len(rows)))
+    avg = []
+    for a, c in zip(accum, count):
+        avg.append(np.float32(a) / np.float32(c) if c > 0 else np.float32(0.0))
+    thr = np.float32(math.log(scale_thr))
+    big = lambda r: np.float32(np.max(r["log_scales"])) > thr
+    n0 = len(rows)
+    for i in range(n0):                                   # clone
+        if avg[i] >= np.float32(tau_g) and not big(rows[i]):
+            rows.append({k: v.copy() for k, v in rows[i].items()})
+            src.append(i)
+            avg.append(np.float32(0.0))
+    sel = [i for i in range(len(rows)) if avg[i] >= np.float32(tau_g) and big(rows[i])]
+    for c in range(2):                                    # split: stacked blocks of children
+        for i in sel:
+            r = {k: v.copy() for k, v in rows[i].items()}
+            q = [float(v) for v in rows[i]["quats"]]
+            nq = math.sqrt(sum(v * v for v in q))
+            w, x, y, z = (v / nq for v in q)
+            Rm = [[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                  [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                  [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]]
+            s = [math.exp(float(v)) for v in rows[i]["log_scales"]]
+            zz = [float(v) for v in normals[i, c]]
+            r["means"] = np.array([float(rows[i]["means"][a]) + sum(Rm[a][b] * s[b] * zz[b] for b in range(3))
+                                   for a in range(3)])
+            r["log_scales"] = np.array([math.log(v / 1.6) for v in s])
+            rows.append(r)
+            src.append(src[i])
+    keep = [j for j in range(len(rows)) if j not in set(sel)]
+    out = {k: np.stack([rows[j][k] for j in keep]) for k in keys}
+    return out, [src[j] for j in keep]
+
+
+def test_densify_equals_the_3dgs_procedure():
+    scene = synth.blob_scene(400, 4, 31, log_scale=(-3.0, 0.7), masks=True)
+    rng = np.random.default_rng(8)
+    count = rng.integers(0, 5, size=400).astype(np.int32)
+    accum = (rng.exponential(0.5, size=400) * count).astype(np.float32)
+    normals = rng.normal(size=(400, 2, 3))
+    tau_g, thr = 0.4, math.exp(-3.0)
+    out, src, n_clone, n_split = oracle.densify(scene, accum, count, tau_g, thr, normals)
+    ref, ref_src = _densify_3dgs_procedure(scene, accum, count, tau_g, thr, normals)
+    assert n_clone > 10 and n_split > 10
+    assert list(src) == ref_src and len(src) == 400 + n_clone + n_split
+    for k, v in ref.items():
+        np.testing.assert_allclose(np.asarray(out[k], np.float64), v, rtol=1e-12, atol=1e-12, err_msg=k)
+
+
+def test_densify_children_recover_their_normals():
+    """R^T (child - parent) / scale is the caller's normal draw; log-scales drop by log 1.6; an
+    axis-aligned Gaussian's children sit at mu + s * z."""
+    scene = synth.blob_scene(60, 2, 32, log_scale=(-1.0, 0.3), masks=False)
+    scene["quats"][0] = [1.0, 0.0, 0.0, 0.0]
+    n = 60
+    rng = np.random.default_rng(9)
+    normals = rng.normal(size=(n, 2, 3))
+    accum, count = np.ones(n, np.float32), np.ones(n, np.int32)
+    out, src, n_clone, n_split = oracle.densify(scene, accum, count, 0.5, 1e-6, normals)
+    assert n_clone == 0 and n_split == n and len(src) == 2 * n
+    for c in range(2):
+        for j in range(n):
+            row = c * n + j
+            q = np.asarray(scene["quats"][j], np.float64)
+            Rm = oracle._rotation(q / np.linalg.norm(q))
+            s = np.exp(np.asarray(scene["log_scales"][j], np.float64))
+            d = out["means"][row] - np.asarray(scene["means"][j], np.float64)
+            np.testing.assert_allclose(Rm.T @ d / s, normals[j, c], rtol=1e-9, atol=1e-12)
+            np.testing.assert_allclose(out["log_scales"][row], np.log(s) - math.log(1.6), rtol=0, atol=1e-12)
+    s0 = np.exp(np.asarray(scene["log_scales"][0], np.float64))
+    np.testing.assert_allclose(out["means"][0], np.asarray(scene["means"][0], np.float64) + s0 * normals[0, 0],
+                               rtol=1e-12, atol=1e-12)
+
+
+def test_densify_decision_edges():
+    """Zero visibility is never chosen; the gradient test is >= and the scale test strict >."""
+    scene = synth.uniform_scene(4, 33)
+    t = np.float32(0.25)
+    scene["log_scales"][:] = np.float32(-2.0)
+    accum = np.array([t, t * 2, 0.0, 5.0], np.float32)
+    count = np.array([1, 2, 0, 0], np.int32)
+    thr = float(np.exp(np.float64(np.float32(-2.0))))     # log(thr) rounds to the log-scale itself
+    assert np.float32(np.log(np.float64(thr))) == np.float32(-2.0)
+    out, src, n_clone, n_split = oracle.densify(scene, accum, count, float(t), thr, np.zeros((4, 2, 3)))
+    assert (n_clone, n_split) == (2, 0) and list(src) == [0, 1, 2, 3, 0, 1]
