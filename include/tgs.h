@@ -348,7 +348,9 @@ tgs_status tgs_bin_noalloc(const float *splats, const int32_t *radii, int64_t n,
 /* Ray hits of the significance score: renders the V views (forward only, nothing else
    written) and adds to hit_count [n] (device, uint32) the number of pixels of each view
    whose blend (Eq. 2) blends the Gaussian -- alpha >= 1/255 and before the pixel's stop.
-   Same decisions as tgs_forward. Errors: TGS_ERR_INVALID_ARG for a null pointer or V <= 0. */
+   Same decisions as tgs_forward. All V views are preprocessed, binned and blended together
+   (scratch for n * V records and all their keys); synchronises the stream once to read the key
+   count. Errors: TGS_ERR_INVALID_ARG for a null pointer or V <= 0. */
 tgs_status tgs_count_hits(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
                           uint32_t *hit_count, tgs_stream stream);
 /* Significance score of each Gaussian, scores [n] (device float):
@@ -407,6 +409,35 @@ tgs_status tgs_params_to_half(const tgs_gaussians *g, const tgs_half_params *out
 tgs_status tgs_compact(tgs_ctx *ctx, const tgs_gaussians *g, const uint8_t *remove, uint32_t flags,
                        const tgs_grads *out, uint8_t *sh_degree_out, uint32_t *kept_index,
                        int64_t *n_kept, tgs_stream stream);
+
+/* --- densification --------------------------------------------------------------------- */
+
+/* Densification by clone and split, driven by the statistics the preprocess backward
+   accumulates (Sec. "Preliminaries": Gaussians are densified by their gradient magnitudes; Sec.
+   "Implementation details": the paper densifies as 3DGS does, every 100 iterations until 15K
+   and again from 20K to 20.5K). The paper states no rule of its own; this library takes 3DGS's:
+     avg = grad_norm_accum / vis_count (float32 division; vis_count 0 is never chosen),
+     chosen = avg >= grad_threshold (pixel units of the accumulated |dL/d mean2d|),
+     large = max_k log_scale_k > float32(log(scale_threshold)) (3DGS: 0.01 x scene extent),
+     clone = chosen and not large: an identical copy is added,
+     split = chosen and large: replaced by 2 children with means mu + R(q/|q|)(exp(l) * z_c),
+             z_c = normals[i, c] (device float [n,2,3], the caller's standard normal draws; only
+             the rows of split Gaussians are read), log-scales l - log(1.6), every other
+             parameter copied.
+   New order: the Gaussians not split (in order), the clones (in order), the first children of
+   the split Gaussians (in order), their second children.
+   out: caller-allocated arrays with room for `capacity` Gaussians, in the layouts of
+   tgs_gaussians under the field names of tgs_grads (NULL fields, or absent inputs, are not
+   written); sh_degree_out [capacity] uint8 or NULL; src_index [capacity] device uint32 or NULL
+   receives the old index of each new row (children and clones: their source). The outputs must
+   not overlap the inputs. *n_out (host) = n + n_clone + n_split; n_clone and n_split (host) may
+   be NULL. Synchronises the stream once to read the counts; returns TGS_ERR_CAPACITY (counts
+   set, nothing written) when *n_out > capacity. TGS_ERR_INVALID_ARG for null arguments, a
+   non-positive scale_threshold or float16 parameters. */
+tgs_status tgs_densify(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_stats *stats, const float *normals,
+                       float grad_threshold, float scale_threshold, const tgs_grads *out, uint8_t *sh_degree_out,
+                       uint32_t *src_index, int64_t capacity, int64_t *n_out, int64_t *n_clone, int64_t *n_split,
+                       tgs_stream stream);
 
 /* --- measurement ------------------------------------------------------------------------ */
 

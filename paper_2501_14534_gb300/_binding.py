@@ -109,6 +109,8 @@ SIGNATURES = {
     "tgs_params_to_half": (C.c_int32, [_gp, C.POINTER(tgs_half_params), _vp]),
     "tgs_compact": (C.c_int32, [_ctx_p, _gp, _vp, C.c_uint32, _gradp, _vp, _vp, C.POINTER(C.c_int64), _vp]),
     "tgs_mask_loss": (C.c_int32, [_ctx_p, _gp, _vp, _gradp, _vp]),
+    "tgs_densify": (C.c_int32, [_ctx_p, _gp, _statp, _vp, C.c_float, C.c_float, _gradp, _vp, _vp, C.c_int64,
+                                C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64), _vp]),
     "tgs_plan": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, C.c_double, C.POINTER(C.c_int64)]),
     "tgs_train_step_batched": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _pp, _pp, _gradp,
                                            _statp, _vp, C.c_uint32, _vp]),

@@ -706,18 +706,22 @@ tgs_status tgs_count_hits(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *
     cudaStream_t st = (cudaStream_t)stream;
     GaussPtrs gp;
     TGS_TRY(make_gauss(c->cfg, g, gp, true));
-    for (int v = 0; v < V; v++) {
-        CamBatch cb;
-        uint32_t *ids = nullptr;
-        TGS_TRY(plain_bin_view(c, g, gp, cams + v, cb, st, &ids));
-        PixPtrs px;
-        memset(&px, 0, sizeof px);  // nothing but the hits is written
-        launch_blend_forward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb,
-                             px, c->cfg.bg, st, hit_count, g->n);
-        TGS_TRY(last_error());
-    }
+    // all views at once: one preprocess, one binning (one host read of the key count), one
+    // forward blend over every (view, tile) counting hits
+    CamBatch cb;
+    TGS_TRY(make_batch(c->cfg, cams, V, cb));
+    const int64_t nt = g->n * V;
+    TGS_TRY(ensure_records(c, nt, st));
+    launch_preprocess(gp, cb, as<float4>(c->splats), as<int32_t>(c->radii), nullptr, as<uint32_t>(c->dbits),
+                      nullptr, st);
+    uint32_t *ids = nullptr;
     c->state_valid = false;  // the binning kept for a backward is not this one's
-    return TGS_OK;
+    TGS_TRY(bin_plain(c, g->n, cb, st, nullptr, -1, &ids));
+    PixPtrs px;
+    memset(&px, 0, sizeof px);  // nothing but the hits is written
+    launch_blend_forward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
+                         c->cfg.bg, st, hit_count, g->n);
+    return last_error();
 }
 
 tgs_status tgs_significance(tgs_ctx *c, const tgs_gaussians *g, const uint32_t *hit_count, double quantile,
@@ -802,6 +806,38 @@ tgs_status tgs_compact(tgs_ctx *c, const tgs_gaussians *g, const uint8_t *remove
     TGS_CHECK(cudaMemcpyAsync(c->h_counts + 3, counts + nb, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     TGS_CHECK(cudaStreamSynchronize(st));
     *n_kept = c->h_counts[3];
+    return last_error();
+}
+
+tgs_status tgs_densify(tgs_ctx *c, const tgs_gaussians *g, const tgs_stats *stats, const float *normals,
+                       float grad_threshold, float scale_threshold, const tgs_grads *out, uint8_t *sh_degree_out,
+                       uint32_t *src_index, int64_t capacity, int64_t *n_out, int64_t *n_clone, int64_t *n_split,
+                       tgs_stream stream) {
+    if (!c || !g || !stats || !out || !n_out || capacity < 0 || !(scale_threshold > 0.f)) return TGS_ERR_INVALID_ARG;
+    GaussPtrs gp;
+    TGS_TRY(make_gauss(c->cfg, g, gp));
+    *n_out = g->n;
+    if (n_clone) *n_clone = 0;
+    if (n_split) *n_split = 0;
+    if (g->n == 0) return TGS_OK;
+    if (!stats->grad_norm_accum || !stats->vis_count || !normals) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nb = compact_blocks(g->n);
+    TGS_TRY(ensure(c->cbuf, sizeof(uint32_t) * (size_t)(3 * (nb + 1) + 4), st));
+    uint32_t *scratch = as<uint32_t>(c->cbuf), *totals = scratch + 3 * (nb + 1);
+    DensifyArgs d{stats->grad_norm_accum, stats->vis_count, normals, grad_threshold,
+                  (float)std::log((double)scale_threshold)};
+    GradPtrs o = grad_ptrs(out, nullptr, 0);
+    launch_densify(gp, d, o, sh_degree_out, src_index, scratch, totals, false, st);
+    uint32_t h[3];
+    TGS_CHECK(cudaMemcpyAsync(h, totals, sizeof h, cudaMemcpyDeviceToHost, st));
+    TGS_CHECK(cudaStreamSynchronize(st));
+    const int64_t nn = (int64_t)h[0] + h[1] + 2 * (int64_t)h[2];
+    *n_out = nn;
+    if (n_clone) *n_clone = h[1];
+    if (n_split) *n_split = h[2];
+    if (nn > capacity) return TGS_ERR_CAPACITY;
+    launch_densify(gp, d, o, sh_degree_out, src_index, scratch, totals, true, st);
     return last_error();
 }
 

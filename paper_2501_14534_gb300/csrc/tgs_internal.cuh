@@ -234,6 +234,20 @@ int64_t compact_blocks(int64_t n);
 void launch_compact(const GaussPtrs &g, const uint8_t *remove, bool masked, const GradPtrs &out, uint8_t *deg_out,
                     uint32_t *kept_index, uint32_t *block_counts, uint32_t *total, cudaStream_t st);
 
+// compact.cu: densification by clone and split (3DGS's rule as stated in include/tgs.h).
+struct DensifyArgs {
+    const float *accum;      // [n] summed per-view |dL/d mean2d| (pixels)
+    const int32_t *count;    // [n] views where visible
+    const float *normals;    // [n,2,3] standard normals of the caller
+    float tau_g;             // threshold on accum / count
+    float tau_ls;            // float32(log(scale threshold)) on the largest log-scale
+};
+constexpr float kLogSplitDivisor = 0.47000362924573558f;  // log(1.6): children's scales / (0.8 x 2)
+// copy == false: per-block counts of (not split, clones, splits) and their scans into scratch
+// (3 (compact_blocks(n) + 1) words) with the totals in totals[0..2]; copy == true: the rows.
+void launch_densify(const GaussPtrs &g, const DensifyArgs &d, const GradPtrs &out, uint8_t *deg_out,
+                    uint32_t *src_index, uint32_t *scratch, uint32_t *totals, bool copy, cudaStream_t st);
+
 // significance.cu (Eq. significance-score)
 void launch_volumes(const GaussPtrs &g, float *vol, uint32_t *keys, cudaStream_t st);
 void launch_scores(const GaussPtrs &g, const uint32_t *hits, const float *vol, const uint32_t *sorted_vol_bits,

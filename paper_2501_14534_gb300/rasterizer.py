@@ -418,6 +418,29 @@ class Rasterizer:
                          sh_degree=deg[:k] if deg is not None else None, sh_degree_max=g.sh_degree_max)
         return kept, (idx[:k] if idx is not None else None)
 
+    # ---- densification ----
+
+    def densify(self, g: Gaussians, stats, normals, grad_threshold, scale_threshold):
+        """Clone and split from the statistics of the preprocess backward (tgs_densify; 3DGS's
+        rule). normals: CUDA float32 [n,2,3] standard normal draws. Returns (Gaussians, src_index,
+        n_clone, n_split) with src_index[new] = the old index of each row."""
+        assert normals.is_cuda and normals.dtype == torch.float32 and normals.is_contiguous()
+        assert normals.numel() == 6 * g.n
+        cap = 2 * g.n
+        out = {k: torch.empty((cap,) + tuple(v.shape[1:]), device="cuda", dtype=v.dtype)
+               for k, v in g.params().items()}
+        deg = torch.empty(cap, device="cuda", dtype=torch.uint8) if g.sh_degree is not None else None
+        src = torch.empty(cap, device="cuda", dtype=torch.int32)
+        n_out, n_clone, n_split = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+        B.check(B.lib.tgs_densify(self._h, C.byref(g.struct()), C.byref(self._stats_struct(stats)), _p(normals),
+                                  float(grad_threshold), float(scale_threshold), C.byref(self._grad_struct(out)),
+                                  _p(deg), _p(src), cap, C.byref(n_out), C.byref(n_clone), C.byref(n_split),
+                                  _stream()), "tgs_densify")
+        k = int(n_out.value)
+        new = Gaussians(**{name: t[:k] for name, t in out.items()},
+                        sh_degree=deg[:k] if deg is not None else None, sh_degree_max=g.sh_degree_max)
+        return new, src[:k], int(n_clone.value), int(n_split.value)
+
     # ---- significance pruning (Eq. significance-score) ----
 
     def count_hits(self, g: Gaussians, cams, hit_count=None):

@@ -91,3 +91,55 @@ def test_pruning_round(R):
     keep_ref = ~oracle.prune_select(s.astype(np.float64), 0.6)
     np.testing.assert_array_equal(np_(idx), np.flatnonzero(keep_ref))
     np.testing.assert_array_equal(np_(kept.means), scene["means"][keep_ref])
+
+
+# ---- densification (clone and split) ---------------------------------------------------------
+
+@pytest.mark.parametrize("n,degree", [(1, False), (33, False), (1025, True), (70001, False)])
+def test_densify_matches_oracle(R, n, degree):
+    """tgs_densify against the oracle on seeded statistics: the same Gaussians cloned and split
+    (decisions bit-exact, in float32 on both sides), the index map and every copied row bit for
+    bit, the children's means and log-scales within float32 rounding of the float64 oracle."""
+    scene = synth.blob_scene(n, 4, 40 + n, log_scale=(-3.0, 0.7), masks=not degree, per_gaussian_degree=degree)
+    rng = np.random.default_rng(n)
+    count = rng.integers(0, 6, size=n).astype(np.int32)
+    accum = (rng.exponential(0.5, size=n) * count).astype(np.float32)
+    normals = rng.normal(size=(n, 2, 3)).astype(np.float32)
+    tau_g, thr = 0.45, math.exp(-3.0)
+    rast = R.Rasterizer()
+    g = R.Gaussians.from_numpy(scene)
+    stats = {"grad_norm_accum": torch.from_numpy(accum).cuda(), "vis_count": torch.from_numpy(count).cuda()}
+    new, src, nc, ns = rast.densify(g, stats, torch.from_numpy(normals).cuda(), tau_g, thr)
+    ref, ref_src, rc, rs = oracle.densify(scene, accum, count, tau_g, thr, normals.astype(np.float64))
+    assert (nc, ns) == (rc, rs) and new.n == len(ref_src)
+    np.testing.assert_array_equal(np_(src).astype(np.int64), ref_src)
+    if n >= 1025:
+        assert nc > 0 and ns > 0
+    child = np.arange(new.n) >= n - ns + nc           # rows of the split children
+    for k in oracle.SCENE_KEYS:
+        if scene.get(k) is None:
+            continue
+        got = np_(getattr(new, k) if k != "sh_degree" else new.sh_degree)
+        if k in ("means", "log_scales"):
+            np.testing.assert_array_equal(got[~child], np.asarray(scene[k])[ref_src[~child]])
+            np.testing.assert_allclose(got[child], ref[k][child], rtol=2e-6, atol=2e-6, err_msg=k)
+        else:
+            np.testing.assert_array_equal(got, ref[k], err_msg=k)
+
+
+def test_densify_reports_capacity(R):
+    from paper_2501_14534_gb300 import _binding as B
+    import ctypes as C
+    scene = synth.blob_scene(500, 4, 41, log_scale=(-3.0, 0.7))
+    g = R.Gaussians.from_numpy(scene)
+    rast = R.Rasterizer()
+    stats = {"grad_norm_accum": torch.full((500,), 10.0, device="cuda"),
+             "vis_count": torch.ones(500, device="cuda", dtype=torch.int32)}
+    normals = torch.zeros((500, 2, 3), device="cuda")
+    out = {k: torch.empty_like(v) for k, v in g.params().items()}
+    n_out, nc, ns = C.c_int64(0), C.c_int64(0), C.c_int64(0)
+    st = B.lib.tgs_densify(rast._h, C.byref(g.struct()), C.byref(rast._stats_struct(stats)),
+                           C.c_void_p(normals.data_ptr()), 1.0, 0.05, C.byref(rast._grad_struct(out)), None, None,
+                           500, C.byref(n_out), C.byref(nc), C.byref(ns),
+                           C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == B.TGS_ERR_CAPACITY and n_out.value == 1000 and nc.value + ns.value == 500
