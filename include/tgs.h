@@ -124,7 +124,8 @@ typedef struct {
     float ssim_lambda;     /* lambda_SSIM of Eq. loss3dgs for TGS_LOSS_DSSIM, in [0, 1] (default 0.2) */
     float lambda_mask;     /* lambda_m of Eq. loss3dgs for TGS_MASK_LOSS, >= 0 (default 0.05) */
     float lambda_sh_mask;  /* lambda_sh of Eq. loss3dgs for TGS_MASK_LOSS, >= 0 (default 0.05) */
-    int32_t reserved0;
+    int32_t batch;         /* Gaussians staged per shared-memory batch of the fused blend, as a
+                              multiple of its threads: 1 or 2 (0 = 1); tuned by tgs_autotune */
 } tgs_config;
 
 #define TGS_PARAM_F32 0         /* parameter arrays hold float32 */
@@ -279,8 +280,13 @@ tgs_status tgs_train_step_batched_host(tgs_ctx *ctx, const tgs_gaussians *g_host
                                        int32_t V, const float *const *targets_host, const tgs_grads *grads,
                                        const tgs_stats *stats, float *loss_host, uint32_t flags,
                                        tgs_stream stream);
-/* Times the batched step for tile in {8, 16, 32} x ppt in {1, 2, 4} and keeps the fastest in
-   the context's config. cache_path (may be NULL) is a JSON file read first and written after. */
+/* Times the batched step for tile in {8, 16, 32} x ppt in {1, 2, 4} x batch in {1, 2} (the
+   supported combinations; 2 warm-up and 3 timed steps each) and keeps the fastest in the
+   context's config, with a key capacity planned for it. cache_path (may be NULL) is a JSON file
+   {"n<N>_V<V>_<W>x<H>...": {"tile": T, "ppt": P, "batch": B}, ...}: an entry for these Gaussian
+   count and view sizes is adopted without timing; otherwise the result is added and the file
+   rewritten. Synchronises the stream. Images do not depend on the choice (a Gaussian covers
+   the pixels of its rect, whatever the tile). */
 tgs_status tgs_autotune(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
                         const float *const *targets, const char *cache_path,
                         tgs_stream stream);

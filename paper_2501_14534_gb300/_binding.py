@@ -43,7 +43,7 @@ class tgs_config(C.Structure):
                 ("low_pass", C.c_float), ("eps_mask", C.c_float), ("eps_sh", C.c_float),
                 ("near_plane", C.c_float), ("bg", C.c_float * 3), ("key_capacity", C.c_int64),
                 ("spin_limit", C.c_int64), ("ssim_lambda", C.c_float), ("lambda_mask", C.c_float),
-                ("lambda_sh_mask", C.c_float), ("reserved0", C.c_int32)]
+                ("lambda_sh_mask", C.c_float), ("batch", C.c_int32)]
 
 
 class tgs_gaussians(C.Structure):

@@ -127,7 +127,8 @@ bool valid_cfg(const tgs_config &c) {
     return blend_supported(c.tile, c.ppt) && (c.support == TGS_SUPPORT_BOX3 || c.support == TGS_SUPPORT_ALPHA) &&
            c.low_pass >= 0.f && c.eps_mask > 0.f && c.eps_mask < 1.f && c.eps_sh > 0.f && c.eps_sh < 1.f &&
            c.near_plane > 0.f && c.key_capacity >= 0 && c.ssim_lambda >= 0.f && c.ssim_lambda <= 1.f &&
-           c.lambda_mask >= 0.f && c.lambda_mask < 1e30f && c.lambda_sh_mask >= 0.f && c.lambda_sh_mask < 1e30f;
+           c.lambda_mask >= 0.f && c.lambda_mask < 1e30f && c.lambda_sh_mask >= 0.f && c.lambda_sh_mask < 1e30f &&
+           c.batch >= 0 && c.batch <= 2;
 }
 
 tgs_status make_batch(const tgs_config &cfg, const tgs_camera *cams, int V, CamBatch &cb) {
@@ -342,6 +343,69 @@ void with_mask_loss(const tgs_config &cfg, int64_t n, GradPtrs &o) {
     if (n <= 0) return;
     o.lam_m_n = (float)((double)cfg.lambda_mask / (double)n);
     o.lam_sh_n = (float)((double)cfg.lambda_sh_mask / (double)n);
+}
+
+// Entries of the autotuner's JSON cache, {"key": {"tile": T, "ppt": P, "batch": B}, ...}, with any
+// whitespace and field order; "batch" defaults to 1; malformed entries are skipped.
+template <class F>
+void parse_tune_cache(const std::string &s, F &&emit) {
+    size_t i = 0;
+    const size_t n = s.size();
+    auto skip_ws = [&]() {
+        while (i < n && (s[i] == ' ' || s[i] == '\n' || s[i] == '\r' || s[i] == '\t')) i++;
+    };
+    auto read_str = [&](std::string &out) {
+        if (i >= n || s[i] != '"') return false;
+        const size_t e = s.find('"', i + 1);
+        if (e == std::string::npos) return false;
+        out = s.substr(i + 1, e - i - 1);
+        i = e + 1;
+        return true;
+    };
+    skip_ws();
+    if (i >= n || s[i] != '{') return;
+    i++;
+    for (;;) {
+        skip_ws();
+        std::string key;
+        if (!read_str(key)) return;
+        skip_ws();
+        if (i >= n || s[i] != ':') return;
+        i++;
+        skip_ws();
+        if (i >= n || s[i] != '{') return;
+        i++;
+        int vals[3] = {0, 0, 1};  // tile, ppt, batch
+        for (;;) {
+            skip_ws();
+            if (i < n && s[i] == '}') {
+                i++;
+                break;
+            }
+            std::string field;
+            if (!read_str(field)) return;
+            skip_ws();
+            if (i >= n || s[i] != ':') return;
+            i++;
+            skip_ws();
+            char *end = nullptr;
+            const long v = strtol(s.c_str() + i, &end, 10);
+            if (end == s.c_str() + i) return;
+            i = (size_t)(end - s.c_str());
+            if (field == "tile") vals[0] = (int)v;
+            else if (field == "ppt") vals[1] = (int)v;
+            else if (field == "batch") vals[2] = (int)v;
+            skip_ws();
+            if (i < n && s[i] == ',') i++;
+        }
+        emit(key, vals[0], vals[1], vals[2]);
+        skip_ws();
+        if (i < n && s[i] == ',') {
+            i++;
+            continue;
+        }
+        return;
+    }
 }
 
 bool same_cam(const tgs_camera &a, const tgs_camera &b) { return memcmp(&a, &b, sizeof a) == 0; }
@@ -949,7 +1013,7 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
         int *counter = reinterpret_cast<int *>(as<uint32_t>(c->counts) + 2);
         TGS_CHECK(cudaMemsetAsync(counter, 0, sizeof(int), st));
         mark(c, stage++, "fused_blend", st);
-        launch_fused_l1(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), order, counter,
+        launch_fused_l1(c->cfg.tile, c->cfg.ppt, c->cfg.batch > 1 ? 2 : 1, as<float4>(c->splats), ids, as<uint2>(c->ranges), order, counter,
                         cb, px, c->cfg.bg, as<float>(c->sgrads), loss_out, as<uint16_t>(c->viskeys), st,
                         stats ? stats->hit_count : nullptr, n);
     }
@@ -1185,30 +1249,36 @@ tgs_status tgs_autotune(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *ca
     // cache key: n, V and the view sizes
     std::string key = "n" + std::to_string(g->n) + "_V" + std::to_string(V);
     for (int v = 0; v < V; v++) key += "_" + std::to_string(cams[v].width) + "x" + std::to_string(cams[v].height);
-    std::vector<std::pair<std::string, std::pair<int, int>>> cache;
+    struct Entry {
+        std::string key;
+        int tile, ppt, batch;
+    };
+    std::vector<Entry> cache;
     if (cache_path) {
-        FILE *f = fopen(cache_path, "r");
-        if (f) {
-            char line[1024];
-            while (fgets(line, sizeof line, f)) {
-                char k[900];
-                int tl = 0, pp = 0;
-                if (sscanf(line, " \"%899[^\"]\" : { \"tile\" : %d , \"ppt\" : %d", k, &tl, &pp) == 3)
-                    cache.push_back({k, {tl, pp}});
-            }
+        std::string text;
+        if (FILE *f = fopen(cache_path, "r")) {
+            char buf[4096];
+            size_t got;
+            while ((got = fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
             fclose(f);
         }
+        parse_tune_cache(text, [&cache](const std::string &k, int tl, int pp, int bt) {
+            cache.push_back({k, tl, pp, bt});
+        });
         for (auto &e : cache)
-            if (e.first == key) {
+            if (e.key == key) {  // a cached choice: adopted without timing anything
                 tgs_config cf = c->cfg;
-                cf.tile = e.second.first;
-                cf.ppt = e.second.second;
+                cf.tile = e.tile;
+                cf.ppt = e.ppt;
+                cf.batch = e.batch;
+                cf.key_capacity = 0;
                 if (!valid_cfg(cf)) break;
                 TGS_TRY(tgs_set_config(c, &cf));
                 return tgs_plan(c, g, cams, V, 1.25, nullptr);
             }
     }
-    const int tiles[3] = {8, 16, 32}, ppts[3] = {1, 2, 4};
+    // tile x pixels per thread x Gaussians per shared-memory batch (multiples of the threads)
+    const int tiles[3] = {8, 16, 32}, ppts[3] = {1, 2, 4}, batches[2] = {1, 2};
     float best = 1e30f;
     tgs_config best_cfg = c->cfg, base = c->cfg;
     struct Events {  // destroyed on every return path
@@ -1226,23 +1296,30 @@ tgs_status tgs_autotune(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *ca
             tgs_config cf = base;
             cf.tile = tl;
             cf.ppt = pp;
+            cf.batch = 1;
             if (!valid_cfg(cf)) continue;
             cf.key_capacity = 0;
             TGS_TRY(tgs_set_config(c, &cf));
-            TGS_TRY(tgs_plan(c, g, cams, V, 1.25, nullptr));
-            for (int w = 0; w < 2; w++)
-                TGS_TRY(tgs_train_step_batched(c, g, cams, V, targets, nullptr, nullptr, nullptr, nullptr, 0, st));
-            TGS_CHECK(cudaEventRecord(e0, st));
-            const int reps = 3;
-            for (int r = 0; r < reps; r++)
-                TGS_TRY(tgs_train_step_batched(c, g, cams, V, targets, nullptr, nullptr, nullptr, nullptr, 0, st));
-            TGS_CHECK(cudaEventRecord(e1, st));
-            TGS_CHECK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            TGS_CHECK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) {
-                best = ms;
-                best_cfg = cf;
+            TGS_TRY(tgs_plan(c, g, cams, V, 1.25, nullptr));  // keys depend on the tile only
+            const int64_t cap = c->cfg.key_capacity;
+            for (int bt : batches) {
+                cf.batch = bt;
+                cf.key_capacity = cap;
+                TGS_TRY(tgs_set_config(c, &cf));
+                for (int w = 0; w < 2; w++)
+                    TGS_TRY(tgs_train_step_batched(c, g, cams, V, targets, nullptr, nullptr, nullptr, nullptr, 0, st));
+                TGS_CHECK(cudaEventRecord(e0, st));
+                const int reps = 3;
+                for (int r = 0; r < reps; r++)
+                    TGS_TRY(tgs_train_step_batched(c, g, cams, V, targets, nullptr, nullptr, nullptr, nullptr, 0, st));
+                TGS_CHECK(cudaEventRecord(e1, st));
+                TGS_CHECK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                TGS_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    best_cfg = cf;
+                }
             }
         }
     best_cfg.key_capacity = 0;
@@ -1251,17 +1328,19 @@ tgs_status tgs_autotune(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *ca
     if (cache_path) {
         bool found = false;
         for (auto &e : cache)
-            if (e.first == key) {
-                e.second = {best_cfg.tile, best_cfg.ppt};
+            if (e.key == key) {
+                e.tile = best_cfg.tile;
+                e.ppt = best_cfg.ppt;
+                e.batch = best_cfg.batch;
                 found = true;
             }
-        if (!found) cache.push_back({key, {best_cfg.tile, best_cfg.ppt}});
+        if (!found) cache.push_back({key, best_cfg.tile, best_cfg.ppt, best_cfg.batch});
         FILE *f = fopen(cache_path, "w");
         if (f) {
             fprintf(f, "{\n");
             for (size_t i = 0; i < cache.size(); i++)
-                fprintf(f, "  \"%s\": {\"tile\": %d, \"ppt\": %d}%s\n", cache[i].first.c_str(),
-                        cache[i].second.first, cache[i].second.second, i + 1 < cache.size() ? "," : "");
+                fprintf(f, "  \"%s\": {\"tile\": %d, \"ppt\": %d, \"batch\": %d}%s\n", cache[i].key.c_str(),
+                        cache[i].tile, cache[i].ppt, cache[i].batch, i + 1 < cache.size() ? "," : "");
             fprintf(f, "}\n");
             fclose(f);
         }

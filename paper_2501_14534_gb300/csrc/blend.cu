@@ -15,7 +15,7 @@ k_blend_fwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
             const uint2 *__restrict__ ranges, const __grid_constant__ CamBatch cb,
             const __grid_constant__ PixPtrs px, float bg0, float bg1, float bg2,
             uint32_t *__restrict__ hits, uint32_t n_gauss) {
-    __shared__ BlendSmem<TILE * TILE / PPT> sm;
+    __shared__ BlendSmemFor<TILE, PPT, COUNT> sm;
     const int gt = blockIdx.x;
     const int v = view_of_tile(cb, gt);
     const DevCam &cam = cb.c[v];
@@ -23,8 +23,11 @@ k_blend_fwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
     TilePixels<TILE, PPT> P;
     P.init(lt % cam.gx, lt / cam.gx, cam.W, cam.H);
     FwdState<PPT> S;
-    tile_forward<TILE, PPT, COUNT, false, HITS>(sm, splats, ids, ranges[gt], P, S, nullptr, hits,
-                                                (uint32_t)v * n_gauss);
+    if constexpr (PPT == 2 && !COUNT)
+        tile_forward2<TILE, false, HITS>(sm, splats, ids, ranges[gt], P, S, nullptr, hits, (uint32_t)v * n_gauss);
+    else
+        tile_forward<TILE, PPT, COUNT, false, HITS>(sm, splats, ids, ranges[gt], P, S, nullptr, hits,
+                                                    (uint32_t)v * n_gauss);
     const int HW = cam.W * cam.H;
     float *img = px.image[v];
     float *Tf = px.T_final[v];

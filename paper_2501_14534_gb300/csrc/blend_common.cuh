@@ -10,6 +10,8 @@
 // staged values, so their skip decisions (alpha < 1/255, the rect) agree bit for bit.
 #pragma once
 
+#include <type_traits>
+
 #include "tgs_internal.cuh"
 
 namespace tgs {
@@ -156,14 +158,15 @@ struct FwdState {
 // number of list entries it examined.
 // With HITS every blended fragment counts one ray hit of its Gaussian (Eq.
 // significance-score): hits[record - rec_off] += the pixels of the warp that blended it.
-template <int TILE, int PPT, bool COUNT = false, bool KEEPVIS = false, bool HITS = false>
-__device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
+template <int TILE, int PPT, bool COUNT = false, bool KEEPVIS = false, bool HITS = false, int SB = 1>
+__device__ __forceinline__ void tile_forward(BlendSmem<SB * TILE * TILE / PPT> &sm,
                                              const float4 *__restrict__ splats,
                                              const uint32_t *__restrict__ ids, uint2 rg,
                                              const TilePixels<TILE, PPT> &P, FwdState<PPT> &S,
                                              uint16_t *__restrict__ vis_out = nullptr,
                                              uint32_t *__restrict__ hits = nullptr, uint32_t rec_off = 0) {
     constexpr int NT = TILE * TILE / PPT;
+    constexpr int BS = SB * NT;  // splats per shared-memory batch
     const unsigned full = 0xffffffffu;
     const int t = threadIdx.x;
 #pragma unroll
@@ -175,19 +178,22 @@ __device__ __forceinline__ void tile_forward(BlendSmem<TILE * TILE / PPT> &sm,
         S.eval[k] = S.contrib[k] = 0;
         S.done[k] = !P.inside[k];
     }
-    for (uint32_t base = rg.x; base < rg.y; base += NT) {
+    for (uint32_t base = rg.x; base < rg.y; base += BS) {
         bool mine = true;
 #pragma unroll
         for (int k = 0; k < PPT; k++) mine = mine && S.done[k];
         if (__syncthreads_count(mine) == NT) break;
-        const uint32_t j = base + t;
-        if (j < rg.y) {
-            stage_splat<TILE, PPT>(sm, t, splats, __ldg(ids + j), P.tx0, P.ty0);
-            if (KEEPVIS) vis_out[j] = (uint16_t)sm.vis[t];  // read back by the backward's staging
+#pragma unroll
+        for (int sl = t; sl < BS; sl += NT) {
+            const uint32_t j = base + sl;
+            if (j < rg.y) {
+                stage_splat<TILE, PPT>(sm, sl, splats, __ldg(ids + j), P.tx0, P.ty0);
+                if (KEEPVIS) vis_out[j] = (uint16_t)sm.vis[sl];  // read back by the backward's staging
+            }
         }
         __syncthreads();
         if (__all_sync(full, mine)) continue;  // this warp is finished
-        const int cnt = min((uint32_t)NT, rg.y - base);
+        const int cnt = min((uint32_t)BS, rg.y - base);
         const int pos0 = (int)(base - rg.x);
         bool warp_done = false;
         for (int c0 = 0; c0 < cnt && !warp_done; c0 += 32) {
@@ -310,8 +316,8 @@ struct BwdInput {
 // contention of full warps).
 constexpr int kDirectLanes = 28;
 
-template <int TILE, int PPT, bool MOMENTS = false, bool KEEPVIS = false>
-__device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
+template <int TILE, int PPT, bool MOMENTS = false, bool KEEPVIS = false, int SB = 1>
+__device__ __forceinline__ void tile_backward(BlendSmem<SB * TILE * TILE / PPT> &sm,
                                               const float4 *__restrict__ splats,
                                               const uint32_t *__restrict__ ids, uint2 rg,
                                               const TilePixels<TILE, PPT> &P, const BwdInput<PPT> &in,
@@ -319,6 +325,7 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
                                               float *__restrict__ sgrads,
                                               const uint16_t *__restrict__ vis_in = nullptr) {
     constexpr int NT = TILE * TILE / PPT;
+    constexpr int BS = SB * NT;  // splats per shared-memory batch
     const unsigned full = 0xffffffffu;
     const int t = threadIdx.x, lane = t & 31;
     // acd = (colour of the fragments behind the current one, blended among themselves) . dL/dC
@@ -340,12 +347,15 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
     const uint32_t end = min(rg.y, rg.x + (uint32_t)sm.maxlast);
 
     for (uint32_t bend = end; bend > rg.x;) {
-        const uint32_t bstart = (bend - rg.x > (uint32_t)NT) ? bend - NT : rg.x;
+        const uint32_t bstart = (bend - rg.x > (uint32_t)BS) ? bend - BS : rg.x;
         const int cnt = (int)(bend - bstart);
         __syncthreads();
-        if (t < cnt) {  // slot t holds list position bend-1-t
-            stage_splat<TILE, PPT, NT, !KEEPVIS>(sm, t, splats, __ldg(ids + bend - 1 - t), P.tx0, P.ty0);
-            if (KEEPVIS) sm.vis[t] = vis_in[bend - 1 - t];  // as the forward's staging found it
+#pragma unroll
+        for (int sl = t; sl < BS; sl += NT) {
+            if (sl < cnt) {  // slot sl holds list position bend-1-sl
+                stage_splat<TILE, PPT, BS, !KEEPVIS>(sm, sl, splats, __ldg(ids + bend - 1 - sl), P.tx0, P.ty0);
+                if (KEEPVIS) sm.vis[sl] = vis_in[bend - 1 - sl];  // as the forward's staging found it
+            }
         }
         __syncthreads();
         const int top = (int)(bend - rg.x);   // 1-based position of slot 0
@@ -457,5 +467,226 @@ __device__ __forceinline__ void tile_backward(BlendSmem<TILE * TILE / PPT> &sm,
         bend = bstart;
     }
 }
+
+// ---- packed pairs (2 pixels per thread) ----------------------------------------------------
+//
+// A thread's two pixels share their column (rows y and y + RS), so every splat operand is the
+// same for both: their arithmetic runs as fma/mul/add/sub.rn.f32x2 on (pixel 0, pixel 1) pairs.
+// Each half of a packed instruction is the IEEE operation the scalar code applies to that pixel,
+// in the same order, so images, transmittances and every blend decision are bit-identical to
+// the scalar path; the floating-point instructions issued halve. The staged splat scalars are
+// stored pre-duplicated as pairs, so one 16-byte shared load yields two ready pair operands.
+
+typedef unsigned long long f2_t;  // two floats (pixel 0, pixel 1) in one 64-bit register pair
+
+__device__ __forceinline__ f2_t f2(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2get(f2_t a, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+}
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t sub2(f2_t a, f2_t b) {
+    f2_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
+    f2_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {  // a * b + c
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ float sum2(f2_t a) {
+    float lo, hi;
+    f2get(a, lo, hi);
+    return lo + hi;
+}
+
+template <int NT>
+struct BlendSmem2 {
+    ulonglong2 p0[NT];  // (mx, mx), (my, my)
+    ulonglong2 p1[NT];  // (A, A), (B, B): the conic scaled as in stage_splat
+    ulonglong2 p2[NT];  // (C, C), (o, o)
+    ulonglong2 p3[NT];  // (r, r), (g, g)
+    float4 p4[NT];      // b, b, qmin, cover bits
+    int4 rect[NT];      // inclusive pixel rect x_lo, x_hi, y_lo, y_hi
+    uint32_t hit[NT], vis[NT], id[NT];
+    int maxlast;
+};
+
+// The values of stage_splat, stored as pairs.
+template <int TILE, int NT, bool VIS = true>
+__device__ __forceinline__ void stage_splat2(BlendSmem2<NT> &sm, int slot, const float4 *__restrict__ splats,
+                                             uint32_t id, int tx0, int ty0) {
+    constexpr int PPT = 2;
+    const float4 *rp = splats + (size_t)kSplatWords / 4 * id;
+    const float4 s0 = __ldg(rp), s1 = __ldg(rp + 1), s2 = __ldg(rp + 2);
+    const float A = __fmul_rn(-0.5f * kLog2e, s0.z), B = __fmul_rn(-kLog2e, s0.w);
+    const float Cq = __fmul_rn(-0.5f * kLog2e, s1.x);
+    sm.p0[slot] = make_ulonglong2(f2(s0.x, s0.x), f2(s0.y, s0.y));
+    sm.p1[slot] = make_ulonglong2(f2(A, A), f2(B, B));
+    sm.p2[slot] = make_ulonglong2(f2(Cq, Cq), f2(s1.y, s1.y));
+    sm.p3[slot] = make_ulonglong2(f2(s1.z, s1.z), f2(s1.w, s1.w));
+    const float qmin = -log2f(__fmul_rn(255.f, s1.y));
+    const uint32_t rx = __float_as_uint(s2.y), ry = __float_as_uint(s2.z);
+    const int4 r = make_int4((int)(rx & 0xFFFFu), (int)(rx >> 16), (int)(ry & 0xFFFFu), (int)(ry >> 16));
+    sm.rect[slot] = r;
+    uint32_t hit, cov;
+    block_masks<TILE, PPT>(r.x, r.y, r.z, r.w, tx0, ty0, hit, cov);
+    sm.hit[slot] = hit;
+    sm.p4[slot] = make_float4(s2.x, s2.x, qmin, __uint_as_float(cov));
+    sm.id[slot] = id;
+    if (!VIS) return;
+    using L = BlendLayout<TILE, PPT>;
+    const float4 s3 = __ldg(rp + 3);
+    uint32_t vis = hit, bits = hit;
+    while (bits) {
+        const int w = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        const int bx0 = tx0 + (w % L::WX) * L::BW, by0 = ty0 + (w / L::WX) * L::BH;
+        if (!tile_keep(s0.x, s0.y, s0.z, s0.w, s1.x, s3.x, s3.y, s3.z, max(bx0, r.x),
+                       min(bx0 + L::BW - 1, r.y), max(by0, r.z), min(by0 + L::BH - 1, r.w)))
+            vis &= ~(1u << w);
+    }
+    sm.vis[slot] = vis;
+}
+
+// tile_forward for 2 pixels per thread with packed pairs (no per-pixel counters).
+template <int TILE, bool KEEPVIS = false, bool HITS = false, int SB = 1>
+__device__ __forceinline__ void tile_forward2(BlendSmem2<SB * TILE * TILE / 2> &sm, const float4 *__restrict__ splats,
+                                              const uint32_t *__restrict__ ids, uint2 rg,
+                                              const TilePixels<TILE, 2> &P, FwdState<2> &S,
+                                              uint16_t *__restrict__ vis_out = nullptr,
+                                              uint32_t *__restrict__ hits = nullptr, uint32_t rec_off = 0) {
+    constexpr int NT = TILE * TILE / 2;
+    constexpr int BS = SB * NT;  // splats per shared-memory batch
+    const unsigned full = 0xffffffffu;
+    const int t = threadIdx.x;
+    const f2_t one2 = f2(1.f, 1.f);
+    const f2_t fx2 = f2(P.fx[0], P.fx[0]);  // same column
+    const f2_t fy2 = f2(P.fy[0], P.fy[1]);
+    f2_t T2 = one2, Cr2 = f2(0.f, 0.f), Cg2 = Cr2, Cb2 = Cr2;
+    int last0 = 0, last1 = 0, exam0 = 0, exam1 = 0;
+    bool done0 = !P.inside[0], done1 = !P.inside[1];
+    for (uint32_t base = rg.x; base < rg.y; base += BS) {
+        const bool mine = done0 && done1;
+        if (__syncthreads_count(mine) == NT) break;
+#pragma unroll
+        for (int sl = t; sl < BS; sl += NT) {
+            const uint32_t j = base + sl;
+            if (j < rg.y) {
+                stage_splat2<TILE, BS>(sm, sl, splats, __ldg(ids + j), P.tx0, P.ty0);
+                if (KEEPVIS) vis_out[j] = (uint16_t)sm.vis[sl];  // read back by the backward's staging
+            }
+        }
+        __syncthreads();
+        if (__all_sync(full, mine)) continue;  // this warp is finished
+        const int cnt = min((uint32_t)BS, rg.y - base);
+        const int pos0 = (int)(base - rg.x);
+        bool warp_done = false;
+        for (int c0 = 0; c0 < cnt && !warp_done; c0 += 32) {
+            uint32_t bits = __ballot_sync(full, (c0 + (t & 31) < cnt) && (sm.vis[c0 + (t & 31)] & P.wbit));
+            while (bits) {
+                const int m = c0 + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const int4 r = sm.rect[m];
+                const float4 p4 = sm.p4[m];
+                const bool cover = (__float_as_uint(p4.w) & P.wbit) != 0u;
+                const bool xin = cover || (unsigned)(P.x[0] - r.x) <= (unsigned)(r.y - r.x);
+                const bool in0 = !done0 && (cover || (xin && (unsigned)(P.y[0] - r.z) <= (unsigned)(r.w - r.z)));
+                const bool in1 = !done1 && (cover || (xin && (unsigned)(P.y[1] - r.z) <= (unsigned)(r.w - r.z)));
+                bool b0 = false, b1 = false;  // the pixels that blend this fragment
+                if (in0 || in1) {
+                    const ulonglong2 a = sm.p0[m], b = sm.p1[m], c = sm.p2[m];
+                    const f2_t dx2 = sub2(a.x, fx2);
+                    const f2_t dy2 = sub2(a.y, fy2);
+                    const f2_t q2 = fma2(dx2, fma2(b.y, dy2, mul2(b.x, dx2)), mul2(mul2(c.x, dy2), dy2));
+                    float qa, qb;
+                    f2get(q2, qa, qb);
+                    const float qmin = p4.z;
+                    const bool v0 = in0 && !(qa > 0.f || qa < qmin);  // alpha >= 1/255
+                    const bool v1 = in1 && !(qb > 0.f || qb < qmin);
+                    if (v0 || v1) {
+                        float xa, xb;
+                        f2get(mul2(c.y, f2(ex2_approx(qa), ex2_approx(qb))), xa, xb);
+                        const f2_t al2 = f2(v0 ? fminf(kAlphaMax, xa) : 0.f, v1 ? fminf(kAlphaMax, xb) : 0.f);
+                        const f2_t tT2 = mul2(T2, sub2(one2, al2));
+                        float ta, tb;
+                        f2get(tT2, ta, tb);
+                        const bool s0 = v0 && ta < kTMin, s1 = v1 && tb < kTMin;  // stop before this fragment
+                        b0 = v0 && !s0;
+                        b1 = v1 && !s1;
+                        const int pos = pos0 + m + 1;
+                        if (s0) {
+                            done0 = true;
+                            exam0 = pos;
+                        }
+                        if (s1) {
+                            done1 = true;
+                            exam1 = pos;
+                        }
+                        if (b0 || b1) {
+                            float wa, wb, Ta, Tb;
+                            f2get(mul2(al2, T2), wa, wb);
+                            const f2_t w2 = f2(b0 ? wa : 0.f, b1 ? wb : 0.f);
+                            const ulonglong2 col = sm.p3[m];
+                            Cr2 = fma2(col.x, w2, Cr2);
+                            Cg2 = fma2(col.y, w2, Cg2);
+                            Cb2 = fma2(f2(p4.x, p4.y), w2, Cb2);
+                            f2get(T2, Ta, Tb);
+                            T2 = f2(b0 ? ta : Ta, b1 ? tb : Tb);
+                            if (b0) last0 = pos;
+                            if (b1) last1 = pos;
+                        }
+                    }
+                }
+                if (HITS) {
+                    const uint32_t tot = __reduce_add_sync(full, (uint32_t)b0 + (uint32_t)b1);
+                    if ((t & 31) == 0 && tot) atomicAdd(hits + (sm.id[m] - rec_off), tot);
+                }
+            }
+            warp_done = __all_sync(full, done0 && done1);
+        }
+    }
+    const int len = (int)(rg.y - rg.x);
+    f2get(T2, S.T[0], S.T[1]);
+    f2get(Cr2, S.Cr[0], S.Cr[1]);
+    f2get(Cg2, S.Cg[0], S.Cg[1]);
+    f2get(Cb2, S.Cb[0], S.Cb[1]);
+    S.last[0] = last0;
+    S.last[1] = last1;
+    S.exam[0] = (P.inside[0] && exam0 == 0) ? len : exam0;  // never stopped: saw the whole list
+    S.exam[1] = (P.inside[1] && exam1 == 0) ? len : exam1;
+    S.done[0] = done0;
+    S.done[1] = done1;
+    S.eval[0] = S.eval[1] = S.contrib[0] = S.contrib[1] = 0;
+}
+
+// Shared memory of a forward blend: the packed layout for 2 pixels per thread (without per-pixel
+// counters), the scalar one otherwise. The backward always stages the scalar layout: with its
+// chain of per-pixel decisions the pairs do not pay (measured: 4.98 ms scalar, 5.12 ms packed,
+// 5.36 ms packed exponents only, per batched step at tile 32), while the packed forward does
+// (2.98 -> 2.75 ms).
+template <int TILE, int PPT, bool COUNT = false>
+using BlendSmemFor = typename std::conditional<PPT == 2 && !COUNT, BlendSmem2<TILE * TILE / 2>,
+                                               BlendSmem<TILE * TILE / PPT>>::type;
+
+// The fused kernel's shared memory: the forward's layout, then the backward's in the same space.
+template <int TILE, int PPT, int SB = 1>
+union FusedSmem {
+    typename std::conditional<PPT == 2, BlendSmem2<SB * TILE * TILE / 2>, BlendSmem<SB * TILE * TILE / PPT>>::type f;
+    BlendSmem<SB * TILE * TILE / PPT> b;
+};
 
 }  // namespace tgs

@@ -32,7 +32,7 @@ __global__ void k_item_keys(const uint2 *__restrict__ ranges, int n, uint32_t *_
     vals[i] = (uint32_t)i;
 }
 
-template <int TILE, int PPT, bool HITS>
+template <int TILE, int PPT, bool HITS, int SB>
 __global__ void __launch_bounds__(TILE * TILE / PPT)
 k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
            const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, int n_items,
@@ -43,7 +43,8 @@ k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
     constexpr int NT = TILE * TILE / PPT;
     constexpr int NW = NT / 32;
     static_assert(NW <= 16, "the per-key warp masks are 16 bits");
-    __shared__ BlendSmem<NT> sm;
+    extern __shared__ __align__(16) unsigned char s_dyn[];  // FusedSmem<TILE, PPT, SB>
+    FusedSmem<TILE, PPT, SB> &sm = *reinterpret_cast<FusedSmem<TILE, PPT, SB> *>(s_dyn);
     __shared__ int s_item;
     __shared__ float s_loss[NW];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -61,7 +62,11 @@ k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
         P.init(lt % cam.gx, lt / cam.gx, cam.W, cam.H);
         const uint2 rg = ranges[gt];
         FwdState<PPT> S;
-        tile_forward<TILE, PPT, false, true, HITS>(sm, splats, ids, rg, P, S, vis_keys, hits, (uint32_t)v * n_gauss);
+        if constexpr (PPT == 2)
+            tile_forward2<TILE, true, HITS, SB>(sm.f, splats, ids, rg, P, S, vis_keys, hits, (uint32_t)v * n_gauss);
+        else
+            tile_forward<TILE, PPT, false, true, HITS, SB>(sm.f, splats, ids, rg, P, S, vis_keys, hits,
+                                                           (uint32_t)v * n_gauss);
 
         // L1 loss: L = mean over views of mean over 3HW |C - target|; dL/dC = sign / (3HWV)
         const int HW = cam.W * cam.H;
@@ -93,7 +98,7 @@ k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
         }
         lsum = warp_sum(lsum);
         if (lane == 0) s_loss[w] = lsum;
-        tile_backward<TILE, PPT, true, true>(sm, splats, ids, rg, P, in, bg0, bg1, bg2, sgrads, vis_keys);
+        tile_backward<TILE, PPT, true, true, SB>(sm.b, splats, ids, rg, P, in, bg0, bg1, bg2, sgrads, vis_keys);
         // s_loss was written before the barriers inside tile_backward
         if (t == 0 && loss) {
             float x = 0.f;
@@ -104,21 +109,22 @@ k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
     }
 }
 
-template <int TILE, int PPT, bool HITS>
+template <int TILE, int PPT, bool HITS, int SB>
 int fused_blocks_per_sm() {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_l1<TILE, PPT, HITS>, TILE * TILE / PPT, 0) !=
-        cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_l1<TILE, PPT, HITS, SB>, TILE * TILE / PPT,
+                                                      sizeof(FusedSmem<TILE, PPT, SB>)) != cudaSuccess) {
         cudaGetLastError();
         b = 1;
     }
     return b < 1 ? 1 : b;
 }
 
-template <int TILE, int PPT, bool HITS>
+template <int TILE, int PPT, bool HITS, int SB>
 void fused_launch_t(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const uint32_t *order,
                     int *counter, const CamBatch &cb, const PixPtrs &px, const float *bg, float *sgrads,
                     float *loss, uint16_t *vis_keys, uint32_t *hits, uint32_t n_gauss, cudaStream_t st) {
+    constexpr size_t smem = sizeof(FusedSmem<TILE, PPT, SB>);
     // persistent grid: SMs x resident CTAs per SM, found once per device
     constexpr int kDevices = 64;
     static std::mutex mu;
@@ -140,28 +146,37 @@ void fused_launch_t(const float4 *splats, const uint32_t *ids, const uint2 *rang
                 cudaGetLastError();
                 sms = 1;
             }
-            grid = sms * fused_blocks_per_sm<TILE, PPT, HITS>();
+            // dynamic shared memory beyond the default 48 KB is opted into once per device
+            if (cudaFuncSetAttribute(k_fused_l1<TILE, PPT, HITS, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem) != cudaSuccess)
+                cudaGetLastError();
+            grid = sms * fused_blocks_per_sm<TILE, PPT, HITS, SB>();
             if (dev >= 0 && dev < kDevices) grid_of[dev] = grid;
         }
     }
     if (grid > cb.total_tiles) grid = cb.total_tiles;
     if (grid < 1) grid = 1;
     count_launch();
-    k_fused_l1<TILE, PPT, HITS><<<grid, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, order, cb.total_tiles,
-                                                                    counter, cb, px, bg[0], bg[1], bg[2], sgrads,
-                                                                    loss, vis_keys, hits, n_gauss);
+    k_fused_l1<TILE, PPT, HITS, SB><<<grid, TILE * TILE / PPT, smem, st>>>(
+        splats, ids, ranges, order, cb.total_tiles, counter, cb, px, bg[0], bg[1], bg[2], sgrads, loss, vis_keys,
+        hits, n_gauss);
 }
 
 template <int TILE, int PPT>
-void fused_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const uint32_t *order,
+void fused_launch(int batch, const float4 *splats, const uint32_t *ids, const uint2 *ranges, const uint32_t *order,
                   int *counter, const CamBatch &cb, const PixPtrs &px, const float *bg, float *sgrads,
                   float *loss, uint16_t *vis_keys, uint32_t *hits, uint32_t n_gauss, cudaStream_t st) {
-    if (hits)
-        fused_launch_t<TILE, PPT, true>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys,
-                                        hits, n_gauss, st);
-    else
-        fused_launch_t<TILE, PPT, false>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys,
-                                         hits, n_gauss, st);
+#define TGS_FUSED(H, S)                                                                                     \
+    fused_launch_t<TILE, PPT, H, S>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, \
+                                    hits, n_gauss, st)
+    if (batch == 2) {
+        if (hits) TGS_FUSED(true, 2);
+        else TGS_FUSED(false, 2);
+    } else {
+        if (hits) TGS_FUSED(true, 1);
+        else TGS_FUSED(false, 1);
+    }
+#undef TGS_FUSED
 }
 
 }  // namespace
@@ -176,19 +191,19 @@ void build_item_order(const uint2 *ranges, int total_tiles, uint32_t *k0, uint32
     *order = v;
 }
 
-void launch_fused_l1(int tile, int ppt, const float4 *splats, const uint32_t *ids, const uint2 *ranges,
+void launch_fused_l1(int tile, int ppt, int batch, const float4 *splats, const uint32_t *ids, const uint2 *ranges,
                      const uint32_t *order, int *counter, const CamBatch &cb, const PixPtrs &px,
                      const float *bg, float *sgrads, float *loss, uint16_t *vis_keys, cudaStream_t st,
                      uint32_t *hits, int64_t n_gauss) {
     if (cb.total_tiles <= 0) return;
     const uint32_t n = (uint32_t)n_gauss;
-    if (tile == 8 && ppt == 1) fused_launch<8, 1>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
-    else if (tile == 8 && ppt == 2) fused_launch<8, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
-    else if (tile == 16 && ppt == 1) fused_launch<16, 1>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
-    else if (tile == 16 && ppt == 2) fused_launch<16, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
-    else if (tile == 16 && ppt == 4) fused_launch<16, 4>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
-    else if (tile == 32 && ppt == 2) fused_launch<32, 2>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
-    else if (tile == 32 && ppt == 4) fused_launch<32, 4>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    if (tile == 8 && ppt == 1) fused_launch<8, 1>(batch, splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    else if (tile == 8 && ppt == 2) fused_launch<8, 2>(batch, splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    else if (tile == 16 && ppt == 1) fused_launch<16, 1>(batch, splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    else if (tile == 16 && ppt == 2) fused_launch<16, 2>(batch, splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    else if (tile == 16 && ppt == 4) fused_launch<16, 4>(batch, splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    else if (tile == 32 && ppt == 2) fused_launch<32, 2>(batch, splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
+    else if (tile == 32 && ppt == 4) fused_launch<32, 4>(batch, splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
 }
 
 }  // namespace tgs

@@ -214,7 +214,7 @@ void build_item_order(const uint2 *ranges, int total_tiles, uint32_t *k0, uint32
                       uint32_t *v1, uint32_t **order, uint32_t *hist, uint32_t *partials, cudaStream_t st);
 // vis_keys: scratch of one uint16 per key (key capacity): the forward's per-warp visibility
 // masks of each list entry, read back by the backward
-void launch_fused_l1(int tile, int ppt, const float4 *splats, const uint32_t *ids, const uint2 *ranges,
+void launch_fused_l1(int tile, int ppt, int batch, const float4 *splats, const uint32_t *ids, const uint2 *ranges,
                      const uint32_t *order, int *counter, const CamBatch &cb, const PixPtrs &px,
                      const float *bg, float *sgrads, float *loss, uint16_t *vis_keys, cudaStream_t st,
                      uint32_t *hits = nullptr, int64_t n_gauss = 0);

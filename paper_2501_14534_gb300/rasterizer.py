@@ -126,11 +126,12 @@ class Rasterizer:
 
     def __init__(self, tile=16, ppt=1, support=B.TGS_SUPPORT_BOX3, low_pass=0.3, eps_mask=0.05,
                  eps_sh=0.1, near=0.2, bg=(0.0, 0.0, 0.0), key_capacity=0, ssim_lambda=0.2,
-                 lambda_mask=0.05, lambda_sh_mask=0.05):
+                 lambda_mask=0.05, lambda_sh_mask=0.05, batch=1):
         cfg = B.tgs_config()
         B.lib.tgs_default_config(C.byref(cfg))
         cfg.ssim_lambda = ssim_lambda
         cfg.lambda_mask, cfg.lambda_sh_mask = lambda_mask, lambda_sh_mask
+        cfg.batch = batch
         cfg.tile, cfg.ppt, cfg.support = tile, ppt, support
         cfg.low_pass, cfg.eps_mask, cfg.eps_sh, cfg.near_plane = low_pass, eps_mask, eps_sh, near
         for i in range(3):
@@ -509,7 +510,7 @@ class Rasterizer:
                                    None if cache_path is None else cache_path.encode(),
                                    _stream()), "tgs_autotune")
         cfg = self.config
-        return dict(tile=cfg.tile, ppt=cfg.ppt, key_capacity=cfg.key_capacity)
+        return dict(tile=cfg.tile, ppt=cfg.ppt, batch=cfg.batch, key_capacity=cfg.key_capacity)
 
 
 class RasterizeViews(torch.autograd.Function):

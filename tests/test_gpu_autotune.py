@@ -1,0 +1,89 @@
+"""The autotuner of the batched step (tile x pixels per thread x Gaussians per shared-memory
+batch): its JSON cache round-trips, a cached entry is adopted without timing anything, and
+the configuration it picks renders the same images, bit for bit, as tile 16 / 1 pixel per
+thread / one Gaussian per thread (images do not depend on the launch shape)."""
+import json
+
+import numpy as np
+import pytest
+
+from paper_2501_14534_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def R():
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA is not available: the GPU tests cannot run")
+    from paper_2501_14534_gb300 import build
+    build.build()
+    from paper_2501_14534_gb300 import rasterizer as R
+    return R
+
+
+def case():
+    scene = synth.blob_scene(20000, 8, 61, log_scale=(-3.5, 0.5))
+    sizes = [(160, 104), (320, 208), (320, 208)]
+    return scene, synth.ring_cameras(len(sizes), sizes), synth.target_images(62, sizes)
+
+
+def key_of(n, cams):
+    return f"n{n}_V{len(cams)}" + "".join(f"_{c.width}x{c.height}" for c in cams)
+
+
+def test_autotune_cache_round_trip_and_reuse(R, tmp_path):
+    scene, cams, targets = case()
+    g = R.Gaussians.from_numpy(scene)
+    tg = [torch.from_numpy(t).cuda() for t in targets]
+    path = tmp_path / "tune.json"
+    rast = R.Rasterizer(eps_mask=0.5, eps_sh=0.5)
+    got = rast.autotune(g, cams, tg, cache_path=str(path))
+    assert got["tile"] in (8, 16, 32) and got["ppt"] in (1, 2, 4) and got["batch"] in (1, 2)
+    assert got["key_capacity"] > 0
+    cache = json.loads(path.read_text())
+    assert cache[key_of(g.n, cams)] == {"tile": got["tile"], "ppt": got["ppt"], "batch": got["batch"]}
+    # a different cached choice is adopted as it stands: nothing was timed
+    other = {"tile": 8, "ppt": 2, "batch": 2} if got != {"tile": 8, "ppt": 2, "batch": 2} else \
+        {"tile": 16, "ppt": 1, "batch": 1}
+    cache[key_of(g.n, cams)] = other
+    cache["n1_V1_8x8"] = {"tile": 32, "ppt": 4, "batch": 1}   # another entry, kept
+    path.write_text(json.dumps(cache, indent=1))
+    fresh = R.Rasterizer(eps_mask=0.5, eps_sh=0.5)
+    got2 = fresh.autotune(g, cams, tg, cache_path=str(path))
+    assert {k: got2[k] for k in ("tile", "ppt", "batch")} == other
+    assert got2["key_capacity"] > 0
+    assert json.loads(path.read_text()) == cache   # a hit leaves the file as it was
+    # a step in the adopted configuration runs
+    grads = fresh.alloc_grads(g)
+    loss = torch.zeros(1, device="cuda")
+    fresh.train_step_batched(g, cams, tg, grads, None, loss)
+    fresh.poll()
+    assert loss.item() > 0
+
+
+def test_autotuned_config_renders_the_same_images(R):
+    scene, cams, targets = case()
+    g = R.Gaussians.from_numpy(scene)
+    tg = [torch.from_numpy(t).cuda() for t in targets]
+    tuned = R.Rasterizer(eps_mask=0.5, eps_sh=0.5)
+    tuned.autotune(g, cams, tg)
+    base = R.Rasterizer(tile=16, ppt=1, batch=1, eps_mask=0.5, eps_sh=0.5)
+    base.plan(g, cams)
+    out = {}
+    for name, r in (("tuned", tuned), ("base", base)):
+        imgs = [torch.empty((3, c.height, c.width), device="cuda") for c in cams]
+        grads = r.alloc_grads(g)
+        loss = torch.zeros(1, device="cuda")
+        r.train_step_batched(g, cams, tg, grads, None, loss, images=imgs)
+        r.poll()
+        out[name] = (imgs, grads, loss.item())
+    for a, b in zip(out["tuned"][0], out["base"][0]):
+        assert torch.equal(a, b)
+    assert abs(out["tuned"][2] - out["base"][2]) <= 1e-6 * out["base"][2]
+    for k in out["base"][1]:
+        a = out["tuned"][1][k].double().cpu().numpy()
+        b = out["base"][1][k].double().cpu().numpy()
+        assert np.linalg.norm(a - b) <= 1e-4 * max(np.linalg.norm(b), 1e-30), k

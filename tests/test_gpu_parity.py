@@ -333,13 +333,15 @@ def batched_case(n=4000):
     return scene, cams, targets, settings_for(eps=(0.5, 0.5))
 
 
-@pytest.mark.parametrize("tile,ppt,fused", [(16, 1, True), (8, 2, True), (32, 4, True),
-                                            (16, 2, True), (32, 2, True), (16, 4, False),
-                                            (32, 4, False)])
-def test_batched_train_step_matches_oracle(R, tile, ppt, fused):
+@pytest.mark.parametrize("tile,ppt,fused,batch", [(16, 1, True, 1), (8, 2, True, 1), (32, 4, True, 1),
+                                                  (16, 2, True, 1), (32, 2, True, 1), (16, 4, False, 1),
+                                                  (32, 4, False, 1), (32, 2, True, 2), (16, 1, True, 2),
+                                                  (8, 2, True, 2)])
+def test_batched_train_step_matches_oracle(R, tile, ppt, fused, batch):
     scene, cams, targets, st = batched_case()
     st.tile = tile
     rast = make_rast(R, st, ppt=ppt)
+    rast.set(batch=batch)
     g = gpu_scene(R, scene)
     tg = [torch.from_numpy(t).cuda() for t in targets]
     grads = rast.alloc_grads(g)
