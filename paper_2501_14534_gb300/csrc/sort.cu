@@ -168,6 +168,7 @@ k_count_keys(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict
     __shared__ int4 s_r[NW][32];       // pixel rect x0, x1, y0, y1 (inclusive)
     __shared__ uint32_t s_m[NW][32][2];  // kept-tile bits of rects of at most 64 tiles
     __shared__ uint32_t s_c[NW][32];     // kept-tile counts
+    __shared__ uint4 s_k[NW][32];        // pair prefix, nx (bit 31: at most 64 tiles), rcp(nx), tx0 | ty0 << 16
     __shared__ uint32_t s_warp[33];
     const int lb = __ffs(B) - 1;  // B is 8, 16 or 32
     const unsigned full = 0xffffffffu;
@@ -210,6 +211,8 @@ k_count_keys(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict
         const uint32_t inc = warp_incl_scan(ntiles, lane);
         const uint32_t excl = inc - ntiles;
         const uint32_t total = __shfl_sync(full, inc, 31);
+        s_k[w][lane] = make_uint4(excl, (uint32_t)nx | (ntiles <= 64u ? 0x80000000u : 0u), __float_as_uint(rcp),
+                                  (uint32_t)tx0 | ((uint32_t)ty0 << 16));
         __syncwarp();
         for (uint32_t p0 = 0; p0 < total; p0 += 32) {
             const uint32_t p = p0 + (uint32_t)lane;
@@ -218,22 +221,19 @@ k_count_keys(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict
 #pragma unroll
             for (int step = 16; step >= 1; step >>= 1)
                 if (__shfl_sync(full, excl, r + step) <= p) r += step;
-            const uint32_t er = __shfl_sync(full, excl, r);
-            const uint32_t nxr = (uint32_t)__shfl_sync(full, nx, r);
-            const float rcpr = __shfl_sync(full, rcp, r);
-            const int txr = __shfl_sync(full, tx0, r), tyr = __shfl_sync(full, ty0, r);
-            const uint32_t ntr = __shfl_sync(full, ntiles, r);
             if (p < total) {
-                const uint32_t local = p - er;
+                const uint4 kr = s_k[w][r];
+                const uint32_t local = p - kr.x;
+                const uint32_t nxr = kr.y & 0x7FFFFFFFu;
                 uint32_t row, col;
-                divmod_small(local, nxr, rcpr, row, col);
-                const int tx = txr + (int)col, ty = tyr + (int)row;
+                divmod_small(local, nxr, __uint_as_float(kr.z), row, col);
+                const int tx = (int)(kr.w & 0xFFFFu) + (int)col, ty = (int)(kr.w >> 16) + (int)row;
                 const float4 g = s_g[w][r], h = s_h[w][r];
                 const int4 rc = s_r[w][r];
                 if (tile_keep(g.x, g.y, g.z, g.w, h.x, h.y, h.z, h.w, max(tx * B, rc.x),
                               min(tx * B + B - 1, rc.y), max(ty * B, rc.z), min(ty * B + B - 1, rc.w))) {
                     atomicAdd(&s_c[w][r], 1u);
-                    if (ntr <= 64u) atomicOr(&s_m[w][r][local >> 5], 1u << (local & 31u));
+                    if (kr.y & 0x80000000u) atomicOr(&s_m[w][r][local >> 5], 1u << (local & 31u));
                 }
             }
         }
@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(kRadixBins) k_digit_starts(uint32_t *__restric
 // order, and written out so that each digit's run of the block goes to consecutive addresses.
 // The values wait in shared memory in input order meanwhile (registers only for keys and
 // ranks: 5 CTAs per SM).
+template <int BITS>
 __global__ void __launch_bounds__(kRadixThreads, 5)
 k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 const uint32_t *n_dev, int64_t n_cap, int shift, uint32_t mask,
@@ -378,7 +379,7 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
         const uint32_t d = (kr[r] >> shift) & mask;
         uint32_t peers = __ballot_sync(full, valid);
 #pragma unroll
-        for (int b = 0; b < 8; b++) {
+        for (int b = 0; b < BITS; b++) {  // one ballot per bit of the digit
             const uint32_t bal = __ballot_sync(full, (d >> b) & 1u);
             peers &= bal ^ (((d >> b) & 1u) - 1u);   // bal where the bit is set, ~bal where not
         }
@@ -464,6 +465,9 @@ k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ blo
     constexpr int NW = kScanThreads / 32;
     __shared__ uint64_t s_wtot[NW];
     __shared__ int s_bad;
+    // the fields of the 32 records of a group, for the lanes that emit their keys
+    __shared__ uint4 s_oa[NW][32];   // kept-tile mask lo, hi, nx, rcp(nx) bits
+    __shared__ uint4 s_ob[NW][32];   // tx0 | ty0 << 16, gx | gy << 16, tile offset, record
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (int64_t)*K_dev > key_cap) atomicOr(status, kStatusCapacity);
@@ -575,6 +579,12 @@ k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ blo
             }
         }
         const uint32_t lim = (int64_t)total < key_cap - off ? total : (uint32_t)(key_cap - off);
+        // rects of more than 64 tiles were emitted above: their keys are skipped below by a mask
+        // of 0 (select_bit is never reached for them: p - excl < cnt only for small rects)
+        s_oa[w][lane] = make_uint4(big ? 0u : m.x, big ? 0u : m.y, (uint32_t)nx, __float_as_uint(rcp));
+        s_ob[w][lane] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)gx | ((uint32_t)gy << 16),
+                                   (uint32_t)toff | (big ? 0x80000000u : 0u), rec);
+        __syncwarp();
         for (uint32_t p0 = 0; p0 < lim; p0 += 32) {
             const uint32_t p = p0 + (uint32_t)lane;
             int o = 0;
@@ -582,24 +592,21 @@ k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ blo
             for (int step = 16; step >= 1; step >>= 1)
                 if (__shfl_sync(full, excl, o + step) <= p) o += step;
             const uint32_t eo = __shfl_sync(full, excl, o);
-            const uint32_t mlo = __shfl_sync(full, m.x, o), mhi = __shfl_sync(full, m.y, o);
-            const uint32_t nxo = (uint32_t)__shfl_sync(full, nx, o);
-            const float rcpo = __shfl_sync(full, rcp, o);
-            const int txo = __shfl_sync(full, tx0, o), tyo = __shfl_sync(full, ty0, o);
-            const int gxo = __shfl_sync(full, gx, o), gyo = __shfl_sync(full, gy, o);
-            const int toffo = __shfl_sync(full, toff, o);
-            const uint32_t reco = __shfl_sync(full, rec, o);
-            const bool bigo = __shfl_sync(full, big ? 1 : 0, o) != 0;
             const int64_t gp = off + p;
-            if (p < total && !bigo && gp < key_cap) {
-                uint32_t row, col;
-                divmod_small((uint32_t)select_bit(mlo, mhi, p - eo), nxo, rcpo, row, col);
-                const int tx = txo + (int)col, ty = tyo + (int)row;
-                const bool ok = tx < gxo && ty < gyo;
-                tile_keys[gp] = ok ? (uint32_t)(toffo + ty * gxo + tx) : 0xffffffffu;
-                tile_vals[gp] = reco;
+            if (p < total && gp < key_cap) {
+                const uint4 oa = s_oa[w][o], ob = s_ob[w][o];
+                if (!(ob.z & 0x80000000u)) {
+                    uint32_t row, col;
+                    divmod_small((uint32_t)select_bit(oa.x, oa.y, p - eo), oa.z, __uint_as_float(oa.w), row, col);
+                    const int tx = (int)(ob.x & 0xFFFFu) + (int)col, ty = (int)(ob.x >> 16) + (int)row;
+                    const int gxo = (int)(ob.y & 0xFFFFu), gyo = (int)(ob.y >> 16);
+                    const bool ok = tx < gxo && ty < gyo;
+                    tile_keys[gp] = ok ? (uint32_t)((int)ob.z + ty * gxo + tx) : 0xffffffffu;
+                    tile_vals[gp] = ob.w;
+                }
             }
         }
+        __syncwarp();  // s_oa / s_ob are rewritten by the next group
         off += total;
     }
 }
@@ -682,9 +689,16 @@ void radix_sort_pairs(uint32_t *&keys, uint32_t *&vals, uint32_t *keys_alt, uint
         count_launch();
         k_digit_starts<<<1, kRadixBins, 0, st>>>(hist, nb);
         count_launch();
-        k_radix_scatter<<<(unsigned)nb, kRadixThreads, 0, st>>>(keys, (first && index_vals) ? nullptr : vals,
-                                                                n_dev, n_cap, bit, mask, hist, nb, keys_alt,
-                                                                vals_alt);
+        const uint32_t *vin = (first && index_vals) ? nullptr : vals;
+        if (bits == 8)
+            k_radix_scatter<8><<<(unsigned)nb, kRadixThreads, 0, st>>>(keys, vin, n_dev, n_cap, bit, mask, hist, nb,
+                                                                       keys_alt, vals_alt);
+        else if (bits == 7)
+            k_radix_scatter<7><<<(unsigned)nb, kRadixThreads, 0, st>>>(keys, vin, n_dev, n_cap, bit, mask, hist, nb,
+                                                                       keys_alt, vals_alt);
+        else
+            k_radix_scatter<6><<<(unsigned)nb, kRadixThreads, 0, st>>>(keys, vin, n_dev, n_cap, bit, mask, hist, nb,
+                                                                       keys_alt, vals_alt);
         first = false;
         uint32_t *tk = keys, *tv = vals;
         keys = keys_alt;
