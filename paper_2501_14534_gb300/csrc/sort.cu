@@ -465,9 +465,6 @@ k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ blo
     constexpr int NW = kScanThreads / 32;
     __shared__ uint64_t s_wtot[NW];
     __shared__ int s_bad;
-    // the fields of the 32 records of a group, for the lanes that emit their keys
-    __shared__ uint4 s_oa[NW][32];   // kept-tile mask lo, hi, nx, rcp(nx) bits
-    __shared__ uint4 s_ob[NW][32];   // tx0 | ty0 << 16, gx | gy << 16, tile offset, record
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (int64_t)*K_dev > key_cap) atomicOr(status, kStatusCapacity);
@@ -579,12 +576,6 @@ k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ blo
             }
         }
         const uint32_t lim = (int64_t)total < key_cap - off ? total : (uint32_t)(key_cap - off);
-        // rects of more than 64 tiles were emitted above: their keys are skipped below by a mask
-        // of 0 (select_bit is never reached for them: p - excl < cnt only for small rects)
-        s_oa[w][lane] = make_uint4(big ? 0u : m.x, big ? 0u : m.y, (uint32_t)nx, __float_as_uint(rcp));
-        s_ob[w][lane] = make_uint4((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)gx | ((uint32_t)gy << 16),
-                                   (uint32_t)toff | (big ? 0x80000000u : 0u), rec);
-        __syncwarp();
         for (uint32_t p0 = 0; p0 < lim; p0 += 32) {
             const uint32_t p = p0 + (uint32_t)lane;
             int o = 0;
@@ -592,21 +583,24 @@ k_emit(const uint32_t *__restrict__ sorted_ids, const uint32_t *__restrict__ blo
             for (int step = 16; step >= 1; step >>= 1)
                 if (__shfl_sync(full, excl, o + step) <= p) o += step;
             const uint32_t eo = __shfl_sync(full, excl, o);
+            const uint32_t mlo = __shfl_sync(full, m.x, o), mhi = __shfl_sync(full, m.y, o);
+            const uint32_t nxo = (uint32_t)__shfl_sync(full, nx, o);
+            const float rcpo = __shfl_sync(full, rcp, o);
+            const int txo = __shfl_sync(full, tx0, o), tyo = __shfl_sync(full, ty0, o);
+            const int gxo = __shfl_sync(full, gx, o), gyo = __shfl_sync(full, gy, o);
+            const int toffo = __shfl_sync(full, toff, o);
+            const uint32_t reco = __shfl_sync(full, rec, o);
+            const bool bigo = __shfl_sync(full, big ? 1 : 0, o) != 0;
             const int64_t gp = off + p;
-            if (p < total && gp < key_cap) {
-                const uint4 oa = s_oa[w][o], ob = s_ob[w][o];
-                if (!(ob.z & 0x80000000u)) {
-                    uint32_t row, col;
-                    divmod_small((uint32_t)select_bit(oa.x, oa.y, p - eo), oa.z, __uint_as_float(oa.w), row, col);
-                    const int tx = (int)(ob.x & 0xFFFFu) + (int)col, ty = (int)(ob.x >> 16) + (int)row;
-                    const int gxo = (int)(ob.y & 0xFFFFu), gyo = (int)(ob.y >> 16);
-                    const bool ok = tx < gxo && ty < gyo;
-                    tile_keys[gp] = ok ? (uint32_t)((int)ob.z + ty * gxo + tx) : 0xffffffffu;
-                    tile_vals[gp] = ob.w;
-                }
+            if (p < total && !bigo && gp < key_cap) {
+                uint32_t row, col;
+                divmod_small((uint32_t)select_bit(mlo, mhi, p - eo), nxo, rcpo, row, col);
+                const int tx = txo + (int)col, ty = tyo + (int)row;
+                const bool ok = tx < gxo && ty < gyo;
+                tile_keys[gp] = ok ? (uint32_t)(toffo + ty * gxo + tx) : 0xffffffffu;
+                tile_vals[gp] = reco;
             }
         }
-        __syncwarp();  // s_oa / s_ob are rewritten by the next group
         off += total;
     }
 }
