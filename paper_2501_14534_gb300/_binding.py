@@ -116,6 +116,7 @@ SIGNATURES = {
                                            _statp, _vp, C.c_uint32, _vp]),
     "tgs_train_step_batched_host": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _pp, _gradp, _statp, _vp,
                                                 C.c_uint32, _vp]),
+    "tgs_render_batched": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _outp, C.c_uint32, _vp]),
     "tgs_autotune": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _pp, C.c_char_p, _vp]),
     "tgs_preprocess": (C.c_int32, [_ctx_p, _gp, _camp, C.c_int32, _vp, _vp, _vp]),
     "tgs_bin": (C.c_int32, [_ctx_p, _vp, _vp, C.c_int64, _camp, C.c_int32, _vp, _vp, _vp,

@@ -914,7 +914,7 @@ tgs_status tgs_plan(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, 
     CamBatch cb;
     GaussPtrs gp;
     TGS_TRY(make_batch(c->cfg, cams, V, cb));
-    TGS_TRY(make_gauss(c->cfg, g, gp));
+    TGS_TRY(make_gauss(c->cfg, g, gp, true));  // FP16 storage plans the render path
     const int64_t nt = g->n * V;
     TGS_TRY(ensure_records(c, nt, st));
     launch_preprocess(gp, cb, as<float4>(c->splats), as<int32_t>(c->radii), nullptr,
@@ -1203,6 +1203,89 @@ tgs_status tgs_train_step_batched_host(tgs_ctx *c, const tgs_gaussians *gh, cons
     if (s != TGS_OK) return s;
     if (loss_host) TGS_CHECK(cudaMemcpyAsync(loss_host, loss_dev, sizeof(float), cudaMemcpyDeviceToHost, st));
     return last_error();
+}
+
+// The body of a batched render; issues only asynchronous work (capturable).
+static tgs_status render_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPtrs &gp, const CamBatch &cb,
+                              const tgs_view_out *outs, int V, cudaStream_t st) {
+    const int64_t n = g->n, nt = n * V;
+    const int64_t cap = c->cfg.key_capacity;
+    const int64_t launches0 = g_launches;
+    launch_preprocess(gp, cb, as<float4>(c->splats), as<int32_t>(c->radii), nullptr, as<uint32_t>(c->dbits),
+                      nullptr, st);
+    uint32_t *sorted = nullptr;
+    bin_front(c, nt, &sorted, st);
+    uint32_t *ids = bin_back(c, nt, n, sorted, cb, cap, st);
+    PixPtrs px = pix_for(outs, V, nullptr);
+    launch_blend_forward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
+                         c->cfg.bg, st);
+    c->kernels_per_step = g_launches - launches0;
+    return last_error();
+}
+
+tgs_status tgs_render_batched(tgs_ctx *c, const tgs_gaussians *g, const tgs_camera *cams, int32_t V,
+                              const tgs_view_out *outs, uint32_t flags, tgs_stream stream) {
+    if (!c || !cams || !outs || V <= 0 || V > kMaxViews) return TGS_ERR_INVALID_ARG;
+    for (int v = 0; v < V; v++)
+        if (!outs[v].image) return TGS_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    CamBatch cb;
+    GaussPtrs gp;
+    TGS_TRY(make_batch(c->cfg, cams, V, cb));
+    TGS_TRY(make_gauss(c->cfg, g, gp, true));
+    if (c->cfg.key_capacity <= 0) {
+        if (capturing(st)) return TGS_ERR_CAPACITY;
+        TGS_TRY(tgs_plan(c, g, cams, V, 1.25, nullptr));
+        TGS_CHECK(cudaDeviceSynchronize());
+    }
+    TGS_TRY(ensure_records(c, g->n * V, st));
+    TGS_TRY(ensure_keys(c, c->cfg.key_capacity, cb.total_tiles, st));
+    c->state_valid = false;
+    if (!(flags & TGS_USE_GRAPH) || st == nullptr || capturing(st)) return render_body(c, g, gp, cb, outs, V, st);
+    std::vector<unsigned char> key;
+    auto put = [&key](const void *p, size_t n) {
+        const unsigned char *b = (const unsigned char *)p;
+        key.insert(key.end(), b, b + n);
+    };
+    const char tag[] = "render";
+    put(tag, sizeof tag);
+    put(g, sizeof *g);
+    put(cams, sizeof(tgs_camera) * V);
+    put(&V, sizeof V);
+    put(outs, sizeof(tgs_view_out) * V);
+    put(&c->cfg, sizeof c->cfg);
+    void *arena[] = {c->splats.p, c->tk0.p, c->hist.p};
+    put(arena, sizeof arena);
+    tgs_ctx::Graph *hit = nullptr;
+    for (auto &gr : c->graphs)
+        if (gr.key == key) hit = &gr;
+    if (!hit) {
+        constexpr size_t kMaxGraphs = 4;
+        if (c->graphs.size() >= kMaxGraphs) {
+            auto lru = std::min_element(c->graphs.begin(), c->graphs.end(),
+                                        [](const tgs_ctx::Graph &a, const tgs_ctx::Graph &b) { return a.used < b.used; });
+            cudaGraphExecDestroy(lru->exec);
+            c->graphs.erase(lru);
+        }
+        cudaGraph_t graph = nullptr;
+        TGS_CHECK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        tgs_status s = render_body(c, g, gp, cb, outs, V, st);
+        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (s != TGS_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        TGS_CHECK(e);
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        TGS_CHECK(e);
+        c->graphs.push_back(tgs_ctx::Graph{key, exec, 0});
+        hit = &c->graphs.back();
+    }
+    hit->used = ++c->graph_clock;
+    TGS_CHECK(cudaGraphLaunch(hit->exec, st));
+    return TGS_OK;
 }
 
 tgs_status tgs_set_profiling(tgs_ctx *c, int32_t on) {

@@ -387,6 +387,17 @@ class Rasterizer:
             C.byref(self._grad_struct(grads)), C.byref(self._stats_struct(stats)), _p(loss_host), flags,
             _stream()), "tgs_train_step_batched_host")
 
+    def render_batched(self, g: Gaussians, cams, outs=None, want_state=False, graph=False, cams_struct=None):
+        """Forward-only render of the views through the batched machinery (tgs_render_batched):
+        no host synchronisation once the key capacity is planned (plan)."""
+        outs = outs or self._alloc_views(cams, g.n, want_state)
+        for d in outs:
+            assert "radii" not in d
+        camarr = cams_struct if cams_struct is not None else cameras_array(cams)
+        B.check(B.lib.tgs_render_batched(self._h, C.byref(g.struct()), camarr, len(camarr), self._out_structs(outs),
+                                         B.TGS_USE_GRAPH if graph else 0, _stream()), "tgs_render_batched")
+        return outs
+
     # ---- FP16 storage ----
 
     @staticmethod

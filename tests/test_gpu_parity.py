@@ -558,3 +558,32 @@ def test_non_finite_parameters_are_culled(R):
     ref = oracle.render(scene, cams[0], st, margins=True)
     m, _ = image_compare(img, ref["image"], ref["margin"])
     assert m <= IMAGE_ATOL
+
+
+@pytest.mark.parametrize("tile,ppt", [(16, 1), (32, 2)])
+def test_batched_render_equals_plain_forward(R, tile, ppt):
+    """tgs_render_batched (all views in one preprocess, binning and forward launch, no host
+    synchronisation) renders the images, transmittances and last contributors of the plain
+    path bit for bit, on graph replays too, and from FP16 storage."""
+    scene, cams, targets, st = batched_case(5000)
+    st.tile = tile
+    rast = make_rast(R, st, ppt=ppt)
+    g = gpu_scene(R, scene)
+    ref = make_rast(R, st, ppt=ppt).forward(g, cams)
+    rast.plan(g, cams)
+    s = torch.cuda.Stream()
+    outs = rast._alloc_views(cams, g.n, want_state=True)
+    with torch.cuda.stream(s):
+        for _ in range(3):   # direct, capture, replay
+            rast.render_batched(g, cams, outs=outs, graph=True)
+    s.synchronize()
+    rast.poll()
+    for a, b in zip(outs, ref):
+        for k in ("image", "T_final", "last"):
+            assert torch.equal(a[k], b[k]), k
+    gh = R.Rasterizer.to_half(g)
+    href = make_rast(R, st, ppt=ppt).forward(gh, cams)
+    hout = rast.render_batched(gh, cams)
+    rast.poll()
+    for a, b in zip(hout, href):
+        assert torch.equal(a["image"], b["image"])
