@@ -60,6 +60,13 @@ def image_compare(gpu, ref, margin):
     return m, 1.0 - clear.mean()
 
 
+def mismatch_fraction(gpu, ref):
+    """Fraction of all pixels (margin cases included) where some channel differs by more than
+    IMAGE_ATOL: the pixels where a decision actually fell the other way."""
+    diff = np.abs(np.asarray(gpu, np.float64) - ref).max(axis=0)
+    return float((diff > IMAGE_ATOL).mean())
+
+
 def elem_err(a, b, rtol=GRAD_RTOL, stol=GRAD_RTOL):
     """Largest |a - b| / (rtol |b| + stol max|b|) over the elements (<= 1 passes); b is the
     reference. An all-zero reference requires an all-zero a."""
