@@ -31,7 +31,7 @@ def R():
 EXCL_E2E = 0.04
 # Largest fraction of all pixels whose value differs by more than IMAGE_ATOL end to end (a
 # decision that actually fell the other way in float32).
-MISMATCH_E2E = 5e-3
+MISMATCH_E2E = 1e-3
 
 
 def settings_for(tile=16, eps=(0.05, 0.1), support=0, bg=(0.0, 0.0, 0.0)):
