@@ -46,19 +46,19 @@ OPS_BWD = 51         # evaluation again + T recovery, colour-behind update, dL/d
 # special-function operations per contributing pair: ex2 in the forward, ex2 and the
 # reciprocal of the T recovery in the backward
 SFU_PER_CONTRIB = 3
-# DRAM bytes (read + write) of one fused-blend launch on the default workload at tile 32,
-# 2 px/thread, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum; the command
-# is in profiles/k_fused_l1_300k_8x1280x832_tile32_ppt2.md). Reported only while the kernel's
-# sources, its launcher included, are the ones measured (their sha256 below), else null.
-FUSED_TRAFFIC = {"bytes": 718117632 + 96742144, "tile": 32, "ppt": 2,
+# DRAM bytes (read + write) of one fused-blend launch (k_fused_warp) on the default workload at
+# tile 32, 2 px/thread, batch 1, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum;
+# the command is in profiles/k_fused_warp_300k_8x1280x832_tile32_ppt2.md). Reported only while the
+# kernel's sources, its launcher included, are the ones measured (their sha256 below), else null.
+FUSED_TRAFFIC = {"bytes": 626542336 + 86510080, "tile": 32, "ppt": 2, "batch": 1,
                  "sources": ("fused.cu", "blend_common.cuh", "tgs_internal.cuh"),
-                 "sha256": "b0e54ad0c18a687313044b7bc3678c7eae320724769e187456c734db93bcc472"}
+                 "sha256": "b4001cc3c606dd88c65c4bd3954bd57a6494f28a7970f5406ed7ed7b6beaca08"}
 
 
 def fused_traffic(cfg, n, views):
     import hashlib
     t = FUSED_TRAFFIC
-    if (cfg.tile, cfg.ppt, n, views) != (t["tile"], t["ppt"], N_GAUSS, N_VIEWS):
+    if (cfg.tile, cfg.ppt, max(cfg.batch, 1), n, views) != (t["tile"], t["ppt"], t["batch"], N_GAUSS, N_VIEWS):
         return None
     h = hashlib.sha256()
     for f in t["sources"]:

@@ -1,10 +1,10 @@
 // Front-to-back alpha blending (Eq. 2 of the paper) and its backward, one CTA per (view,
-// tile). The per-tile work lives in blend_common.cuh (shared with the fused kernel): the
+// tile), or at 32 x 32 tiles and 2 pixels per thread one warp per 8 x 8 block (blend_warp.cuh). The per-tile work lives in blend_common.cuh (shared with the fused kernel): the
 // tile's depth-sorted list is streamed through shared memory in batches of one splat per
 // thread; the forward stops a pixel before the fragment that would bring its transmittance
 // below 1e-4; the backward walks the list in reverse from each pixel's last contributor and
 // scatters per-splat gradients with one transposed warp reduction and one atomic per value.
-#include "blend_common.cuh"
+#include "blend_warp.cuh"
 
 namespace tgs {
 namespace {
@@ -81,6 +81,78 @@ k_blend_bwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
     tile_backward<TILE, PPT>(sm, splats, ids, ranges[gt], P, in, bg0, bg1, bg2, sgrads);
 }
 
+// Warp items at 32 x 32 tiles and 2 pixels per thread (blend_warp.cuh): CTA b takes 4 of the
+// 16 blocks of tile b / 4, one per warp, so that the warps reading one tile's records share L1.
+constexpr int kWarpCta = 128;
+
+template <bool HITS>
+__global__ void __launch_bounds__(kWarpCta)
+k_blend_fwd_warp(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
+                 const uint2 *__restrict__ ranges, const __grid_constant__ CamBatch cb,
+                 const __grid_constant__ PixPtrs px, float bg0, float bg1, float bg2,
+                 uint32_t *__restrict__ hits, uint32_t n_gauss) {
+    __shared__ WarpSlots s_slots[kWarpCta / 32];
+    const int w = threadIdx.x >> 5;
+    const int gt = blockIdx.x / (kWBlocks / (kWarpCta / 32));
+    const int blk = (blockIdx.x % (kWBlocks / (kWarpCta / 32))) * (kWarpCta / 32) + w;
+    const int v = view_of_tile(cb, gt);
+    const DevCam &cam = cb.c[v];
+    WarpPixels P;
+    P.init(cam, gt - cam.tile_offset, blk);
+    float T[2], Cr[2], Cg[2], Cb[2];
+    int last[2], exam[2];
+    warp_forward<HITS, true>(s_slots[w].f, splats, ids, ranges[gt], P, T, Cr, Cg, Cb, last, exam, hits,
+                             (uint32_t)v * n_gauss);
+    const int HW = cam.W * cam.H;
+    float *img = px.image[v];
+    float *Tf = px.T_final[v];
+    int32_t *ls = px.last[v];
+    int32_t *ex = px.n_exam[v];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        if (!(k == 0 ? P.in0 : P.in1)) continue;
+        const int pix = (k == 0 ? P.y0 : P.y1) * cam.W + P.x;
+        if (img) {
+            img[pix] = Cr[k] + T[k] * bg0;
+            img[HW + pix] = Cg[k] + T[k] * bg1;
+            img[2 * HW + pix] = Cb[k] + T[k] * bg2;
+        }
+        if (Tf) Tf[pix] = T[k];
+        if (ls) ls[pix] = last[k];
+        if (ex) ex[pix] = exam[k];
+    }
+}
+
+__global__ void __launch_bounds__(kWarpCta)
+k_blend_bwd_warp(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
+                 const uint2 *__restrict__ ranges, const __grid_constant__ CamBatch cb,
+                 const __grid_constant__ PixPtrs px, float bg0, float bg1, float bg2,
+                 float *__restrict__ sgrads) {
+    __shared__ WarpSlots s_slots[kWarpCta / 32];
+    const int w = threadIdx.x >> 5;
+    const int gt = blockIdx.x / (kWBlocks / (kWarpCta / 32));
+    const int blk = (blockIdx.x % (kWBlocks / (kWarpCta / 32))) * (kWarpCta / 32) + w;
+    const int v = view_of_tile(cb, gt);
+    const DevCam &cam = cb.c[v];
+    WarpPixels P;
+    P.init(cam, gt - cam.tile_offset, blk);
+    const int HW = cam.W * cam.H;
+    const float *d = px.dL[v];
+    int last[2];
+    float Tf[2], dR[2], dG[2], dB[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const bool ok = k == 0 ? P.in0 : P.in1;
+        const int pix = (k == 0 ? P.y0 : P.y1) * cam.W + P.x;
+        last[k] = ok ? px.last[v][pix] : 0;
+        Tf[k] = ok ? px.T_final[v][pix] : 1.f;
+        dR[k] = ok ? d[pix] : 0.f;
+        dG[k] = ok ? d[HW + pix] : 0.f;
+        dB[k] = ok ? d[2 * HW + pix] : 0.f;
+    }
+    warp_backward<false>(s_slots[w].b, splats, ids, ranges[gt], P, last, Tf, dR, dG, dB, bg0, bg1, bg2, sgrads);
+}
+
 __global__ void k_l1(const float *__restrict__ img, const float *__restrict__ tgt, int64_t count,
                      float scale, float *__restrict__ loss, float *__restrict__ grad) {
     float acc = 0.f;
@@ -108,6 +180,12 @@ void fwd_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, 
     for (int v = 0; v < cb.V; v++) count = count || px.n_contrib[v] || px.n_eval[v];
     const uint32_t n = (uint32_t)n_gauss;
     count_launch();
+    if (TILE == 32 && PPT == 2 && !count) {
+        const unsigned grid = (unsigned)cb.total_tiles * (kWBlocks / (kWarpCta / 32));
+        if (hits) k_blend_fwd_warp<true><<<grid, kWarpCta, 0, st>>>(splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], hits, n);
+        else k_blend_fwd_warp<false><<<grid, kWarpCta, 0, st>>>(splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], hits, n);
+        return;
+    }
 #define TGS_FWD(C, HT)                                                                                 \
     k_blend_fwd<TILE, PPT, C, HT><<<cb.total_tiles, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, cb, px, \
                                                                                bg[0], bg[1], bg[2], hits, n)
@@ -122,6 +200,11 @@ template <int TILE, int PPT>
 void bwd_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const CamBatch &cb,
                 const PixPtrs &px, const float *bg, float *sg, cudaStream_t st) {
     count_launch();
+    if (TILE == 32 && PPT == 2) {
+        const unsigned grid = (unsigned)cb.total_tiles * (kWBlocks / (kWarpCta / 32));
+        k_blend_bwd_warp<<<grid, kWarpCta, 0, st>>>(splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], sg);
+        return;
+    }
     k_blend_bwd<TILE, PPT><<<cb.total_tiles, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, cb, px,
                                                                          bg[0], bg[1], bg[2], sg);
 }
