@@ -36,10 +36,12 @@ def test_clock_summary_median_and_reasons(bench):
 
 def test_traffic_reported_only_for_the_measured_sources_and_shape(bench, monkeypatch):
     t = bench.FUSED_TRAFFIC
-    cfg = types.SimpleNamespace(tile=t["tile"], ppt=t["ppt"])
+    cfg = types.SimpleNamespace(tile=t["tile"], ppt=t["ppt"], batch=t["batch"])
     got = bench.fused_traffic(cfg, bench.N_GAUSS, bench.N_VIEWS)
     assert got in (t["bytes"], None)          # None once a hashed source has changed
-    assert bench.fused_traffic(types.SimpleNamespace(tile=16, ppt=1), bench.N_GAUSS, bench.N_VIEWS) is None
+    assert bench.fused_traffic(types.SimpleNamespace(tile=16, ppt=1, batch=1), bench.N_GAUSS, bench.N_VIEWS) is None
+    # batch 2 runs the CTA kernel, not the one measured
+    assert bench.fused_traffic(types.SimpleNamespace(tile=32, ppt=2, batch=2), bench.N_GAUSS, bench.N_VIEWS) is None
     assert bench.fused_traffic(cfg, 300_000, 8) is None
     monkeypatch.setitem(bench.FUSED_TRAFFIC, "sha256", "0" * 64)
     assert bench.fused_traffic(cfg, bench.N_GAUSS, bench.N_VIEWS) is None
