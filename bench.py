@@ -50,9 +50,9 @@ SFU_PER_CONTRIB = 3
 # tile 32, 2 px/thread, batch 1, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum;
 # the command is in profiles/k_fused_warp_300k_8x1280x832_tile32_ppt2.md). Reported only while the
 # kernel's sources, its launcher included, are the ones measured (their sha256 below), else null.
-FUSED_TRAFFIC = {"bytes": 626542336 + 86510080, "tile": 32, "ppt": 2, "batch": 1,
-                 "sources": ("fused.cu", "blend_common.cuh", "tgs_internal.cuh"),
-                 "sha256": "b4001cc3c606dd88c65c4bd3954bd57a6494f28a7970f5406ed7ed7b6beaca08"}
+FUSED_TRAFFIC = {"bytes": 633680384 + 88229632, "tile": 32, "ppt": 2, "batch": 1,
+                 "sources": ("fused.cu", "blend_warp.cuh", "blend_common.cuh", "tgs_internal.cuh"),
+                 "sha256": "383b85931ee3c0110c8a5e606c95e480f25b10e85a223c02769f859004c81edf"}
 
 
 def fused_traffic(cfg, n, views):

@@ -545,13 +545,18 @@ __global__ void __launch_bounds__(kBwdThreads) k_preprocess_bwd_colour(GaussPtrs
             const float *r = rows + kRest * lane + 3 * (k - 1);
             sh.f[k] = (g.sh_rest && s.deg >= band_of(k)) ? make_float3(r[0], r[1], r[2]) : make_float3(0.f, 0.f, 0.f);
         }
-        float3 nrgb = make_float3(0.f, 0.f, 0.f);
+        float3 nrgb = make_float3(0.f, 0.f, 0.f), nrgb2 = nrgb;
         if (vis & 1ull) nrgb = make_float3(rec[12 * i + 6], rec[12 * i + 7], rec[12 * i + 8]);
+        if (cb.V > 1 && (vis & 2ull)) {
+            const int64_t rn = 12 * ((int64_t)n + i);
+            nrgb2 = make_float3(rec[rn + 6], rec[rn + 7], rec[rn + 8]);
+        }
         for (int v = 0; v < cb.V; v++) {
             const float3 g_rgb = nrgb;
-            if (v + 1 < cb.V && ((vis >> (v + 1)) & 1ull)) {
-                const int64_t rn = 12 * ((int64_t)(v + 1) * n + i);
-                nrgb = make_float3(rec[rn + 6], rec[rn + 7], rec[rn + 8]);
+            nrgb = nrgb2;
+            if (v + 2 < cb.V && ((vis >> (v + 2)) & 1ull)) {
+                const int64_t rn = 12 * ((int64_t)(v + 2) * n + i);
+                nrgb2 = make_float3(rec[rn + 6], rec[rn + 7], rec[rn + 8]);
             }
             if (!((vis >> v) & 1ull)) continue;
             const DevCam &c = cb.c[v];
@@ -649,17 +654,23 @@ __global__ void __launch_bounds__(kBwdThreads, 5) k_preprocess_bwd_geom(GaussPtr
                 st_max = max(st_max, rad);
             }
         }
-        float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na;
+        float4 na = make_float4(0.f, 0.f, 0.f, 0.f), nb = na, na2 = na, nb2 = na;
         if (vis & 1ull) {
             na = sgrads[3 * i];
             nb = sgrads[3 * i + 1];
         }
+        if (cb.V > 1 && (vis & 2ull)) {
+            na2 = sgrads[3 * (n + i)];
+            nb2 = sgrads[3 * (n + i) + 1];
+        }
         for (int v = 0; v < cb.V; v++) {
             const float4 ga = na, gb4 = nb;
-            if (v + 1 < cb.V && ((vis >> (v + 1)) & 1ull)) {
-                const int64_t rn = (int64_t)(v + 1) * n + i;
-                na = sgrads[3 * rn];
-                nb = sgrads[3 * rn + 1];
+            na = na2;
+            nb = nb2;
+            if (v + 2 < cb.V && ((vis >> (v + 2)) & 1ull)) {
+                const int64_t rn = (int64_t)(v + 2) * n + i;
+                na2 = sgrads[3 * rn];
+                nb2 = sgrads[3 * rn + 1];
             }
             if (!((vis >> v) & 1ull)) continue;
             const DevCam &c = cb.c[v];
