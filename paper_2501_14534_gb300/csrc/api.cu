@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -101,10 +102,15 @@ bool capturing(cudaStream_t st) {
 }
 
 // Grows a scratch buffer; never inside stream capture.
+// Bumped on every reallocation of a device buffer: part of every captured graph's key, so that
+// no graph holding a freed buffer's address is replayed (it no longer matches and ages out).
+std::atomic<uint64_t> g_arena_gen{0};
+
 tgs_status ensure(Buf &b, size_t bytes, cudaStream_t st) {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return TGS_OK;
     if (capturing(st)) return TGS_ERR_CAPACITY;
+    g_arena_gen.fetch_add(1);
     size_t nb = bytes + bytes / 4;
     if (b.p) {
         cudaStreamSynchronize(st);
@@ -977,9 +983,21 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
     if (loss_out) TGS_CHECK(cudaMemsetAsync(loss_out, 0, sizeof(float), st));
     int stage = 2;
     if (split) {
+        // at tile 32 / 2 px per thread the warp-item kernels take their items heaviest first
+        const bool warp_items = c->cfg.tile == 32 && c->cfg.ppt == 2;
+        uint32_t *order = nullptr;
+        int *ctr = reinterpret_cast<int *>(as<uint32_t>(c->counts) + 2);  // forward, backward
+        if (warp_items) {
+            mark(c, stage++, "item_order", st);
+            uint32_t *it = as<uint32_t>(c->items);
+            const size_t T = ((size_t)cb.total_tiles + 3) / 4 * 4;  // 16-byte aligned quarters
+            build_item_order(as<uint2>(c->ranges), cb.total_tiles, it, it + T, it + 2 * T, it + 3 * T, &order,
+                             as<uint32_t>(c->hist), as<uint32_t>(c->partials), st);
+            TGS_CHECK(cudaMemsetAsync(ctr, 0, 2 * sizeof(int), st));
+        }
         mark(c, stage++, "blend_forward", st);
         launch_blend_forward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
-                             c->cfg.bg, st, stats ? stats->hit_count : nullptr, n);
+                             c->cfg.bg, st, stats ? stats->hit_count : nullptr, n, order, order ? ctr : nullptr);
         if (flags & TGS_LOSS_DSSIM) {
             mark(c, stage++, "l1_dssim_loss", st);
             int W[kMaxViews], H[kMaxViews];
@@ -1002,7 +1020,7 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
         }
         mark(c, stage++, "blend_backward", st);
         launch_blend_backward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
-                              c->cfg.bg, as<float>(c->sgrads), st);
+                              c->cfg.bg, as<float>(c->sgrads), st, order, order ? ctr + 1 : nullptr);
     } else {
         mark(c, stage++, "item_order", st);
         uint32_t *it = as<uint32_t>(c->items);
@@ -1092,6 +1110,8 @@ tgs_status tgs_train_step_batched(tgs_ctx *c, const tgs_gaussians *g, const tgs_
     put(&c->cfg, sizeof c->cfg);
     void *arena[] = {c->splats.p, c->tk0.p, c->hist.p, c->images.p, c->pixstate.p};
     put(arena, sizeof arena);
+    const uint64_t gen = g_arena_gen.load();
+    put(&gen, sizeof gen);
     tgs_ctx::Graph *hit = nullptr;
     for (auto &gr : c->graphs)
         if (gr.key == key) hit = &gr;
@@ -1217,8 +1237,18 @@ static tgs_status render_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPtr
     bin_front(c, nt, &sorted, st);
     uint32_t *ids = bin_back(c, nt, n, sorted, cb, cap, st);
     PixPtrs px = pix_for(outs, V, nullptr);
+    // at tile 32 / 2 px per thread the warp-item kernel takes its items heaviest first
+    uint32_t *order = nullptr;
+    int *ctr = reinterpret_cast<int *>(as<uint32_t>(c->counts) + 2);
+    if (c->cfg.tile == 32 && c->cfg.ppt == 2) {
+        uint32_t *it = as<uint32_t>(c->items);
+        const size_t T = ((size_t)cb.total_tiles + 3) / 4 * 4;  // 16-byte aligned quarters
+        build_item_order(as<uint2>(c->ranges), cb.total_tiles, it, it + T, it + 2 * T, it + 3 * T, &order,
+                         as<uint32_t>(c->hist), as<uint32_t>(c->partials), st);
+        TGS_CHECK(cudaMemsetAsync(ctr, 0, sizeof(int), st));
+    }
     launch_blend_forward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
-                         c->cfg.bg, st);
+                         c->cfg.bg, st, nullptr, 0, order, order ? ctr : nullptr);
     c->kernels_per_step = g_launches - launches0;
     return last_error();
 }
@@ -1240,6 +1270,7 @@ tgs_status tgs_render_batched(tgs_ctx *c, const tgs_gaussians *g, const tgs_came
     }
     TGS_TRY(ensure_records(c, g->n * V, st));
     TGS_TRY(ensure_keys(c, c->cfg.key_capacity, cb.total_tiles, st));
+    TGS_TRY(ensure(c->items, sizeof(uint32_t) * 4 * (((size_t)std::max(cb.total_tiles, 1) + 3) / 4 * 4), st));
     c->state_valid = false;
     if (!(flags & TGS_USE_GRAPH) || st == nullptr || capturing(st)) return render_body(c, g, gp, cb, outs, V, st);
     std::vector<unsigned char> key;
@@ -1256,6 +1287,8 @@ tgs_status tgs_render_batched(tgs_ctx *c, const tgs_gaussians *g, const tgs_came
     put(&c->cfg, sizeof c->cfg);
     void *arena[] = {c->splats.p, c->tk0.p, c->hist.p};
     put(arena, sizeof arena);
+    const uint64_t gen = g_arena_gen.load();
+    put(&gen, sizeof gen);
     tgs_ctx::Graph *hit = nullptr;
     for (auto &gr : c->graphs)
         if (gr.key == key) hit = &gr;

@@ -4,6 +4,9 @@
 // thread; the forward stops a pixel before the fragment that would bring its transmittance
 // below 1e-4; the backward walks the list in reverse from each pixel's last contributor and
 // scatters per-splat gradients with one transposed warp reduction and one atomic per value.
+#include <algorithm>
+#include <mutex>
+
 #include "blend_warp.cuh"
 
 namespace tgs {
@@ -81,45 +84,67 @@ k_blend_bwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
     tile_backward<TILE, PPT>(sm, splats, ids, ranges[gt], P, in, bg0, bg1, bg2, sgrads);
 }
 
-// Warp items at 32 x 32 tiles and 2 pixels per thread (blend_warp.cuh): CTA b takes 4 of the
-// 16 blocks of tile b / 4, one per warp, so that the warps reading one tile's records share L1.
+// Warp items at 32 x 32 tiles and 2 pixels per thread (blend_warp.cuh). Without an item
+// order, CTA b takes 4 of the 16 blocks of tile b / 4, one per warp, so that the warps reading
+// one tile's records share L1. With one (order: tiles heaviest first, counter: zero before the
+// launch), a persistent grid takes (tile, block) items from the counter in that order.
 constexpr int kWarpCta = 128;
+
+// The next item of this warp: false when there is none.
+__device__ __forceinline__ bool next_warp_item(const uint32_t *__restrict__ order, int *__restrict__ counter,
+                                               int n_tiles, bool first, int &gt, int &blk) {
+    if (!counter) {  // one item per warp
+        if (!first) return false;
+        gt = blockIdx.x / (kWBlocks / (kWarpCta / 32));
+        blk = (blockIdx.x % (kWBlocks / (kWarpCta / 32))) * (kWarpCta / 32) + (threadIdx.x >> 5);
+        return true;
+    }
+    int it = 0;
+    if ((threadIdx.x & 31) == 0) it = atomicAdd(counter, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n_tiles * kWBlocks) return false;
+    gt = (int)order[it / kWBlocks];
+    blk = it % kWBlocks;
+    return true;
+}
 
 template <bool HITS>
 __global__ void __launch_bounds__(kWarpCta)
 k_blend_fwd_warp(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
                  const uint2 *__restrict__ ranges, const __grid_constant__ CamBatch cb,
                  const __grid_constant__ PixPtrs px, float bg0, float bg1, float bg2,
-                 uint32_t *__restrict__ hits, uint32_t n_gauss) {
+                 uint32_t *__restrict__ hits, uint32_t n_gauss, const uint32_t *__restrict__ order,
+                 int *__restrict__ counter) {
     __shared__ WarpSlots s_slots[kWarpCta / 32];
     const int w = threadIdx.x >> 5;
-    const int gt = blockIdx.x / (kWBlocks / (kWarpCta / 32));
-    const int blk = (blockIdx.x % (kWBlocks / (kWarpCta / 32))) * (kWarpCta / 32) + w;
-    const int v = view_of_tile(cb, gt);
-    const DevCam &cam = cb.c[v];
-    WarpPixels P;
-    P.init(cam, gt - cam.tile_offset, blk);
-    float T[2], Cr[2], Cg[2], Cb[2];
-    int last[2], exam[2];
-    warp_forward<HITS, true>(s_slots[w].f, splats, ids, ranges[gt], P, T, Cr, Cg, Cb, last, exam, hits,
-                             (uint32_t)v * n_gauss);
-    const int HW = cam.W * cam.H;
-    float *img = px.image[v];
-    float *Tf = px.T_final[v];
-    int32_t *ls = px.last[v];
-    int32_t *ex = px.n_exam[v];
+    int gt = 0, blk = 0;
+    for (bool first = true; next_warp_item(order, counter, cb.total_tiles, first, gt, blk); first = false) {
+        const int v = view_of_tile(cb, gt);
+        const DevCam &cam = cb.c[v];
+        WarpPixels P;
+        P.init(cam, gt - cam.tile_offset, blk);
+        float T[2], Cr[2], Cg[2], Cb[2];
+        int last[2], exam[2];
+        warp_forward<HITS, true>(s_slots[w].f, splats, ids, ranges[gt], P, T, Cr, Cg, Cb, last, exam, hits,
+                                 (uint32_t)v * n_gauss);
+        const int HW = cam.W * cam.H;
+        float *img = px.image[v];
+        float *Tf = px.T_final[v];
+        int32_t *ls = px.last[v];
+        int32_t *ex = px.n_exam[v];
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-        if (!(k == 0 ? P.in0 : P.in1)) continue;
-        const int pix = (k == 0 ? P.y0 : P.y1) * cam.W + P.x;
-        if (img) {
-            img[pix] = Cr[k] + T[k] * bg0;
-            img[HW + pix] = Cg[k] + T[k] * bg1;
-            img[2 * HW + pix] = Cb[k] + T[k] * bg2;
+        for (int k = 0; k < 2; k++) {
+            if (!(k == 0 ? P.in0 : P.in1)) continue;
+            const int pix = (k == 0 ? P.y0 : P.y1) * cam.W + P.x;
+            if (img) {
+                img[pix] = Cr[k] + T[k] * bg0;
+                img[HW + pix] = Cg[k] + T[k] * bg1;
+                img[2 * HW + pix] = Cb[k] + T[k] * bg2;
+            }
+            if (Tf) Tf[pix] = T[k];
+            if (ls) ls[pix] = last[k];
+            if (ex) ex[pix] = exam[k];
         }
-        if (Tf) Tf[pix] = T[k];
-        if (ls) ls[pix] = last[k];
-        if (ex) ex[pix] = exam[k];
     }
 }
 
@@ -127,30 +152,63 @@ __global__ void __launch_bounds__(kWarpCta)
 k_blend_bwd_warp(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
                  const uint2 *__restrict__ ranges, const __grid_constant__ CamBatch cb,
                  const __grid_constant__ PixPtrs px, float bg0, float bg1, float bg2,
-                 float *__restrict__ sgrads) {
+                 float *__restrict__ sgrads, const uint32_t *__restrict__ order, int *__restrict__ counter) {
     __shared__ WarpSlots s_slots[kWarpCta / 32];
     const int w = threadIdx.x >> 5;
-    const int gt = blockIdx.x / (kWBlocks / (kWarpCta / 32));
-    const int blk = (blockIdx.x % (kWBlocks / (kWarpCta / 32))) * (kWarpCta / 32) + w;
-    const int v = view_of_tile(cb, gt);
-    const DevCam &cam = cb.c[v];
-    WarpPixels P;
-    P.init(cam, gt - cam.tile_offset, blk);
-    const int HW = cam.W * cam.H;
-    const float *d = px.dL[v];
-    int last[2];
-    float Tf[2], dR[2], dG[2], dB[2];
+    int gt = 0, blk = 0;
+    for (bool first = true; next_warp_item(order, counter, cb.total_tiles, first, gt, blk); first = false) {
+        const int v = view_of_tile(cb, gt);
+        const DevCam &cam = cb.c[v];
+        WarpPixels P;
+        P.init(cam, gt - cam.tile_offset, blk);
+        const int HW = cam.W * cam.H;
+        const float *d = px.dL[v];
+        int last[2];
+        float Tf[2], dR[2], dG[2], dB[2];
 #pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const bool ok = k == 0 ? P.in0 : P.in1;
-        const int pix = (k == 0 ? P.y0 : P.y1) * cam.W + P.x;
-        last[k] = ok ? px.last[v][pix] : 0;
-        Tf[k] = ok ? px.T_final[v][pix] : 1.f;
-        dR[k] = ok ? d[pix] : 0.f;
-        dG[k] = ok ? d[HW + pix] : 0.f;
-        dB[k] = ok ? d[2 * HW + pix] : 0.f;
+        for (int k = 0; k < 2; k++) {
+            const bool ok = k == 0 ? P.in0 : P.in1;
+            const int pix = (k == 0 ? P.y0 : P.y1) * cam.W + P.x;
+            last[k] = ok ? px.last[v][pix] : 0;
+            Tf[k] = ok ? px.T_final[v][pix] : 1.f;
+            dR[k] = ok ? d[pix] : 0.f;
+            dG[k] = ok ? d[HW + pix] : 0.f;
+            dB[k] = ok ? d[2 * HW + pix] : 0.f;
+        }
+        warp_backward<false>(s_slots[w].b, splats, ids, ranges[gt], P, last, Tf, dR, dG, dB, bg0, bg1, bg2, sgrads);
     }
-    warp_backward<false>(s_slots[w].b, splats, ids, ranges[gt], P, last, Tf, dR, dG, dB, bg0, bg1, bg2, sgrads);
+}
+
+// Grid of a warp-item launch: one CTA per 4 blocks without a counter, else a persistent grid of
+// SMs x resident CTAs (found once per device and kernel), capped by the items.
+template <class K>
+unsigned warp_grid(K kernel, const CamBatch &cb, bool persistent) {
+    const unsigned one = (unsigned)cb.total_tiles * (kWBlocks / (kWarpCta / 32));
+    if (!persistent) return one;
+    constexpr int kDevices = 64;
+    static std::mutex mu;
+    static int grid_of[kDevices] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= kDevices || grid_of[dev] == 0) {
+        int sms = 1, b = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+            cudaGetLastError();
+            sms = 1;
+        }
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, kWarpCta, 0) != cudaSuccess) {
+            cudaGetLastError();
+            b = 1;
+        }
+        const int g = sms * (b < 1 ? 1 : b);
+        if (dev < 0 || dev >= kDevices) return std::min(one, (unsigned)g);
+        grid_of[dev] = g;
+    }
+    return std::min(one, (unsigned)grid_of[dev]);
 }
 
 __global__ void k_l1(const float *__restrict__ img, const float *__restrict__ tgt, int64_t count,
@@ -175,15 +233,21 @@ __global__ void k_l1(const float *__restrict__ img, const float *__restrict__ tg
 
 template <int TILE, int PPT>
 void fwd_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const CamBatch &cb,
-                const PixPtrs &px, const float *bg, uint32_t *hits, int64_t n_gauss, cudaStream_t st) {
+                const PixPtrs &px, const float *bg, uint32_t *hits, int64_t n_gauss, const uint32_t *order,
+                int *counter, cudaStream_t st) {
     bool count = false;
     for (int v = 0; v < cb.V; v++) count = count || px.n_contrib[v] || px.n_eval[v];
     const uint32_t n = (uint32_t)n_gauss;
     count_launch();
     if (TILE == 32 && PPT == 2 && !count) {
-        const unsigned grid = (unsigned)cb.total_tiles * (kWBlocks / (kWarpCta / 32));
-        if (hits) k_blend_fwd_warp<true><<<grid, kWarpCta, 0, st>>>(splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], hits, n);
-        else k_blend_fwd_warp<false><<<grid, kWarpCta, 0, st>>>(splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], hits, n);
+        const bool pers = order && counter;
+        if (!pers) order = nullptr, counter = nullptr;
+        if (hits)
+            k_blend_fwd_warp<true><<<warp_grid(k_blend_fwd_warp<true>, cb, pers), kWarpCta, 0, st>>>(
+                splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], hits, n, order, counter);
+        else
+            k_blend_fwd_warp<false><<<warp_grid(k_blend_fwd_warp<false>, cb, pers), kWarpCta, 0, st>>>(
+                splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], hits, n, order, counter);
         return;
     }
 #define TGS_FWD(C, HT)                                                                                 \
@@ -198,11 +262,14 @@ void fwd_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, 
 
 template <int TILE, int PPT>
 void bwd_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const CamBatch &cb,
-                const PixPtrs &px, const float *bg, float *sg, cudaStream_t st) {
+                const PixPtrs &px, const float *bg, float *sg, const uint32_t *order, int *counter,
+                cudaStream_t st) {
     count_launch();
     if (TILE == 32 && PPT == 2) {
-        const unsigned grid = (unsigned)cb.total_tiles * (kWBlocks / (kWarpCta / 32));
-        k_blend_bwd_warp<<<grid, kWarpCta, 0, st>>>(splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], sg);
+        const bool pers = order && counter;
+        if (!pers) order = nullptr, counter = nullptr;
+        k_blend_bwd_warp<<<warp_grid(k_blend_bwd_warp, cb, pers), kWarpCta, 0, st>>>(
+            splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], sg, order, counter);
         return;
     }
     k_blend_bwd<TILE, PPT><<<cb.total_tiles, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, cb, px,
@@ -232,16 +299,18 @@ int blend_supported(int tile, int ppt) {
 
 void launch_blend_forward(int tile, int ppt, const float4 *splats, const uint32_t *ids,
                           const uint2 *ranges, const CamBatch &cb, const PixPtrs &px,
-                          const float *bg, cudaStream_t st, uint32_t *hits, int64_t n_gauss) {
+                          const float *bg, cudaStream_t st, uint32_t *hits, int64_t n_gauss,
+                          const uint32_t *order, int *counter) {
     if (cb.total_tiles <= 0) return;
-    TGS_DISPATCH(fwd_launch, splats, ids, ranges, cb, px, bg, hits, n_gauss, st);
+    TGS_DISPATCH(fwd_launch, splats, ids, ranges, cb, px, bg, hits, n_gauss, order, counter, st);
 }
 
 void launch_blend_backward(int tile, int ppt, const float4 *splats, const uint32_t *ids,
                            const uint2 *ranges, const CamBatch &cb, const PixPtrs &px,
-                           const float *bg, float *sgrads, cudaStream_t st) {
+                           const float *bg, float *sgrads, cudaStream_t st, const uint32_t *order,
+                           int *counter) {
     if (cb.total_tiles <= 0) return;
-    TGS_DISPATCH(bwd_launch, splats, ids, ranges, cb, px, bg, sgrads, st);
+    TGS_DISPATCH(bwd_launch, splats, ids, ranges, cb, px, bg, sgrads, order, counter, st);
 }
 
 void launch_l1(const float *img, const float *tgt, int64_t count, float scale, float *loss,

@@ -199,13 +199,17 @@ void make_full_keys(const uint32_t *tile_keys, const uint32_t *tile_vals, const 
 int blend_supported(int tile, int ppt);
 // hits (may be null): per-Gaussian ray hits added in (Eq. significance-score); record r of
 // view v is Gaussian r - v n_gauss
+// order / counter (both or neither): tiles heaviest first (build_item_order) and a zeroed item
+// counter; at tile 32 / 2 px per thread the warp-item kernels then run a persistent grid in
+// that order (other configurations ignore them)
 void launch_blend_forward(int tile, int ppt, const float4 *splats, const uint32_t *ids,
                           const uint2 *ranges, const CamBatch &cb, const PixPtrs &px,
                           const float *bg, cudaStream_t st, uint32_t *hits = nullptr,
-                          int64_t n_gauss = 0);
+                          int64_t n_gauss = 0, const uint32_t *order = nullptr, int *counter = nullptr);
 void launch_blend_backward(int tile, int ppt, const float4 *splats, const uint32_t *ids,
                            const uint2 *ranges, const CamBatch &cb, const PixPtrs &px,
-                           const float *bg, float *sgrads, cudaStream_t st);
+                           const float *bg, float *sgrads, cudaStream_t st, const uint32_t *order = nullptr,
+                           int *counter = nullptr);
 void launch_l1(const float *img, const float *tgt, int64_t count, float scale, float *loss,
                float *grad, cudaStream_t st);
 
