@@ -5,7 +5,9 @@
 // below 1e-4; the backward walks the list in reverse from each pixel's last contributor and
 // scatters per-splat gradients with one transposed warp reduction and one atomic per value.
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <utility>
 
 #include "blend_warp.cuh"
 
@@ -148,6 +150,7 @@ k_blend_fwd_warp(const float4 *__restrict__ splats, const uint32_t *__restrict__
     }
 }
 
+template <bool BG>
 __global__ void __launch_bounds__(kWarpCta)
 k_blend_bwd_warp(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
                  const uint2 *__restrict__ ranges, const __grid_constant__ CamBatch cb,
@@ -175,7 +178,7 @@ k_blend_bwd_warp(const float4 *__restrict__ splats, const uint32_t *__restrict__
             dG[k] = ok ? d[HW + pix] : 0.f;
             dB[k] = ok ? d[2 * HW + pix] : 0.f;
         }
-        warp_backward<false>(s_slots[w].b, splats, ids, ranges[gt], P, last, Tf, dR, dG, dB, bg0, bg1, bg2, sgrads);
+        warp_backward<false, BG>(s_slots[w].b, splats, ids, ranges[gt], P, last, Tf, dR, dG, dB, bg0, bg1, bg2, sgrads);
     }
 }
 
@@ -185,16 +188,17 @@ template <class K>
 unsigned warp_grid(K kernel, const CamBatch &cb, bool persistent) {
     const unsigned one = (unsigned)cb.total_tiles * (kWBlocks / (kWarpCta / 32));
     if (!persistent) return one;
-    constexpr int kDevices = 64;
     static std::mutex mu;
-    static int grid_of[kDevices] = {};
+    static std::map<std::pair<int, const void *>, int> grid_of;  // (device, kernel) -> grid
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         dev = 0;
     }
+    const auto key = std::make_pair(dev, reinterpret_cast<const void *>(kernel));
     std::lock_guard<std::mutex> lock(mu);
-    if (dev < 0 || dev >= kDevices || grid_of[dev] == 0) {
+    auto it = grid_of.find(key);
+    if (it == grid_of.end()) {
         int sms = 1, b = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
             cudaGetLastError();
@@ -204,11 +208,9 @@ unsigned warp_grid(K kernel, const CamBatch &cb, bool persistent) {
             cudaGetLastError();
             b = 1;
         }
-        const int g = sms * (b < 1 ? 1 : b);
-        if (dev < 0 || dev >= kDevices) return std::min(one, (unsigned)g);
-        grid_of[dev] = g;
+        it = grid_of.emplace(key, sms * (b < 1 ? 1 : b)).first;
     }
-    return std::min(one, (unsigned)grid_of[dev]);
+    return std::min(one, (unsigned)it->second);
 }
 
 __global__ void k_l1(const float *__restrict__ img, const float *__restrict__ tgt, int64_t count,
@@ -268,8 +270,12 @@ void bwd_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, 
     if (TILE == 32 && PPT == 2) {
         const bool pers = order && counter;
         if (!pers) order = nullptr, counter = nullptr;
-        k_blend_bwd_warp<<<warp_grid(k_blend_bwd_warp, cb, pers), kWarpCta, 0, st>>>(
-            splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], sg, order, counter);
+        if (bg[0] != 0.f || bg[1] != 0.f || bg[2] != 0.f)
+            k_blend_bwd_warp<true><<<warp_grid(k_blend_bwd_warp<true>, cb, pers), kWarpCta, 0, st>>>(
+                splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], sg, order, counter);
+        else
+            k_blend_bwd_warp<false><<<warp_grid(k_blend_bwd_warp<false>, cb, pers), kWarpCta, 0, st>>>(
+                splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], sg, order, counter);
         return;
     }
     k_blend_bwd<TILE, PPT><<<cb.total_tiles, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, cb, px,

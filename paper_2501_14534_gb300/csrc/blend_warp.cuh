@@ -6,7 +6,9 @@
 // block) item and walks the tile's list on its own, 32 entries at a time: it loads the 32
 // records, keeps those whose rect meets its block and that may reach alpha >= 1/255 there (the
 // per-warp-block bits of block_masks and stage_splat, for this block alone), packs them in list
-// order into its own shared-memory slots and blends them. No barrier but __syncwarp.
+// order into its own shared-memory slots and blends them. No barrier but __syncwarp. A slot
+// carries the block's pixels inside the splat's rect as a 64-bit mask (block_pixels), so a
+// fragment's rect test is one bit test per pixel.
 //
 // The pixel layout (BlendLayout<32, 2>: 8 columns x 4 rows of lanes, rows y and y + 4 per
 // thread), the blend decisions and every arithmetic step of a fragment are those of
@@ -33,8 +35,8 @@ struct WarpFwdSlots {
     ulonglong2 p1[32];  // (A, A), (B, B): the conic scaled as in stage_splat
     ulonglong2 p2[32];  // (C, C), (o, o)
     ulonglong2 p3[32];  // (r, r), (g, g)
-    float4 p4[32];      // b, b, qmin, cover (as bits: 1 if the rect covers the block)
-    int4 rect[32];
+    float4 p4[32];      // b, b, qmin, unused
+    uint2 pm[32];       // the block's pixels inside the rect (block_pixels)
     int pos[32];        // 1-based list position
     uint32_t id[32];
 };
@@ -42,8 +44,8 @@ struct WarpFwdSlots {
 struct WarpBwdSlots {
     float4 a[32];       // mean2d x, y; scaled conic A, B
     float4 b[32];       // scaled conic C; opacity; r, g
-    float4 d[32];       // b; qmin; cover (bits); record index (bits)
-    int4 rect[32];
+    float4 d[32];       // b; qmin; unused; record index (bits)
+    uint2 pm[32];       // the block's pixels inside the rect (block_pixels)
     int pos[32];
 };
 
@@ -68,17 +70,27 @@ struct WarpPixels {
     }
 };
 
+// The pixels of the 8 x 8 block at (bx0, by0) that lie inside rect r (which meets the block):
+// bit l of .x is pixel 0 of lane l (row l / 8, column l % 8), bit l of .y its pixel 1 (4 rows
+// further down).
+__device__ __forceinline__ uint2 block_pixels(const int4 &r, int bx0, int by0) {
+    const int cx0 = max(r.x - bx0, 0), cx1 = min(r.y - bx0, kWB - 1);
+    const int cy0 = max(r.z - by0, 0), cy1 = min(r.w - by0, kWB - 1);
+    const uint32_t cols = ((0xFFu >> (kWB - 1 - cx1)) & (0xFFu << cx0)) * 0x01010101u;  // in every row
+    const unsigned long long rows = (~0ull >> (8 * (kWB - 1 - cy1))) & (~0ull << (8 * cy0));
+    return make_uint2(cols & (uint32_t)rows, cols & (uint32_t)(rows >> 32));
+}
+
 __device__ __forceinline__ int4 rect_of(const float4 &s2) {
     const uint32_t rx = __float_as_uint(s2.y), ry = __float_as_uint(s2.z);
     return make_int4((int)(rx & 0xFFFFu), (int)(rx >> 16), (int)(ry & 0xFFFFu), (int)(ry >> 16));
 }
 
 // Whether the splat with record words s0, s1 (rp: its record) and rect r meets the block at
-// (bx0, by0) and may reach alpha >= 1/255 on it; cover: the rect contains the block.
+// (bx0, by0) and may reach alpha >= 1/255 on it.
 __device__ __forceinline__ bool block_vis(const float4 &s0, const float4 &s1, const float4 *__restrict__ rp,
-                                          const int4 &r, int bx0, int by0, bool &cover) {
+                                          const int4 &r, int bx0, int by0) {
     const int bx1 = bx0 + kWB - 1, by1 = by0 + kWB - 1;
-    cover = r.x <= bx0 && r.y >= bx1 && r.z <= by0 && r.w >= by1;
     if (!(r.y >= bx0 && r.x <= bx1 && r.w >= by0 && r.z <= by1)) return false;
     const float4 s3 = __ldg(rp + 3);
     return tile_keep(s0.x, s0.y, s0.z, s0.w, s1.x, s3.x, s3.y, s3.z, max(bx0, r.x), min(bx1, r.y), max(by0, r.z),
@@ -88,8 +100,7 @@ __device__ __forceinline__ bool block_vis(const float4 &s0, const float4 &s1, co
 // Loads entry j of the list (if take) and tests it against the block.
 __device__ __forceinline__ bool warp_take(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
                                           uint32_t j, bool take, int bx0, int by0, float4 &s0, float4 &s1,
-                                          float4 &s2, int4 &r, uint32_t &id, bool &cover) {
-    cover = false;
+                                          float4 &s2, int4 &r, uint32_t &id) {
     if (!take) return false;
     id = __ldg(ids + j);
     const float4 *rp = splats + (size_t)kSplatWords / 4 * id;
@@ -97,7 +108,7 @@ __device__ __forceinline__ bool warp_take(const float4 *__restrict__ splats, con
     s1 = __ldg(rp + 1);
     s2 = __ldg(rp + 2);
     r = rect_of(s2);
-    return block_vis(s0, s1, rp, r, bx0, by0, cover);
+    return block_vis(s0, s1, rp, r, bx0, by0);
 }
 
 // Forward of the block over the list [rg.x, rg.y) (tile_forward2's steps). On return each
@@ -117,14 +128,15 @@ __device__ __forceinline__ void warp_forward(WarpFwdSlots &sm, const float4 *__r
     f2_t T2 = one2, Cr2 = f2(0.f, 0.f), Cg2 = Cr2, Cb2 = Cr2;
     int last0 = 0, last1 = 0, exam0 = 0, exam1 = 0;
     bool done0 = !P.in0, done1 = !P.in1;
+    // this lane's bit while its pixel still blends, else 0
+    uint32_t live0 = P.in0 ? (1u << lane) : 0u, live1 = P.in1 ? (1u << lane) : 0u;
     for (uint32_t c0 = rg.x; c0 < rg.y; c0 += 32) {
         if (__all_sync(full, done0 && done1)) break;
         const uint32_t j = c0 + (uint32_t)lane;
         float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
         int4 r = make_int4(0, 0, 0, 0);
         uint32_t id = 0u;
-        bool cover;
-        const bool vis = warp_take(splats, ids, j, j < rg.y, P.bx0, P.by0, s0, s1, s2, r, id, cover);
+        const bool vis = warp_take(splats, ids, j, j < rg.y, P.bx0, P.by0, s0, s1, s2, r, id);
         const uint32_t vb = __ballot_sync(full, vis);
         if (vis) {
             const int sl = __popc(vb & lt);
@@ -135,8 +147,8 @@ __device__ __forceinline__ void warp_forward(WarpFwdSlots &sm, const float4 *__r
             sm.p2[sl] = make_ulonglong2(f2(Cq, Cq), f2(s1.y, s1.y));
             sm.p3[sl] = make_ulonglong2(f2(s1.z, s1.z), f2(s1.w, s1.w));
             const float qmin = -log2f(__fmul_rn(255.f, s1.y));
-            sm.p4[sl] = make_float4(s2.x, s2.x, qmin, __uint_as_float(cover ? 1u : 0u));
-            sm.rect[sl] = r;
+            sm.p4[sl] = make_float4(s2.x, s2.x, qmin, 0.f);
+            sm.pm[sl] = block_pixels(r, P.bx0, P.by0);
             sm.pos[sl] = (int)(j - rg.x) + 1;
             sm.id[sl] = id;
         }
@@ -145,12 +157,10 @@ __device__ __forceinline__ void warp_forward(WarpFwdSlots &sm, const float4 *__r
         for (int m = 0; m < nv; m++) {
             // every 8 fragments: a warp whose pixels all stopped leaves the chunk
             if ((m & 7) == 7 && __all_sync(full, done0 && done1)) break;
-            const int4 rr = sm.rect[m];
+            const uint2 pm = sm.pm[m];
             const float4 p4 = sm.p4[m];
-            const bool cov = __float_as_uint(p4.w) != 0u;
-            const bool xin = cov || (unsigned)(P.x - rr.x) <= (unsigned)(rr.y - rr.x);
-            const bool in0 = !done0 && (cov || (xin && (unsigned)(P.y0 - rr.z) <= (unsigned)(rr.w - rr.z)));
-            const bool in1 = !done1 && (cov || (xin && (unsigned)(P.y1 - rr.z) <= (unsigned)(rr.w - rr.z)));
+            const bool in0 = (pm.x & live0) != 0u;
+            const bool in1 = (pm.y & live1) != 0u;
             bool b0 = false, b1 = false;  // the pixels that blend this fragment
             if (in0 || in1) {
                 const ulonglong2 a = sm.p0[m], b = sm.p1[m], c = sm.p2[m];
@@ -174,10 +184,12 @@ __device__ __forceinline__ void warp_forward(WarpFwdSlots &sm, const float4 *__r
                     b1 = v1 && !st1;
                     if (st0) {
                         done0 = true;
+                        live0 = 0u;
                         if (EXAM) exam0 = sm.pos[m];
                     }
                     if (st1) {
                         done1 = true;
+                        live1 = 0u;
                         if (EXAM) exam1 = sm.pos[m];
                     }
                     if (b0 || b1) {
@@ -219,8 +231,9 @@ __device__ __forceinline__ void warp_forward(WarpFwdSlots &sm, const float4 *__r
 // Backward of the block (tile_backward's steps): the reverse walk from the warp's last
 // contributor with dL/d pixel colour dR, dG, dB and the forward's final transmittances Tf.
 // MOMENTS: the pixel sums of each fragment are added to its gradient record (the preprocess
-// backward applies the conic and opacity); else the splat gradients themselves.
-template <bool MOMENTS>
+// backward applies the conic and opacity); else the splat gradients themselves. BG: the
+// background colour is not zero (with a zero background its term of dL/dalpha is 0 and skipped).
+template <bool MOMENTS, bool BG>
 __device__ __forceinline__ void warp_backward(WarpBwdSlots &sm, const float4 *__restrict__ splats,
                                               const uint32_t *__restrict__ ids, uint2 rg, const WarpPixels &P,
                                               const int last[2], const float Tf[2], const float dR[2],
@@ -228,7 +241,7 @@ __device__ __forceinline__ void warp_backward(WarpBwdSlots &sm, const float4 *__
                                               float bg2, float *__restrict__ sgrads) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
+    const uint32_t lt = (1u << lane) - 1u, lm = 1u << lane;
     float T[2], acd[2], tbg[2];
 #pragma unroll
     for (int k = 0; k < 2; k++) {
@@ -239,7 +252,6 @@ __device__ __forceinline__ void warp_backward(WarpBwdSlots &sm, const float4 *__
     const int wmax = __reduce_max_sync(full, max(last[0], last[1]));
     const uint32_t end = min(rg.y, rg.x + (uint32_t)wmax);
     const float fx = (float)P.x, fy[2] = {(float)P.y0, (float)P.y1};
-    const int py[2] = {P.y0, P.y1};
     for (uint32_t e1 = end; e1 > rg.x;) {
         const uint32_t e0 = (e1 - rg.x > 32u) ? e1 - 32u : rg.x;
         // lane l takes entry e1 - 1 - l: the slots come out in descending list order
@@ -247,28 +259,26 @@ __device__ __forceinline__ void warp_backward(WarpBwdSlots &sm, const float4 *__
         float4 s0 = make_float4(0.f, 0.f, 0.f, 0.f), s1 = s0, s2 = s0;
         int4 r = make_int4(0, 0, 0, 0);
         uint32_t id = 0u;
-        bool cover;
-        const bool vis = warp_take(splats, ids, j, (uint32_t)lane < e1 - e0, P.bx0, P.by0, s0, s1, s2, r, id, cover);
+        const bool vis = warp_take(splats, ids, j, (uint32_t)lane < e1 - e0, P.bx0, P.by0, s0, s1, s2, r, id);
         const uint32_t vb = __ballot_sync(full, vis);
         if (vis) {
             const int sl = __popc(vb & lt);
             sm.a[sl] = make_float4(s0.x, s0.y, __fmul_rn(-0.5f * kLog2e, s0.z), __fmul_rn(-kLog2e, s0.w));
             sm.b[sl] = make_float4(__fmul_rn(-0.5f * kLog2e, s1.x), s1.y, s1.z, s1.w);
             const float qmin = -log2f(__fmul_rn(255.f, s1.y));
-            sm.d[sl] = make_float4(s2.x, qmin, __uint_as_float(cover ? 1u : 0u), __uint_as_float(id));
-            sm.rect[sl] = r;
+            sm.d[sl] = make_float4(s2.x, qmin, 0.f, __uint_as_float(id));
+            sm.pm[sl] = block_pixels(r, P.bx0, P.by0);
             sm.pos[sl] = (int)(j - rg.x) + 1;
         }
         __syncwarp();
         const int nv = __popc(vb);
         for (int m = 0; m < nv; m++) {
             const int pos = sm.pos[m];
-            const int4 rr = sm.rect[m];
+            const uint2 pm = sm.pm[m];
             const float4 a = sm.a[m], b = sm.b[m], dd = sm.d[m];
-            const bool cov = __float_as_uint(dd.z) != 0u;
             const float cbl = dd.x, qmin = dd.y;
             const float dx = a.x - fx, Adx = __fmul_rn(a.z, dx);
-            const bool xin = cov || (unsigned)(P.x - rr.x) <= (unsigned)(rr.y - rr.x);
+            const uint32_t inr[2] = {pm.x & lm, pm.y & lm};
             // per-warp sums over the pixels of u = dL/da G (tile_backward's g[0..8])
             float g[9];
 #pragma unroll
@@ -276,8 +286,7 @@ __device__ __forceinline__ void warp_backward(WarpBwdSlots &sm, const float4 *__
             bool contrib = false;
 #pragma unroll
             for (int k = 0; k < 2; k++) {
-                if (pos > last[k]) continue;
-                if (!cov && !(xin && (unsigned)(py[k] - rr.z) <= (unsigned)(rr.w - rr.z))) continue;
+                if (pos > last[k] || inr[k] == 0u) continue;
                 const float dy = a.y - fy[k];
                 const float q = frag_q(Adx, a.w, b.x, dx, dy);
                 if (q > 0.f || q < qmin) continue;   // skipped in the forward too
@@ -294,7 +303,7 @@ __device__ __forceinline__ void warp_backward(WarpBwdSlots &sm, const float4 *__
                 // dC/da = T (c - acc) - T_final / (1 - a) bg, acc = colour behind this fragment
                 const float cd = fmaf(cbl, dB[k], fmaf(b.w, dG[k], b.z * dR[k]));
                 const float diff = cd - acd[k];
-                const float dLda = fmaf(diff, T[k], -tbg[k] * inv);
+                const float dLda = BG ? fmaf(diff, T[k], -tbg[k] * inv) : diff * T[k];
                 acd[k] = fmaf(alpha, diff, acd[k]);   // now includes this fragment
                 if (xg <= kAlphaMax) {
                     const float u = dLda * G;

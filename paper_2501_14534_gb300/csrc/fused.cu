@@ -113,7 +113,7 @@ k_fused_l1(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
 
 constexpr int kWarpItemThreads = 128;
 
-template <bool HITS>
+template <bool HITS, bool BG>
 __global__ void __launch_bounds__(kWarpItemThreads)
 k_fused_warp(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
              const uint2 *__restrict__ ranges, const uint32_t *__restrict__ order, int n_items,
@@ -166,12 +166,12 @@ k_fused_warp(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids
             dB[k] = eb > 0.f ? scale : (eb < 0.f ? -scale : 0.f);
         }
         loss_acc += warp_sum(lsum) * scale;
-        warp_backward<true>(sm.b, splats, ids, rg, P, last, Tf, dR, dG, dB, bg0, bg1, bg2, sgrads);
+        warp_backward<true, BG>(sm.b, splats, ids, rg, P, last, Tf, dR, dG, dB, bg0, bg1, bg2, sgrads);
     }
     if (lane == 0 && loss) atomicAdd(loss, loss_acc);
 }
 
-template <bool HITS>
+template <bool HITS, bool BG>
 void warp_launch_t(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const uint32_t *order,
                    int *counter, const CamBatch &cb, const PixPtrs &px, const float *bg, float *sgrads,
                    float *loss, uint32_t *hits, uint32_t n_gauss, cudaStream_t st) {
@@ -195,7 +195,7 @@ void warp_launch_t(const float4 *splats, const uint32_t *ids, const uint2 *range
                 cudaGetLastError();
                 sms = 1;
             }
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_warp<HITS>, kWarpItemThreads, 0) !=
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fused_warp<HITS, BG>, kWarpItemThreads, 0) !=
                 cudaSuccess) {
                 cudaGetLastError();
                 b = 1;
@@ -208,7 +208,7 @@ void warp_launch_t(const float4 *splats, const uint32_t *ids, const uint2 *range
     if ((int64_t)grid * (kWarpItemThreads / 32) > warps) grid = (int)((warps + 3) / 4);
     if (grid < 1) grid = 1;
     count_launch();
-    k_fused_warp<HITS><<<grid, kWarpItemThreads, 0, st>>>(splats, ids, ranges, order, cb.total_tiles, counter, cb, px,
+    k_fused_warp<HITS, BG><<<grid, kWarpItemThreads, 0, st>>>(splats, ids, ranges, order, cb.total_tiles, counter, cb, px,
                                                         bg[0], bg[1], bg[2], sgrads, loss, hits, n_gauss);
 }
 
@@ -306,8 +306,11 @@ void launch_fused_l1(int tile, int ppt, int batch, const float4 *splats, const u
     else if (tile == 16 && ppt == 2) fused_launch<16, 2>(batch, splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
     else if (tile == 16 && ppt == 4) fused_launch<16, 4>(batch, splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
     else if (tile == 32 && ppt == 2 && batch == 1) {
-        if (hits) warp_launch_t<true>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, hits, n, st);
-        else warp_launch_t<false>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, hits, n, st);
+        const bool nzbg = bg[0] != 0.f || bg[1] != 0.f || bg[2] != 0.f;
+        if (hits && nzbg) warp_launch_t<true, true>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, hits, n, st);
+        else if (hits) warp_launch_t<true, false>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, hits, n, st);
+        else if (nzbg) warp_launch_t<false, true>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, hits, n, st);
+        else warp_launch_t<false, false>(splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, hits, n, st);
     }
     else if (tile == 32 && ppt == 2) fused_launch<32, 2>(batch, splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
     else if (tile == 32 && ppt == 4) fused_launch<32, 4>(batch, splats, ids, ranges, order, counter, cb, px, bg, sgrads, loss, vis_keys, hits, n, st);
