@@ -154,6 +154,7 @@ __device__ __forceinline__ void warp_forward(WarpFwdSlots &sm, const float4 *__r
         }
         __syncwarp();
         const int nv = __popc(vb);
+#pragma unroll 2
         for (int m = 0; m < nv; m++) {
             // every 8 fragments: a warp whose pixels all stopped leaves the chunk
             if ((m & 7) == 7 && __all_sync(full, done0 && done1)) break;
@@ -162,7 +163,7 @@ __device__ __forceinline__ void warp_forward(WarpFwdSlots &sm, const float4 *__r
             const bool in0 = (pm.x & live0) != 0u;
             const bool in1 = (pm.y & live1) != 0u;
             bool b0 = false, b1 = false;  // the pixels that blend this fragment
-            if (in0 || in1) {
+            {  // no branch on in0 || in1: some lane of the warp nearly always has one
                 const ulonglong2 a = sm.p0[m], b = sm.p1[m], c = sm.p2[m];
                 const f2_t dx2 = sub2(a.x, fx2);
                 const f2_t dy2 = sub2(a.y, fy2);
