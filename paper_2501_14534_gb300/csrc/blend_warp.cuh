@@ -93,8 +93,8 @@ __device__ __forceinline__ bool block_vis(const float4 &s0, const float4 &s1, co
     const int bx1 = bx0 + kWB - 1, by1 = by0 + kWB - 1;
     if (!(r.y >= bx0 && r.x <= bx1 && r.w >= by0 && r.z <= by1)) return false;
     const float4 s3 = __ldg(rp + 3);
-    return tile_keep(s0.x, s0.y, s0.z, s0.w, s1.x, s3.x, s3.y, s3.z, max(bx0, r.x), min(bx1, r.y), max(by0, r.z),
-                     min(by1, r.w));
+    return tile_keep_flat(s0.x, s0.y, s0.z, s0.w, s1.x, s3.x, s3.y, s3.z, max(bx0, r.x), min(bx1, r.y),
+                          max(by0, r.z), min(by1, r.w));
 }
 
 // Loads entry j of the list (if take) and tests it against the block.

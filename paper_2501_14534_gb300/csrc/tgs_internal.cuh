@@ -139,6 +139,31 @@ __device__ __forceinline__ bool tile_keep(float mx, float my, float a, float b, 
     return q <= tau;
 }
 
+// tile_keep without branches: the same steps, both edge candidates always evaluated and
+// selected, so the result is the same bit for bit. Cheaper where the lanes of a warp take
+// different cases (the blend's per-block tests); the key count keeps the branches (measured
+// faster there).
+__device__ __forceinline__ bool tile_keep_flat(float mx, float my, float a, float b, float c, float tau,
+                                               float b_over_c, float b_over_a, int x0, int x1, int y0,
+                                               int y1) {
+    const float fx0 = (float)x0, fx1 = (float)x1, fy0 = (float)y0, fy1 = (float)y1;
+    const bool xin = mx >= fx0 && mx <= fx1, yin = my >= fy0 && my <= fy1;
+    const float xe = mx < fx0 ? fx0 : fx1;
+    const float dx1 = __fsub_rn(xe, mx);
+    const float ys = __fsub_rn(my, __fmul_rn(b_over_c, dx1));
+    const float dy1 = __fsub_rn(fminf(fmaxf(ys, fy0), fy1), my);
+    const float q1 = cull_quad(a, b, c, dx1, dy1);
+    const float ye = my < fy0 ? fy0 : fy1;
+    const float dy2 = __fsub_rn(ye, my);
+    const float xs = __fsub_rn(mx, __fmul_rn(b_over_a, dy2));
+    const float dx2 = __fsub_rn(fminf(fmaxf(xs, fx0), fx1), mx);
+    const float q2 = cull_quad(a, b, c, dx2, dy2);
+    const float inf = __int_as_float(0x7f800000);
+    float q = fminf(fminf(inf, xin ? inf : q1), yin ? inf : q2);
+    if (xin && yin) q = 0.f;
+    return q <= tau;
+}
+
 // ---- launchers implemented in the .cu files --------------------------------------------
 
 // preprocess.cu: lambda_m L_m + lambda_sh L_sh (Eq. loss3dgs) over n Gaussians added to *loss
