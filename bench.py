@@ -7,7 +7,7 @@ SH-band masks at eps = 0.5).
 Prints one JSON line. value = views per second of the batched step with inputs resident in
 HBM; e2e = the same through one C-ABI call per step with the Gaussian parameters and target
 images in pinned host memory (tgs_train_step_batched_host: the library copies them in, the
-copies of one step overlapping the previous step's compute, and copies the loss back).
+copies of a step overlapping the compute of the steps before it, and copies the loss back).
 Also reports the plain single-view path (views/s, at tile 16 and at its best configuration)
 and forward-only render FPS for comparison, a significance pruning round, the roofline of the
 dominant kernel against peaks measured on the GPU (tgs_measure_peaks), a sub-record for each of
@@ -676,7 +676,7 @@ def main():
         rast.train_step_batched_host(hostg, cams, host_t, grads, stats, loss_host, graph=True, cams_struct=camarr)
 
     with torch.cuda.stream(stream):
-        for _ in range(3):   # both buffer sets filled and their graphs captured
+        for _ in range(4):   # every buffer set filled and its graph captured
             e2e_step()
     stream.synchronize()
     n_e2e = max(5, min(args.steps, 20))
@@ -847,7 +847,7 @@ def main():
             "e2e": {"value": e2e_value, "unit": "views/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": 4, "ms_per_step": e2e_ms, "step_ms": dist(e2e_per),
                     "api": "tgs_train_step_batched_host (pinned host inputs, copies on the library's upload "
-                           "stream overlapping the previous step)"},
+                           "stream into three buffer sets, overlapping the previous steps)"},
             "plain_views_per_s": plain_vps, "plain_best": {"config": best_cfg, "views_per_s": plain_best},
             "plain_by_config": plain_by_cfg,
             "render_fps": render_fps, "render_fps_fp16_params": render_fps_fp16,

@@ -269,9 +269,9 @@ tgs_status tgs_train_step_batched(tgs_ctx *ctx, const tgs_gaussians *g, const tg
    tgs_train_step_batched on them, and copies the loss into *loss_host (host float, may be
    NULL). grads and stats are device memory, as for tgs_train_step_batched.
    The copies go on an upload stream of the context, one cudaMemcpyAsync per array, into one
-   of two buffer sets used in turn, so that the next call's copies overlap this call's step;
-   the step waits for its copies, and the copies into a set wait for the step that last read
-   it. Host buffers should be pinned (cudaHostAlloc / cudaHostRegister) for the copies to be
+   of three buffer sets used in turn, so that the next calls' copies overlap this call's step
+   (up to two steps ahead); the step waits for its copies, and the copies into a set wait for
+   the step that last read it. Host buffers should be pinned (cudaHostAlloc / cudaHostRegister) for the copies to be
    asynchronous, and must not change until the copies have run (e.g. until the next call
    returns, or a stream synchronisation). With TGS_USE_GRAPH each buffer set keeps its own
    captured graph. Not capturable (TGS_ERR_NOT_SUPPORTED inside stream capture); the first

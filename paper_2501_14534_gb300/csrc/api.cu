@@ -54,14 +54,16 @@ struct tgs_ctx {
     std::vector<Graph> graphs;
     uint64_t graph_clock = 0;
     cudaStream_t side = nullptr;
-    // tgs_train_step_batched_host: two sets of device copies of a step's inputs, filled on an
-    // upload stream while the previous step computes
+    // tgs_train_step_batched_host: three sets of device copies of a step's inputs, filled on an
+    // upload stream while the previous steps compute (the copies of a step may run up to two
+    // steps ahead, which absorbs a slow copy)
     struct Stage {
         Buf params, targets;
         cudaEvent_t copied = nullptr, consumed = nullptr;
         bool used = false;
     };
-    Stage stage[2];
+    static constexpr int kStages = 3;
+    Stage stage[kStages];
     int stage_next = 0;
     cudaStream_t upload = nullptr;
     Buf lossbuf;
@@ -1176,7 +1178,7 @@ tgs_status tgs_train_step_batched_host(tgs_ctx *c, const tgs_gaussians *gh, cons
         tb += (12 * (size_t)cams[v].width * cams[v].height + 255) / 256 * 256;
     }
     tgs_ctx::Stage &sg = c->stage[c->stage_next];
-    c->stage_next ^= 1;
+    c->stage_next = (c->stage_next + 1) % tgs_ctx::kStages;
     if (!c->upload) TGS_CHECK(cudaStreamCreateWithFlags(&c->upload, cudaStreamNonBlocking));
     if (!sg.copied) TGS_CHECK(cudaEventCreateWithFlags(&sg.copied, cudaEventDisableTiming));
     if (!sg.consumed) TGS_CHECK(cudaEventCreateWithFlags(&sg.consumed, cudaEventDisableTiming));
@@ -1352,7 +1354,8 @@ size_t tgs_arena_bytes(const tgs_ctx *c) {
                          &c->cv1, &c->offsets, &c->tk0, &c->tv0, &c->tk1, &c->tv1, &c->ranges, &c->hist,
                          &c->partials, &c->sgrads, &c->counts, &c->status, &c->pixstate, &c->dimg,
                          &c->images, &c->items, &c->kmask, &c->viskeys, &c->ssim, &c->cbuf, &c->lossbuf,
-                         &c->stage[0].params, &c->stage[0].targets, &c->stage[1].params, &c->stage[1].targets};
+                         &c->stage[0].params, &c->stage[0].targets, &c->stage[1].params, &c->stage[1].targets,
+                         &c->stage[2].params, &c->stage[2].targets};
     size_t b = 0;
     for (const Buf *x : bufs) b += x->bytes;
     return b;

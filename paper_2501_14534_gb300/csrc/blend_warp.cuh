@@ -26,27 +26,26 @@ constexpr int kWRS = 4;       // rows between a thread's two pixels
 constexpr int kWTile = 32;    // tile side of the lists
 constexpr int kWBlocks = 16;  // blocks per tile
 // Up to this many contributing lanes a fragment's sums go out as per-lane atomics, above it
-// through a warp reduction (measured on the 1M x 16-view step: 16 -> 5.80, 20 -> 5.79,
-// 24 -> 5.82, 28 -> 5.93 ms per fused blend).
-constexpr int kWarpDirectLanes = 20;
+// through a warp reduction (measured on the 1M x 16-view step, fused blend per step: 16 -> 5.80,
+// 20 -> 5.79, 24 -> 5.82, 28 -> 5.93 ms; with the 12-shuffle reduction of the moments
+// 12 -> 5.18, 16 -> 5.15, 20 -> 5.17, 24 -> 5.28 ms).
+constexpr int kWarpDirectLanes = 16;
 
 struct WarpFwdSlots {
     ulonglong2 p0[32];  // (mx, mx), (my, my)
     ulonglong2 p1[32];  // (A, A), (B, B): the conic scaled as in stage_splat
     ulonglong2 p2[32];  // (C, C), (o, o)
     ulonglong2 p3[32];  // (r, r), (g, g)
-    float4 p4[32];      // b, b, qmin, unused
+    float4 p4[32];      // b, b, qmin, 1-based list position (int bits; in the same load as qmin)
     uint2 pm[32];       // the block's pixels inside the rect (block_pixels)
-    int pos[32];        // 1-based list position
     uint32_t id[32];
 };
 
 struct WarpBwdSlots {
     float4 a[32];       // mean2d x, y; scaled conic A, B
     float4 b[32];       // scaled conic C; opacity; r, g
-    float4 d[32];       // b; qmin; unused; record index (bits)
+    float4 d[32];       // b; qmin; 1-based list position (int bits); record index (bits)
     uint2 pm[32];       // the block's pixels inside the rect (block_pixels)
-    int pos[32];
 };
 
 union WarpSlots {
@@ -147,9 +146,8 @@ __device__ __forceinline__ void warp_forward(WarpFwdSlots &sm, const float4 *__r
             sm.p2[sl] = make_ulonglong2(f2(Cq, Cq), f2(s1.y, s1.y));
             sm.p3[sl] = make_ulonglong2(f2(s1.z, s1.z), f2(s1.w, s1.w));
             const float qmin = -log2f(__fmul_rn(255.f, s1.y));
-            sm.p4[sl] = make_float4(s2.x, s2.x, qmin, 0.f);
+            sm.p4[sl] = make_float4(s2.x, s2.x, qmin, __int_as_float((int)(j - rg.x) + 1));
             sm.pm[sl] = block_pixels(r, P.bx0, P.by0);
-            sm.pos[sl] = (int)(j - rg.x) + 1;
             sm.id[sl] = id;
         }
         __syncwarp();
@@ -186,15 +184,15 @@ __device__ __forceinline__ void warp_forward(WarpFwdSlots &sm, const float4 *__r
                     if (st0) {
                         done0 = true;
                         live0 = 0u;
-                        if (EXAM) exam0 = sm.pos[m];
+                        if (EXAM) exam0 = __float_as_int(p4.w);
                     }
                     if (st1) {
                         done1 = true;
                         live1 = 0u;
-                        if (EXAM) exam1 = sm.pos[m];
+                        if (EXAM) exam1 = __float_as_int(p4.w);
                     }
                     if (b0 || b1) {
-                        const int pos = sm.pos[m];
+                        const int pos = __float_as_int(p4.w);
                         float wa, wb, Ta, Tb;
                         f2get(mul2(al2, T2), wa, wb);
                         const f2_t w2 = f2(b0 ? wa : 0.f, b1 ? wb : 0.f);
@@ -267,16 +265,15 @@ __device__ __forceinline__ void warp_backward(WarpBwdSlots &sm, const float4 *__
             sm.a[sl] = make_float4(s0.x, s0.y, __fmul_rn(-0.5f * kLog2e, s0.z), __fmul_rn(-kLog2e, s0.w));
             sm.b[sl] = make_float4(__fmul_rn(-0.5f * kLog2e, s1.x), s1.y, s1.z, s1.w);
             const float qmin = -log2f(__fmul_rn(255.f, s1.y));
-            sm.d[sl] = make_float4(s2.x, qmin, 0.f, __uint_as_float(id));
+            sm.d[sl] = make_float4(s2.x, qmin, __int_as_float((int)(j - rg.x) + 1), __uint_as_float(id));
             sm.pm[sl] = block_pixels(r, P.bx0, P.by0);
-            sm.pos[sl] = (int)(j - rg.x) + 1;
         }
         __syncwarp();
         const int nv = __popc(vb);
         for (int m = 0; m < nv; m++) {
-            const int pos = sm.pos[m];
             const uint2 pm = sm.pm[m];
             const float4 a = sm.a[m], b = sm.b[m], dd = sm.d[m];
+            const int pos = __float_as_int(dd.z);
             const float cbl = dd.x, qmin = dd.y;
             const float dx = a.x - fx, Adx = __fmul_rn(a.z, dx);
             const uint32_t inr[2] = {pm.x & lm, pm.y & lm};
@@ -338,14 +335,51 @@ __device__ __forceinline__ void warp_backward(WarpBwdSlots &sm, const float4 *__
                 }
                 continue;
             }
-            warp_transpose_reduce8(g, lane);
-            const float gb = warp_sum(g[8]);
             if (MOMENTS) {
-                // lane 4j holds the total of value j
+                // values 0..7 by halving exchange over lanes 16, 8, 4 with value 8 summed alongside,
+                // then (value, value 8) by one more exchange over lane 2 and a butterfly over
+                // lane 1: 12 shuffles instead of 14; lane 4j holds the total of value j, lane 2
+                // that of value 8
+                {
+                    const bool up = lane & 16;
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const float send = up ? g[e] : g[e + 4];
+                        const float keep = up ? g[e + 4] : g[e];
+                        g[e] = keep + __shfl_xor_sync(full, send, 16);
+                    }
+                    g[8] += __shfl_xor_sync(full, g[8], 16);
+                }
+                {
+                    const bool up = lane & 8;
+#pragma unroll
+                    for (int e = 0; e < 2; e++) {
+                        const float send = up ? g[e] : g[e + 2];
+                        const float keep = up ? g[e + 2] : g[e];
+                        g[e] = keep + __shfl_xor_sync(full, send, 8);
+                    }
+                    g[8] += __shfl_xor_sync(full, g[8], 8);
+                }
+                {
+                    const bool up = lane & 4;
+                    const float send = up ? g[0] : g[1];
+                    const float keep = up ? g[1] : g[0];
+                    g[0] = keep + __shfl_xor_sync(full, send, 4);
+                    g[8] += __shfl_xor_sync(full, g[8], 4);
+                }
+                {
+                    const bool up = lane & 2;
+                    const float send = up ? g[0] : g[8];
+                    const float keep = up ? g[8] : g[0];
+                    g[0] = keep + __shfl_xor_sync(full, send, 2);
+                }
+                g[0] += __shfl_xor_sync(full, g[0], 1);
                 if ((lane & 3) == 0) atomicAdd(dst + (lane >> 2), g[0]);
-                if (lane == 0) atomicAdd(dst + 8, gb);
+                if (lane == 2) atomicAdd(dst + 8, g[0]);
                 continue;
             }
+            warp_transpose_reduce8(g, lane);
+            const float gb = warp_sum(g[8]);
             // as tile_backward: values 0, 1 mean2d; 2, 3, 4 conic; 5 opacity; 6, 7 rgb
             const int jj = lane >> 2;
             const float Sx = __shfl_sync(full, g[0], 0), Sy = __shfl_sync(full, g[0], 4);

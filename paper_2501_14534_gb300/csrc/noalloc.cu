@@ -17,7 +17,8 @@ namespace {
 
 constexpr int64_t kRec = TGS_NOALLOC_MAX_RECORDS;
 constexpr int64_t kKeys = TGS_NOALLOC_MAX_KEYS;
-// same sizes as radix_hist_needed / scan_partials_needed in sort.cu (checked at set-up)
+// at least the sizes radix_hist_needed / scan_partials_needed in sort.cu ask for (its sort blocks
+// hold at least 2048 items; checked at set-up)
 constexpr int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 constexpr int64_t round4(int64_t a) { return (a + 3) / 4 * 4; }  // 16-byte aligned regions
 constexpr int64_t kItems = kRec > kKeys ? kRec : kKeys;

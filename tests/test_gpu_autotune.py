@@ -82,7 +82,11 @@ def test_autotuned_config_renders_the_same_images(R):
         out[name] = (imgs, grads, loss.item())
     for a, b in zip(out["tuned"][0], out["base"][0]):
         assert torch.equal(a, b)
-    assert abs(out["tuned"][2] - out["base"][2]) <= 1e-6 * out["base"][2]
+    # the same 4.5e5 per-pixel L1 terms (R13) summed in another order: per-warp partials over
+    # each warp's items and one atomic per warp at tile 32, one atomic per tile at tile 16;
+    # float32 rounding of such chains is of order 1e-6 relative (measured 1.0e-6), so 1e-5
+    # (about 170 ulp of the sum) bounds the order effect while the images above are exact
+    assert abs(out["tuned"][2] - out["base"][2]) <= 1e-5 * out["base"][2]
     for k in out["base"][1]:
         a = out["tuned"][1][k].double().cpu().numpy()
         b = out["base"][1][k].double().cpu().numpy()

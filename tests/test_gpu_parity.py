@@ -410,8 +410,9 @@ def test_graph_replay_equals_direct_step(R):
 @pytest.mark.parametrize("graph", [False, True])
 def test_host_buffer_step_equals_device_step(R, graph):
     """tgs_train_step_batched_host (parameters and targets in pinned host memory, copied by
-    the library on its upload stream into two alternating buffer sets) gives the loss and
-    gradients of the device-resident step, on consecutive calls with changing inputs."""
+    the library on its upload stream into three buffer sets used in turn) gives the loss and
+    gradients of the device-resident step, on consecutive calls with changing inputs (every
+    set used, then reused)."""
     scene, cams, targets, st = batched_case(3000)
     rast = make_rast(R, st)
     g = gpu_scene(R, scene)
@@ -419,7 +420,7 @@ def test_host_buffer_step_equals_device_step(R, graph):
     hostg = R.Gaussians(**{k: t.detach().cpu().pin_memory() for k, t in g.params().items()},
                         sh_degree_max=g.sh_degree_max)
     s = torch.cuda.Stream()
-    for call in range(4):
+    for call in range(5):
         # a different target set each call: a copy landing in the wrong buffer set would show
         tgt = [np.ascontiguousarray(np.roll(t, call, axis=2)) for t in targets]
         host_t = [torch.from_numpy(t).pin_memory() for t in tgt]
