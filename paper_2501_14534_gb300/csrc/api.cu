@@ -1021,8 +1021,9 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
             }
         }
         mark(c, stage++, "blend_backward", st);
+        // pixel sums (moments), as the fused kernel leaves them
         launch_blend_backward(c->cfg.tile, c->cfg.ppt, as<float4>(c->splats), ids, as<uint2>(c->ranges), cb, px,
-                              c->cfg.bg, as<float>(c->sgrads), st, order, order ? ctr + 1 : nullptr);
+                              c->cfg.bg, as<float>(c->sgrads), st, order, order ? ctr + 1 : nullptr, 1);
     } else {
         mark(c, stage++, "item_order", st);
         uint32_t *it = as<uint32_t>(c->items);
@@ -1040,9 +1041,9 @@ static tgs_status batched_body(tgs_ctx *c, const tgs_gaussians *g, const GaussPt
     mark(c, stage++, "preprocess_backward", st);
     GradPtrs o = grad_ptrs(grads, stats, (flags & TGS_ACCUMULATE) ? 1 : 0);
     if (flags & TGS_MASK_LOSS) with_mask_loss(c->cfg, n, o);
-    // the fused blend leaves pixel sums (moments) in the gradient records
+    // both blends leave pixel sums (moments) in the gradient records
     launch_preprocess_backward(gp, cb, as<float4>(c->sgrads), as<int32_t>(c->radii), o,
-                               (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, split ? 0 : 1, st);
+                               (flags & TGS_NO_SH_REST_GRAD) ? 1 : 0, 1, st);
     if ((flags & TGS_MASK_LOSS) && loss_out)  // the value of the mask terms (Eq. loss3dgs)
         launch_mask_loss(g->mask_logits, g->sh_mask_logits, n, c->cfg.lambda_mask, c->cfg.lambda_sh_mask, loss_out,
                          nullptr, nullptr, st);

@@ -57,7 +57,7 @@ k_blend_fwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
     }
 }
 
-template <int TILE, int PPT>
+template <int TILE, int PPT, bool MOMENTS>
 __global__ void __launch_bounds__(TILE * TILE / PPT)
 k_blend_bwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
             const uint2 *__restrict__ ranges, const __grid_constant__ CamBatch cb,
@@ -83,7 +83,7 @@ k_blend_bwd(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
         in.dG[k] = ok ? d[HW + pix] : 0.f;
         in.dB[k] = ok ? d[2 * HW + pix] : 0.f;
     }
-    tile_backward<TILE, PPT>(sm, splats, ids, ranges[gt], P, in, bg0, bg1, bg2, sgrads);
+    tile_backward<TILE, PPT, MOMENTS>(sm, splats, ids, ranges[gt], P, in, bg0, bg1, bg2, sgrads);
 }
 
 // Warp items at 32 x 32 tiles and 2 pixels per thread (blend_warp.cuh). Without an item
@@ -150,7 +150,7 @@ k_blend_fwd_warp(const float4 *__restrict__ splats, const uint32_t *__restrict__
     }
 }
 
-template <bool BG>
+template <bool MOMENTS, bool BG>
 __global__ void __launch_bounds__(kWarpCta)
 k_blend_bwd_warp(const float4 *__restrict__ splats, const uint32_t *__restrict__ ids,
                  const uint2 *__restrict__ ranges, const __grid_constant__ CamBatch cb,
@@ -178,7 +178,7 @@ k_blend_bwd_warp(const float4 *__restrict__ splats, const uint32_t *__restrict__
             dG[k] = ok ? d[HW + pix] : 0.f;
             dB[k] = ok ? d[2 * HW + pix] : 0.f;
         }
-        warp_backward<false, BG>(s_slots[w].b, splats, ids, ranges[gt], P, last, Tf, dR, dG, dB, bg0, bg1, bg2, sgrads);
+        warp_backward<MOMENTS, BG>(s_slots[w].b, splats, ids, ranges[gt], P, last, Tf, dR, dG, dB, bg0, bg1, bg2, sgrads);
     }
 }
 
@@ -262,24 +262,33 @@ void fwd_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, 
 #undef TGS_FWD
 }
 
-template <int TILE, int PPT>
-void bwd_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const CamBatch &cb,
-                const PixPtrs &px, const float *bg, float *sg, const uint32_t *order, int *counter,
-                cudaStream_t st) {
+template <int TILE, int PPT, bool MOMENTS>
+void bwd_launch_t(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const CamBatch &cb,
+                  const PixPtrs &px, const float *bg, float *sg, const uint32_t *order, int *counter,
+                  cudaStream_t st) {
     count_launch();
     if (TILE == 32 && PPT == 2) {
         const bool pers = order && counter;
         if (!pers) order = nullptr, counter = nullptr;
         if (bg[0] != 0.f || bg[1] != 0.f || bg[2] != 0.f)
-            k_blend_bwd_warp<true><<<warp_grid(k_blend_bwd_warp<true>, cb, pers), kWarpCta, 0, st>>>(
+            k_blend_bwd_warp<MOMENTS, true><<<warp_grid(k_blend_bwd_warp<MOMENTS, true>, cb, pers), kWarpCta, 0, st>>>(
                 splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], sg, order, counter);
         else
-            k_blend_bwd_warp<false><<<warp_grid(k_blend_bwd_warp<false>, cb, pers), kWarpCta, 0, st>>>(
-                splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], sg, order, counter);
+            k_blend_bwd_warp<MOMENTS, false><<<warp_grid(k_blend_bwd_warp<MOMENTS, false>, cb, pers), kWarpCta, 0,
+                                                st>>>(splats, ids, ranges, cb, px, bg[0], bg[1], bg[2], sg, order,
+                                                      counter);
         return;
     }
-    k_blend_bwd<TILE, PPT><<<cb.total_tiles, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, cb, px,
-                                                                         bg[0], bg[1], bg[2], sg);
+    k_blend_bwd<TILE, PPT, MOMENTS><<<cb.total_tiles, TILE * TILE / PPT, 0, st>>>(splats, ids, ranges, cb, px,
+                                                                                  bg[0], bg[1], bg[2], sg);
+}
+
+template <int TILE, int PPT>
+void bwd_launch(const float4 *splats, const uint32_t *ids, const uint2 *ranges, const CamBatch &cb,
+                const PixPtrs &px, const float *bg, float *sg, const uint32_t *order, int *counter, int moments,
+                cudaStream_t st) {
+    if (moments) bwd_launch_t<TILE, PPT, true>(splats, ids, ranges, cb, px, bg, sg, order, counter, st);
+    else bwd_launch_t<TILE, PPT, false>(splats, ids, ranges, cb, px, bg, sg, order, counter, st);
 }
 
 }  // namespace
@@ -314,9 +323,9 @@ void launch_blend_forward(int tile, int ppt, const float4 *splats, const uint32_
 void launch_blend_backward(int tile, int ppt, const float4 *splats, const uint32_t *ids,
                            const uint2 *ranges, const CamBatch &cb, const PixPtrs &px,
                            const float *bg, float *sgrads, cudaStream_t st, const uint32_t *order,
-                           int *counter) {
+                           int *counter, int moments) {
     if (cb.total_tiles <= 0) return;
-    TGS_DISPATCH(bwd_launch, splats, ids, ranges, cb, px, bg, sgrads, order, counter, st);
+    TGS_DISPATCH(bwd_launch, splats, ids, ranges, cb, px, bg, sgrads, order, counter, moments, st);
 }
 
 void launch_l1(const float *img, const float *tgt, int64_t count, float scale, float *loss,

@@ -231,10 +231,12 @@ void launch_blend_forward(int tile, int ppt, const float4 *splats, const uint32_
                           const uint2 *ranges, const CamBatch &cb, const PixPtrs &px,
                           const float *bg, cudaStream_t st, uint32_t *hits = nullptr,
                           int64_t n_gauss = 0, const uint32_t *order = nullptr, int *counter = nullptr);
+// moments != 0: the records receive the pixel sums of the fused step's backward (see
+// tile_backward) instead of the splat gradients, for launch_preprocess_backward(moments = 1)
 void launch_blend_backward(int tile, int ppt, const float4 *splats, const uint32_t *ids,
                            const uint2 *ranges, const CamBatch &cb, const PixPtrs &px,
                            const float *bg, float *sgrads, cudaStream_t st, const uint32_t *order = nullptr,
-                           int *counter = nullptr);
+                           int *counter = nullptr, int moments = 0);
 void launch_l1(const float *img, const float *tgt, int64_t count, float scale, float *loss,
                float *grad, cudaStream_t st);
 
