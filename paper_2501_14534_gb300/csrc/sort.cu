@@ -335,10 +335,11 @@ __global__ void __launch_bounds__(kRadixBins) k_digit_starts(uint32_t *__restric
 // holding the same digit). Then one pass over the digits turns the per-warp counts into each
 // warp's start within each digit, the items are placed in shared memory in (digit, index)
 // order, and written out so that each digit's run of the block goes to consecutive addresses.
-// The values wait in shared memory in input order meanwhile (registers only for keys and
-// ranks; 59.5 KB of shared memory: 3 CTAs per SM).
+// The values are read from global memory only when placed (registers only for keys and ranks,
+// no shared-memory copy of the input values: 43 KB of shared memory and at most 64 registers,
+// 4 CTAs per SM instead of 3 -- binning 2.28 -> 2.15 ms per step on the 1M x 16-view step).
 template <int BITS>
-__global__ void __launch_bounds__(kRadixThreads, 3)
+__global__ void __launch_bounds__(kRadixThreads, 4)
 k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 const uint32_t *n_dev, int64_t n_cap, int shift, uint32_t mask,
                 const uint32_t *__restrict__ offsets, int64_t nblocks,
@@ -348,7 +349,7 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
     __shared__ uint32_t s_start[kRadixBins];    // start of each digit in the block's order
     __shared__ uint32_t s_goff[kRadixBins];     // global position of the block's digit run
     __shared__ uint32_t s_warp[33];
-    __shared__ uint32_t s_k[kRadixTile], s_v[kRadixTile], s_vin[kRadixTile];
+    __shared__ uint32_t s_k[kRadixTile], s_v[kRadixTile];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const unsigned full = 0xffffffffu;
     const int64_t n = count_of(n_dev, n_cap);
@@ -368,12 +369,6 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
         const int j = wbase + r * 32 + lane;
         const bool valid = j < cnt;
         kr[r] = valid ? keys_in[base + j] : 0u;
-    }
-#pragma unroll
-    for (int r = 0; r < R; r++) {
-        const int j = wbase + r * 32 + lane;
-        // no input values: the items' own positions (the first pass of a sort of indices)
-        if (j < cnt) s_vin[j] = vals_in ? vals_in[base + j] : (uint32_t)(base + j);
     }
 #pragma unroll
     for (int r = 0; r < R; r++) {
@@ -411,7 +406,8 @@ k_radix_scatter(const uint32_t *__restrict__ keys_in, const uint32_t *__restrict
             const uint32_t d = (kr[r] >> shift) & mask;
             const uint32_t lp = s_start[d] + s_cnt[w][d] + rk[r];
             s_k[lp] = kr[r];
-            s_v[lp] = s_vin[j];
+            // no input values: the items' own positions (the first pass of a sort of indices)
+            s_v[lp] = vals_in ? vals_in[base + j] : (uint32_t)(base + j);
         }
     }
     __syncthreads();
